@@ -1,0 +1,406 @@
+/*
+ * lqcd_oracle.c -- plain, slow, obviously-correct FP64 CPU oracle for the
+ * even/odd staggered Dirac operator and the multi-shift conjugate gradient of
+ * Bonati et al., "Design and optimization of a portable LQCD Monte Carlo code
+ * using OpenACC" (arXiv:1701.00426).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the smoke check and the benchmark's CPU
+ * baseline leg do.  It shares no code, header, table or helper with the CUDA
+ * path: it is written directly from the paper's definitions with
+ * full-lattice coordinate loops and C99 `double complex` arithmetic.
+ *
+ * Definitions followed (paper sections / equations):
+ *   - Eq. (lexicographic_eo), Sec. 4.1: half-lattice index
+ *       idxh = (x0 + N0 (x1 + N1 (x2 + N2 x3))) / 2  for sites of one parity;
+ *     all sides even.
+ *   - Eq. (diracblock), Sec. 2.2: M = m I + [[0, D_oe], [D_eo, 0]],
+ *     D_oe^dag = -D_eo; D_eo maps odd-site vectors to even sites.
+ *   - Eq. (lineqeo), Sec. 2.2: (m^2 I - D_eo D_oe) phi_e = b_e, positive
+ *     definite, solved by CG.
+ *   - Eq. (shlineq), Sec. 2.2: shifted systems (A + sigma_i) x_i = b solved
+ *     together using one matrix-vector product per iteration thanks to the
+ *     shift invariance of the Krylov space.
+ *
+ * Readings where the paper is silent (each also listed in the design doc):
+ *   - D carries the factor 1/2:  (D psi)(n) = 1/2 sum_mu [ s_mu(n) U_mu(n)
+ *     psi(n+mu) - s_mu(n-mu) U_mu(n-mu)^dag psi(n-mu) ].
+ *   - Staggered phases eta_0 = 1, eta_mu = (-1)^(x_0+...+x_{mu-1}); time is
+ *     x3; the antiperiodic boundary is a factor -1 on U_3(n) with x3 = N3-1.
+ *     s_mu(n) = eta_mu(n) * (that boundary factor).
+ *   - Multi-shift CG: base system = smallest shift; recurrences for the
+ *     shifted coefficients derived from the collinearity of shifted residuals
+ *     (written out at oracle_mscg below); a shift stops when
+ *     |zeta_i| ||r|| <= tol ||b||; the FP64 true residual is then checked and
+ *     a shift whose true residual exceeds tol is finished by plain CG started
+ *     from its current solution.
+ *
+ * Parity of every function here is pinned by tests/test_oracle_*.py against
+ * invariants and closed forms (anti-hermiticity, gauge covariance, the free
+ * field spectrum, brute-force geometry, dense LAPACK solves).
+ *
+ * Mutation hooks: compiling with -DORACLE_MUTANT=k plants one deliberate
+ * mistake (listed at each #if); the test suite builds those variants on the
+ * CPU and checks that the pins catch every one.  The default build has none.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef ORACLE_MUTANT
+#define ORACLE_MUTANT 0
+#endif
+
+typedef double complex cplx;
+
+/* ------------------------------------------------------------------------ */
+/* Geometry: Eq. (lexicographic_eo)                                          */
+/* ------------------------------------------------------------------------ */
+
+static long volume(const int N[4]) { return (long)N[0] * N[1] * N[2] * N[3]; }
+
+static long lex_index(const int N[4], const int x[4])
+{
+    return x[0] + (long)N[0] * (x[1] + (long)N[1] * (x[2] + (long)N[2] * x[3]));
+}
+
+long oracle_lex(const int N[4], const int x[4]) { return lex_index(N, x); }
+
+long oracle_idxh(const int N[4], const int x[4]) { return lex_index(N, x) / 2; }
+
+int oracle_parity(const int x[4]) { return (x[0] + x[1] + x[2] + x[3]) & 1; }
+
+/* Staggered sign of the link U_mu(x): eta_mu(x) times the antiperiodic
+ * time-boundary factor (reading stated in the header). */
+double oracle_link_sign(const int N[4], const int x[4], int mu)
+{
+    int s = 0;
+    for (int nu = 0; nu < mu; ++nu) s += x[nu];
+#if ORACLE_MUTANT == 5
+    /* planted: eta_2 depends on x1 only (no longer anticommuting) */
+    if (mu == 2) s = x[1];
+#endif
+    double eta = (s & 1) ? -1.0 : 1.0;
+#if ORACLE_MUTANT != 4 /* mutant 4 planted: periodic instead of antiperiodic time */
+    if (mu == 3 && x[3] == N[3] - 1) eta = -eta;
+#endif
+    return eta;
+}
+
+/* ------------------------------------------------------------------------ */
+/* D_eo / D_oe: Eq. (diracblock) with the 1/2 normalisation                  */
+/* ------------------------------------------------------------------------ */
+
+/* out (sites of parity out_parity, [Vh][3]) = D restricted to that parity,
+ * acting on in (sites of the other parity, [Vh][3]).
+ * links: [4][V][3][3], U_mu(x)[row][col] at lexicographic index of x.      */
+void oracle_deo(const int N[4], int out_parity, const cplx *links,
+                const cplx *in, cplx *out)
+{
+    const long V = volume(N);
+#pragma omp parallel for schedule(static)
+    for (int x3 = 0; x3 < N[3]; ++x3)
+        for (int x2 = 0; x2 < N[2]; ++x2)
+            for (int x1 = 0; x1 < N[1]; ++x1)
+                for (int x0 = 0; x0 < N[0]; ++x0) {
+                    const int x[4] = {x0, x1, x2, x3};
+                    if (oracle_parity(x) != out_parity) continue;
+                    cplx acc[3] = {0, 0, 0};
+                    for (int mu = 0; mu < 4; ++mu) {
+                        int xp[4] = {x0, x1, x2, x3}, xm[4] = {x0, x1, x2, x3};
+                        xp[mu] = (x[mu] + 1) % N[mu];
+                        xm[mu] = (x[mu] - 1 + N[mu]) % N[mu];
+#if ORACLE_MUTANT == 10
+                        /* planted: forward and backward neighbours swapped in direction 1 */
+                        if (mu == 1) { int t = xp[1]; xp[1] = xm[1]; xm[1] = t; }
+#endif
+                        const cplx *Uf = links + ((long)mu * V + lex_index(N, x)) * 9;
+#if ORACLE_MUTANT == 2
+                        /* planted: backward hop uses the link at n, not n - mu */
+                        const cplx *Ub = links + ((long)mu * V + lex_index(N, x)) * 9;
+#else
+                        const cplx *Ub = links + ((long)mu * V + lex_index(N, xm)) * 9;
+#endif
+                        const double sf = oracle_link_sign(N, x, mu);
+                        const double sb = oracle_link_sign(N, xm, mu);
+                        const cplx *vf = in + oracle_idxh(N, xp) * 3;
+                        const cplx *vb = in + oracle_idxh(N, xm) * 3;
+                        for (int a = 0; a < 3; ++a)
+                            for (int b = 0; b < 3; ++b) {
+#if ORACLE_MUTANT == 7
+                                /* planted: forward link transposed */
+                                acc[a] += sf * Uf[b * 3 + a] * vf[b];
+#else
+                                acc[a] += sf * Uf[a * 3 + b] * vf[b];
+#endif
+#if ORACLE_MUTANT == 1
+                                /* planted: dagger dropped on the backward hop */
+                                acc[a] -= sb * Ub[a * 3 + b] * vb[b];
+#elif ORACLE_MUTANT == 3
+                                /* planted: backward hop added instead of subtracted */
+                                acc[a] += sb * conj(Ub[b * 3 + a]) * vb[b];
+#else
+                                acc[a] -= sb * conj(Ub[b * 3 + a]) * vb[b];
+#endif
+                            }
+                    }
+                    cplx *o = out + oracle_idxh(N, x) * 3;
+#if ORACLE_MUTANT == 6
+                    /* planted: the 1/2 normalisation is missing */
+                    for (int a = 0; a < 3; ++a) o[a] = acc[a];
+#else
+                    for (int a = 0; a < 3; ++a) o[a] = 0.5 * acc[a];
+#endif
+                }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Vector helpers on half-lattice fields (n = 3 * Vh complex numbers)        */
+/* ------------------------------------------------------------------------ */
+
+/* <a, b> = sum conj(a) b, accumulated serially in index order. */
+cplx oracle_dot(long n, const cplx *a, const cplx *b)
+{
+    cplx s = 0;
+    for (long i = 0; i < n; ++i) s += conj(a[i]) * b[i];
+    return s;
+}
+
+double oracle_norm2(long n, const cplx *a)
+{
+    double s = 0;
+    for (long i = 0; i < n; ++i) s += creal(a[i]) * creal(a[i]) + cimag(a[i]) * cimag(a[i]);
+    return s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Normal operator: Eq. (lineqeo) plus a shift                               */
+/* ------------------------------------------------------------------------ */
+
+/* out = (m^2 + sigma) in - D_eo D_oe in, in/out on even sites;
+ * tmp is an odd-site scratch field of the same size. */
+void oracle_apply_A(const int N[4], const cplx *links, double mass, double sigma,
+                    const cplx *in, cplx *out, cplx *tmp)
+{
+    const long n = volume(N) / 2 * 3;
+    oracle_deo(N, 1, links, in, tmp);   /* D_oe: even -> odd */
+    oracle_deo(N, 0, links, tmp, out);  /* D_eo: odd -> even */
+    const double a = mass * mass + sigma;
+#pragma omp parallel for schedule(static)
+    for (long i = 0; i < n; ++i) out[i] = a * in[i] - out[i];
+}
+
+/* ||(A + sigma) x - b|| / ||b|| in FP64. */
+double oracle_true_residual(const int N[4], const cplx *links, double mass,
+                            double sigma, const cplx *b, const cplx *x)
+{
+    const long n = volume(N) / 2 * 3;
+    cplx *ax = malloc(sizeof(cplx) * n), *tmp = malloc(sizeof(cplx) * n);
+    oracle_apply_A(N, links, mass, sigma, x, ax, tmp);
+    double rr = 0;
+    for (long i = 0; i < n; ++i) {
+        cplx d = ax[i] - b[i];
+        rr += creal(d) * creal(d) + cimag(d) * cimag(d);
+    }
+    double bb = oracle_norm2(n, b);
+    free(ax);
+    free(tmp);
+    return bb > 0 ? sqrt(rr / bb) : sqrt(rr);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Single-shift CG on (A + sigma) x = b, started from the given x            */
+/* ------------------------------------------------------------------------ */
+
+/* Plain conjugate gradient (the SPD solver named after Eq. (lineqeo)).
+ * Stops when ||r|| <= tol ||b|| with r the recursively updated residual.
+ * Returns the number of iterations, or -1 if max_iter was reached. */
+int oracle_cg(const int N[4], const cplx *links, double mass, double sigma,
+              const cplx *b, cplx *x, double tol, int max_iter)
+{
+    const long n = volume(N) / 2 * 3;
+    cplx *r = malloc(sizeof(cplx) * n), *p = malloc(sizeof(cplx) * n);
+    cplx *q = malloc(sizeof(cplx) * n), *tmp = malloc(sizeof(cplx) * n);
+    oracle_apply_A(N, links, mass, sigma, x, q, tmp);
+    for (long i = 0; i < n; ++i) { r[i] = b[i] - q[i]; p[i] = r[i]; }
+    const double bnorm = sqrt(oracle_norm2(n, b));
+    double rho = oracle_norm2(n, r);
+    int k = 0;
+    while (sqrt(rho) > tol * bnorm) {
+        if (k >= max_iter) { k = -1; break; }
+        oracle_apply_A(N, links, mass, sigma, p, q, tmp);
+        const double alpha = rho / creal(oracle_dot(n, p, q));
+        for (long i = 0; i < n; ++i) { x[i] += alpha * p[i]; r[i] -= alpha * q[i]; }
+        const double rho_new = oracle_norm2(n, r);
+        const double beta = rho_new / rho;
+        for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+        rho = rho_new;
+        ++k;
+    }
+    free(r); free(p); free(q); free(tmp);
+    return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multi-shift CG: Eq. (shlineq) on top of Eq. (lineqeo)                     */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Solves (A + sigma_i) x_i = b for i = 0..n_shift-1, with A = m^2 - D_eo D_oe.
+ *
+ * Base system: A0 = A + sigma_b with sigma_b = min_i sigma_i; relative shifts
+ * s_i = sigma_i - sigma_b >= 0.  Plain CG on A0 generates residuals r_k and
+ * search directions p_k with step alpha_k and beta_k.  Because the Krylov
+ * spaces of A0 and A0 + s_i coincide and both start from r_0 = b, the
+ * residual of shift i after k steps is collinear with r_k:
+ * r_k^i = zeta_k^i r_k.  Writing the CG three-term recurrence for both
+ * systems and matching coefficients gives (zeta_{-1} = zeta_0 = 1,
+ * alpha_{-1} = 1, beta_{-1} = 0)
+ *
+ *   zeta_{k+1} = zeta_k zeta_{k-1} alpha_{k-1} /
+ *                [ alpha_k beta_{k-1} (zeta_{k-1} - zeta_k)
+ *                  + zeta_{k-1} alpha_{k-1} (1 + s alpha_k) ]
+ *   alpha_k^i = alpha_k zeta_{k+1} / zeta_k
+ *   beta_k^i  = beta_k (zeta_{k+1} / zeta_k)^2
+ *   x^i_{k+1} = x^i_k + alpha_k^i p^i_k
+ *   p^i_{k+1} = zeta_{k+1} r_{k+1} + beta_k^i p^i_k
+ *
+ * For s = 0 these reduce to plain CG (zeta = 1).  Shift i stops updating
+ * once |zeta^i| ||r|| <= tol ||b||; the loop ends when every shift stopped.
+ * Afterwards the FP64 true residual of every shift is computed and a shift
+ * above tol is finished by oracle_cg from its current x_i.
+ *
+ * x: [n_shift][Vh][3].  iters_out[0] = base iterations, iters_out[1] =
+ * total refinement iterations; shift_iters[i] = iteration at which shift i
+ * stopped; true_resid[i] = final true residual.  Returns 0, -1 when
+ * max_iter was hit before all shifts stopped, -2 for n_shift outside 1..64.
+ */
+int oracle_mscg(const int N[4], const cplx *links, double mass,
+                const double *shifts, int n_shift, const cplx *b, cplx *x,
+                double tol, int max_iter, int *iters_out, int *shift_iters,
+                double *true_resid)
+{
+    const long n = volume(N) / 2 * 3;
+    if (n_shift < 1 || n_shift > 64) return -2;
+    int ib = 0;
+    for (int i = 1; i < n_shift; ++i)
+        if (shifts[i] < shifts[ib]) ib = i;
+    const double sigma_b = shifts[ib];
+
+    cplx *r = malloc(sizeof(cplx) * n), *p = malloc(sizeof(cplx) * n);
+    cplx *q = malloc(sizeof(cplx) * n), *tmp = malloc(sizeof(cplx) * n);
+    cplx *ps = malloc(sizeof(cplx) * n * n_shift);
+    double *zeta = malloc(sizeof(double) * n_shift);
+    double *zeta_prev = malloc(sizeof(double) * n_shift);
+    int *active = malloc(sizeof(int) * n_shift);
+
+    for (long i = 0; i < n; ++i) { r[i] = b[i]; p[i] = b[i]; }
+    for (int s = 0; s < n_shift; ++s) {
+        for (long i = 0; i < n; ++i) { ps[s * n + i] = b[i]; x[s * n + i] = 0; }
+        zeta[s] = zeta_prev[s] = 1.0;
+        active[s] = 1;
+        shift_iters[s] = 0;
+    }
+    const double bnorm = sqrt(oracle_norm2(n, b));
+    double rho = oracle_norm2(n, r);
+    double alpha_prev = 1.0, beta_prev = 0.0;
+    int k = 0, status = 0;
+    for (int s = 0; s < n_shift; ++s)
+        if (fabs(zeta[s]) * sqrt(rho) <= tol * bnorm) active[s] = 0;
+
+    for (;;) {
+        int n_active = 0;
+        for (int s = 0; s < n_shift; ++s) n_active += active[s];
+        if (n_active == 0) break;
+        if (k >= max_iter) { status = -1; break; }
+
+        /* q = A0 p, alpha = rho / <p, q> */
+        oracle_apply_A(N, links, mass, sigma_b, p, q, tmp);
+        const double alpha = rho / creal(oracle_dot(n, p, q));
+
+        /* shifted step lengths and solution updates (old p_i) */
+        double zeta_new[64], alpha_s[64];
+        for (int s = 0; s < n_shift; ++s) {
+            if (!active[s]) continue;
+            const double sh = shifts[s] - sigma_b;
+#if ORACLE_MUTANT == 8
+            /* planted: the beta term of the zeta recurrence is dropped */
+            const double den = zeta_prev[s] * alpha_prev * (1.0 + sh * alpha);
+#else
+            const double den = alpha * beta_prev * (zeta_prev[s] - zeta[s])
+                             + zeta_prev[s] * alpha_prev * (1.0 + sh * alpha);
+#endif
+            zeta_new[s] = zeta[s] * zeta_prev[s] * alpha_prev / den;
+#if ORACLE_MUTANT == 9
+            /* planted: ratio of zetas inverted in the shifted step */
+            alpha_s[s] = alpha * zeta[s] / zeta_new[s];
+#else
+            alpha_s[s] = alpha * zeta_new[s] / zeta[s];
+#endif
+            for (long i = 0; i < n; ++i) x[s * n + i] += alpha_s[s] * ps[s * n + i];
+        }
+
+        /* base residual and new direction */
+        for (long i = 0; i < n; ++i) r[i] -= alpha * q[i];
+        const double rho_new = oracle_norm2(n, r);
+        const double beta = rho_new / rho;
+        for (long i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
+
+        /* shifted directions */
+        for (int s = 0; s < n_shift; ++s) {
+            if (!active[s]) continue;
+            const double ratio = zeta_new[s] / zeta[s];
+            const double beta_s = beta * ratio * ratio;
+            for (long i = 0; i < n; ++i)
+                ps[s * n + i] = zeta_new[s] * r[i] + beta_s * ps[s * n + i];
+            zeta_prev[s] = zeta[s];
+            zeta[s] = zeta_new[s];
+        }
+        alpha_prev = alpha;
+        beta_prev = beta;
+        rho = rho_new;
+        ++k;
+        for (int s = 0; s < n_shift; ++s)
+            if (active[s] && fabs(zeta[s]) * sqrt(rho) <= tol * bnorm) {
+                active[s] = 0;
+                shift_iters[s] = k;
+            }
+    }
+    iters_out[0] = k;
+    iters_out[1] = 0;
+
+    /* true residual per shift; finish any shift above tol with plain CG */
+    for (int s = 0; s < n_shift; ++s) {
+        true_resid[s] = oracle_true_residual(N, links, mass, shifts[s], b, x + s * n);
+        if (true_resid[s] > tol) {
+            int it = oracle_cg(N, links, mass, shifts[s], b, x + s * n, tol, max_iter);
+            if (it < 0) status = -1; else iters_out[1] += it;
+            true_resid[s] = oracle_true_residual(N, links, mass, shifts[s], b, x + s * n);
+        }
+    }
+    free(r); free(p); free(q); free(tmp); free(ps);
+    free(zeta); free(zeta_prev); free(active);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Timing support                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* Number of threads the parallel loops use (1 when built without OpenMP). */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
+int oracle_mutant(void) { return ORACLE_MUTANT; }

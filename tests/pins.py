@@ -1,0 +1,264 @@
+"""Pins for the CPU oracle: checks against what the paper and the mathematics
+fix, written without re-using the oracle's own formulas.
+
+Each check returns (ok: bool, detail: str) so that the same battery can be run
+against the default oracle (tests/test_oracle_pins.py) and against builds
+with a planted mistake (tests/test_oracle_mutants.py).
+
+Sources of truth:
+* Eq. (lexicographic_eo): brute-force rank of a site among the sites of its
+  parity in lexicographic order;
+* Eq. (diracblock): D_oe^dag = -D_eo (anti-hermiticity);
+* gauge covariance of the covariant hops (Sec. 2: links transform as
+  U_mu(n) -> Omega(n) U_mu(n) Omega(n+mu)^dag, quark fields as psi -> Omega psi);
+* free field U = 1: the even-site plane waves are eigenvectors of
+  m^2 - D_eo D_oe with eigenvalue m^2 + sum_mu sin^2 p_mu (antiperiodic
+  momenta in time);
+* Eq. (lineqeo) / Eq. (shlineq): the shifted systems' solutions from LAPACK
+  (numpy.linalg.solve / eigvalsh) on small lattices.
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+from paper_1701_00426_gb300 import inputs
+
+MASS = 0.1
+
+
+def sites(dims):
+    """All coordinates in lexicographic order (x0 fastest)."""
+    for x3, x2, x1, x0 in itertools.product(*(range(d) for d in dims[::-1])):
+        yield (x0, x1, x2, x3)
+
+
+def inner(a, b) -> complex:
+    return complex(np.vdot(a.ravel(), b.ravel()))
+
+
+def rel(a, b) -> float:
+    den = max(np.linalg.norm(b), 1e-300)
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / den)
+
+
+# --------------------------------------------------------------- geometry
+def pin_geometry(orc, dims) -> tuple[bool, str]:
+    rank = [0, 0]
+    for n, x in enumerate(sites(dims)):
+        if orc.lex(dims, x) != n:
+            return False, f"lex of {x} is {orc.lex(dims, x)}, expected {n}"
+        p = sum(x) % 2
+        if orc.parity(x) != p:
+            return False, f"parity of {x}"
+        if orc.idxh(dims, x) != rank[p]:
+            return False, f"idxh of {x} is {orc.idxh(dims, x)}, expected rank {rank[p]}"
+        rank[p] += 1
+    Vh = int(np.prod(dims)) // 2
+    return (rank == [Vh, Vh]), f"parity counts {rank}"
+
+
+# ------------------------------------------------------------------ phases
+def pin_phase_anticommutation(orc, dims) -> tuple[bool, str]:
+    """s_mu(x) s_nu(x+mu) = - s_nu(x) s_mu(x+nu) for every x and mu != nu (the
+    property that makes the free D^2 diagonal; it survives the periodic wrap
+    because every side is even, and the time-boundary sign cancels), and the
+    time-link signs multiply to -1 around every time line (antiperiodic)."""
+    for x in sites(dims):
+        for mu in range(4):
+            for nu in range(4):
+                if mu == nu:
+                    continue
+                xm = list(x); xm[mu] = (xm[mu] + 1) % dims[mu]
+                xn = list(x); xn[nu] = (xn[nu] + 1) % dims[nu]
+                lhs = orc.link_sign(dims, x, mu) * orc.link_sign(dims, xm, nu)
+                rhs = orc.link_sign(dims, x, nu) * orc.link_sign(dims, xn, mu)
+                if lhs != -rhs:
+                    return False, f"signs commute at {x} mu={mu} nu={nu}"
+    for x0, x1, x2 in ((0, 0, 0), (1, 0, 0), (1, 1, 1), (0, 1, 0)):
+        prod = 1.0
+        for t in range(dims[3]):
+            prod *= orc.link_sign(dims, (x0, x1, x2, t), 3)
+        if prod != -1.0:
+            return False, f"time line ({x0},{x1},{x2}) sign product {prod}"
+    return True, "ok"
+
+
+# -------------------------------------------------------- anti-hermiticity
+def pin_antihermitian(orc, dims, seed=11) -> tuple[bool, str]:
+    U = inputs.random_links(dims, seed=seed)
+    Vh = int(np.prod(dims)) // 2
+    rng = np.random.default_rng(seed + 1)
+    x = rng.standard_normal((Vh, 3)) + 1j * rng.standard_normal((Vh, 3))
+    y = rng.standard_normal((Vh, 3)) + 1j * rng.standard_normal((Vh, 3))
+    Dx = orc.deo(dims, 0, U, x)   # D_eo x_odd
+    Dy = orc.deo(dims, 1, U, y)   # D_oe y_even
+    lhs = inner(y, Dx)
+    rhs = -inner(Dy, x)
+    scale = np.linalg.norm(y) * np.linalg.norm(Dx)
+    err = abs(lhs - rhs) / scale
+    return err <= 1e-14, f"anti-hermiticity defect {err:.2e}"
+
+
+# ---------------------------------------------------------- gauge covariance
+def pin_gauge_covariance(orc, dims, seed=21) -> tuple[bool, str]:
+    U = inputs.random_links(dims, seed=seed)
+    V = int(np.prod(dims))
+    Vh = V // 2
+    Om = inputs.random_gauge_transform(dims, seed=seed + 1)
+    # site tables by plain enumeration (independent of the oracle's helpers)
+    coords = list(sites(dims))
+    lex_of = {x: n for n, x in enumerate(coords)}
+    half = {0: [], 1: []}
+    for x in coords:
+        half[sum(x) % 2].append(x)
+    Up = np.empty_like(U)
+    for mu in range(4):
+        for n, x in enumerate(coords):
+            xp = list(x); xp[mu] = (xp[mu] + 1) % dims[mu]
+            Up[mu, n] = Om[n] @ U[mu, n] @ Om[lex_of[tuple(xp)]].conj().T
+    rng = np.random.default_rng(seed + 2)
+    ok = True
+    worst = 0.0
+    for out_par in (0, 1):
+        in_par = 1 - out_par
+        psi = rng.standard_normal((Vh, 3)) + 1j * rng.standard_normal((Vh, 3))
+        psip = np.stack([Om[lex_of[x]] @ psi[i] for i, x in enumerate(half[in_par])])
+        lhs = orc.deo(dims, out_par, Up, psip)
+        D = orc.deo(dims, out_par, U, psi)
+        rhs = np.stack([Om[lex_of[x]] @ D[i] for i, x in enumerate(half[out_par])])
+        e = rel(lhs, rhs)
+        worst = max(worst, e)
+        ok &= e <= 1e-14
+    return ok, f"covariance defect {worst:.2e}"
+
+
+# ------------------------------------------------------------- free field
+def free_eigenvalue(dims, k, mass=MASS) -> float:
+    p = [2 * np.pi * k[m] / dims[m] for m in range(3)]
+    p.append(2 * np.pi * (k[3] + 0.5) / dims[3])
+    return mass * mass + sum(np.sin(q) ** 2 for q in p)
+
+
+def plane_wave_even(dims, k, chi) -> np.ndarray:
+    """e^{i p.x} chi on the even sites, listed by rank in lexicographic order."""
+    p = [2 * np.pi * k[m] / dims[m] for m in range(3)]
+    p.append(2 * np.pi * (k[3] + 0.5) / dims[3])
+    rows = []
+    for x in sites(dims):
+        if sum(x) % 2 == 0:
+            rows.append(np.exp(1j * sum(p[m] * x[m] for m in range(4))) * chi)
+    return np.array(rows)
+
+
+def pin_free_plane_waves(orc, dims, ks, mass=MASS) -> tuple[bool, str]:
+    U = inputs.unit_links(dims)
+    chi = np.array([0.3 + 0.1j, -0.7j, 1.1])
+    worst = 0.0
+    for k in ks:
+        psi = plane_wave_even(dims, k, chi)
+        lam = free_eigenvalue(dims, k, mass)
+        out = orc.apply_A(dims, U, mass, 0.0, psi)
+        worst = max(worst, rel(out, lam * psi))
+    return worst <= 1e-13, f"plane-wave defect {worst:.2e}"
+
+
+def dense_A(orc, dims, U, mass, sigma=0.0) -> np.ndarray:
+    """A + sigma assembled column by column from the oracle's operator."""
+    Vh = int(np.prod(dims)) // 2
+    n = 3 * Vh
+    A = np.empty((n, n), np.complex128)
+    e = np.zeros(n, np.complex128)
+    for j in range(n):
+        e[:] = 0
+        e[j] = 1
+        A[:, j] = orc.apply_A(dims, U, mass, sigma, e.reshape(Vh, 3)).ravel()
+    return A
+
+
+def pin_free_spectrum(orc, dims, mass=MASS) -> tuple[bool, str]:
+    """Whole spectrum of the free even/odd operator vs the closed form."""
+    U = inputs.unit_links(dims)
+    A = dense_A(orc, dims, U, mass)
+    ev = np.linalg.eigvalsh(A)
+    lam = []
+    for k in itertools.product(*(range(d) for d in dims)):
+        lam.append(free_eigenvalue(dims, k, mass))
+    lam = np.sort(np.array(lam))
+    # each even-site plane wave is shared by p and p + (pi,pi,pi,pi); 3 colours
+    expect = np.sort(np.repeat(lam[::2], 3))
+    err = float(np.max(np.abs(ev - expect)))
+    return err <= 1e-12, f"free spectrum max defect {err:.2e}"
+
+
+def pin_two_site(orc, mass=MASS) -> tuple[bool, str]:
+    """On 2^4 (where n+mu = n-mu) the free operator is (m^2 + 1) I."""
+    dims = (2, 2, 2, 2)
+    U = inputs.unit_links(dims)
+    rng = np.random.default_rng(5)
+    v = rng.standard_normal((8, 3)) + 1j * rng.standard_normal((8, 3))
+    out = orc.apply_A(dims, U, mass, 0.0, v)
+    e = rel(out, (mass * mass + 1.0) * v)
+    return e <= 1e-15, f"2^4 free defect {e:.2e}"
+
+
+def pin_hermitian_positive(orc, dims, mass=MASS) -> tuple[bool, str]:
+    U = inputs.random_links(dims, seed=33)
+    A = dense_A(orc, dims, U, mass)
+    herm = float(np.max(np.abs(A - A.conj().T)))
+    ev = np.linalg.eigvalsh(A)
+    ok = herm <= 1e-14 and ev[0] >= mass * mass * (1 - 1e-10)
+    return ok, f"hermiticity {herm:.2e}, lowest eigenvalue {ev[0]:.3e}"
+
+
+# ---------------------------------------------------------------- solvers
+def pin_mscg_vs_lapack(orc, dims, shifts, mass=MASS, tol=1e-10) -> tuple[bool, str]:
+    U = inputs.random_links(dims, seed=44)
+    Vh = int(np.prod(dims)) // 2
+    b = inputs.gaussian_field(dims, k=3)
+    A = dense_A(orc, dims, U, mass)
+    x, info = orc.mscg(dims, U, mass, shifts, b, tol)
+    if info["status"] != 0:
+        return False, f"mscg status {info['status']}"
+    # the shifted recurrences alone must reach tol: the plain-CG clean-up
+    # after the true-residual check exists for rounding drift, and at this
+    # size and tolerance rounding never needs it
+    if info["refine_iters"] != 0:
+        return False, f"shifted recurrences needed {info['refine_iters']} refinement iterations"
+    ev = np.linalg.eigvalsh(A)
+    worst = 0.0
+    for i, s in enumerate(shifts):
+        xs = np.linalg.solve(A + s * np.eye(3 * Vh), b.ravel())
+        kappa = (ev[-1] + s) / (ev[0] + s)
+        e = rel(x[i].ravel(), xs) / (kappa * tol)
+        worst = max(worst, e)
+        r = np.linalg.norm((A + s * np.eye(3 * Vh)) @ x[i].ravel() - b.ravel()) / np.linalg.norm(b)
+        if r > tol:
+            return False, f"shift {s}: LAPACK-checked residual {r:.2e} > tol"
+    return worst <= 1.0, f"max error / (kappa tol) = {worst:.3f}"
+
+
+def pin_free_solve(orc, dims, shifts, k, mass=MASS, tol=1e-12) -> tuple[bool, str]:
+    U = inputs.unit_links(dims)
+    chi = np.array([1.0, 0.5j, -0.25])
+    b = plane_wave_even(dims, k, chi)
+    lam = free_eigenvalue(dims, k, mass)
+    x, info = orc.mscg(dims, U, mass, shifts, b, tol)
+    worst = 0.0
+    for i, s in enumerate(shifts):
+        worst = max(worst, rel(x[i], b / (lam + s)))
+    return worst <= 1e-10, f"free solve defect {worst:.2e}"
+
+
+BATTERY = [
+    ("geometry 4x6x8x10", lambda o: pin_geometry(o, (4, 6, 8, 10))),
+    ("phase anticommutation 4x6x8x10", lambda o: pin_phase_anticommutation(o, (4, 6, 8, 10))),
+    ("anti-hermiticity 4x6x8x10", lambda o: pin_antihermitian(o, (4, 6, 8, 10))),
+    ("gauge covariance 4x4x4x6", lambda o: pin_gauge_covariance(o, (4, 4, 4, 6))),
+    ("free plane waves 4x6x8x10", lambda o: pin_free_plane_waves(
+        o, (4, 6, 8, 10), [(0, 0, 0, 0), (1, 2, 3, 4), (3, 1, 5, 9), (2, 5, 7, 2)])),
+    ("free 2^4", pin_two_site),
+    ("mscg vs LAPACK 4^4", lambda o: pin_mscg_vs_lapack(o, (4, 4, 4, 4), [1e-3, 0.05, 1.0, 30.0])),
+    ("free solve 4x4x6x8", lambda o: pin_free_solve(o, (4, 4, 6, 8), [0.0, 0.3, 7.0], (1, 3, 2, 5))),
+]

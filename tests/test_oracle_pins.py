@@ -1,0 +1,137 @@
+"""The CPU oracle against what the paper and the mathematics fix (no GPU)."""
+import numpy as np
+import pytest
+
+import pins
+from paper_1701_00426_gb300 import inputs
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4), (4, 6, 8, 10)])
+def test_geometry_matches_bruteforce_rank(orc, dims):
+    ok, msg = pins.pin_geometry(orc, dims)
+    assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 6, 8, 10)])
+def test_phases_anticommute_and_time_is_antiperiodic(orc, dims):
+    ok, msg = pins.pin_phase_anticommutation(orc, dims)
+    assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4), (4, 6, 8, 10)])
+def test_deo_antihermitian(orc, dims):
+    """Eq. (diracblock): D_oe^dag = -D_eo."""
+    ok, msg = pins.pin_antihermitian(orc, dims)
+    assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 6)])
+def test_deo_gauge_covariant(orc, dims):
+    ok, msg = pins.pin_gauge_covariance(orc, dims)
+    assert ok, msg
+
+
+def test_free_plane_waves_are_eigenvectors(orc):
+    ks = [(0, 0, 0, 0), (1, 2, 3, 4), (3, 1, 5, 9), (2, 5, 7, 2), (1, 0, 0, 0), (0, 0, 0, 3)]
+    ok, msg = pins.pin_free_plane_waves(orc, (4, 6, 8, 10), ks)
+    assert ok, msg
+
+
+def test_free_two_site_lattice(orc):
+    ok, msg = pins.pin_two_site(orc)
+    assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4), (2, 4, 2, 6)])
+def test_free_spectrum_closed_form(orc, dims):
+    ok, msg = pins.pin_free_spectrum(orc, dims)
+    assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4)])
+def test_A_hermitian_positive(orc, dims):
+    """Eq. (lineqeo): m^2 - D_eo D_oe is Hermitian with spectrum >= m^2."""
+    ok, msg = pins.pin_hermitian_positive(orc, dims)
+    assert ok, msg
+
+
+def test_mscg_matches_lapack_2444(orc):
+    ok, msg = pins.pin_mscg_vs_lapack(orc, (2, 2, 2, 2), [0.0, 1e-3, 1.0])
+    assert ok, msg
+
+
+def test_mscg_matches_lapack_4444(orc):
+    ok, msg = pins.pin_mscg_vs_lapack(orc, (4, 4, 4, 4), [1e-5, 1e-3, 0.05, 1.0, 30.0])
+    assert ok, msg
+
+
+def test_mscg_free_field_closed_form(orc):
+    ok, msg = pins.pin_free_solve(orc, (4, 4, 6, 8), [0.0, 0.3, 7.0], (1, 3, 2, 5))
+    assert ok, msg
+
+
+def test_single_shift_mscg_is_plain_cg(orc):
+    """With one shift the recurrences collapse to CG (zeta = 1 exactly)."""
+    dims = (4, 4, 4, 4)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims)
+    x1, info = orc.mscg(dims, U, 0.1, [0.02], b, 1e-10)
+    x2, it = orc.cg(dims, U, 0.1, 0.02, b, 1e-10)
+    assert info["iters"] == it
+    assert np.array_equal(x1[0], x2)
+
+
+def test_mscg_equals_independent_cgs(orc):
+    dims = (4, 4, 4, 6)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=1)
+    shifts = inputs.log_shifts(6, 1e-4, 10.0)
+    tol = 1e-10
+    x, info = orc.mscg(dims, U, 0.05, shifts, b, tol)
+    assert info["status"] == 0
+    for i, s in enumerate(shifts):
+        xc, it = orc.cg(dims, U, 0.05, s, b, tol)
+        assert it > 0
+        kappa = (0.05 ** 2 + s + 16) / (0.05 ** 2 + s)
+        assert pins.rel(x[i], xc) <= 2 * kappa * tol
+        assert info["true_resid"][i] <= tol
+
+
+def test_mscg_shift_order_irrelevant(orc):
+    """Shifts may come in any order; each x_i belongs to shifts[i]."""
+    dims = (4, 4, 4, 4)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=2)
+    sh = [1.0, 1e-3, 0.1]
+    x, info = orc.mscg(dims, U, 0.1, sh, b, 1e-11)
+    for i, s in enumerate(sh):
+        assert orc.true_residual(dims, U, 0.1, s, b, x[i]) <= 1e-11
+
+
+def test_zero_source_gives_zero(orc):
+    dims = (2, 2, 2, 4)
+    U = inputs.random_links(dims)
+    b = np.zeros((16, 3), np.complex128)
+    x, info = orc.mscg(dims, U, 0.1, [0.0, 1.0], b, 1e-10)
+    assert info["iters"] == 0 and not np.any(x)
+
+
+def test_oracle_rejects_bad_shift_count(orc):
+    dims = (2, 2, 2, 2)
+    U = inputs.unit_links(dims)
+    b = np.ones((8, 3), np.complex128)
+    _, info = orc.mscg(dims, U, 0.1, np.linspace(0, 1, 65), b, 1e-8)
+    assert info["status"] == -2
+
+
+def test_inputs_are_su3_and_seeded():
+    dims = (4, 4, 4, 4)
+    U = inputs.random_links(dims)
+    U2 = inputs.random_links(dims)
+    assert np.array_equal(U, U2)
+    m = U.reshape(-1, 3, 3)
+    eye = np.einsum("nij,nkj->nik", m, m.conj())
+    assert np.max(np.abs(eye - np.eye(3))) < 1e-14
+    assert np.max(np.abs(np.linalg.det(m) - 1)) < 1e-14
+    b = inputs.gaussian_field(dims, k=0)
+    assert b.shape == (128, 3) and abs(np.mean(np.abs(b) ** 2) - 2.0) < 0.3
