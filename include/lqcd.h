@@ -1,0 +1,260 @@
+/*
+ * lqcd.h -- C ABI of the GB300 (sm_103a) staggered-fermion hot path.
+ *
+ * Operations (arXiv:1701.00426, Bonati et al.):
+ *   D_eo / D_oe   the even/odd blocks of the staggered operator,
+ *                 M = m I + [[0, D_oe], [D_eo, 0]], D_oe^dag = -D_eo
+ *                 (Sec. 2.2, Eq. diracblock);
+ *   A             the even-site normal operator m^2 - D_eo D_oe
+ *                 (Sec. 2.2, Eq. lineqeo);
+ *   multi-shift   (A + sigma_i) x_i = b for all poles sigma_i at once, one
+ *                 operator application per iteration (Sec. 2.2, Eq. shlineq).
+ *
+ * Conventions shared by every call:
+ *   - Lattice sides N0..N3 are even and >= 2 (Sec. 4.1: all sides even).
+ *     Time is direction 3.
+ *   - Operator normalisation, staggered phases and boundary:
+ *       (D psi)(n) = 1/2 sum_mu [ s_mu(n) U_mu(n) psi(n+mu)
+ *                                 - s_mu(n-mu) U_mu(n-mu)^dag psi(n-mu) ],
+ *       s_mu(n) = eta_mu(n) * (-1 if mu == 3 and n3 == N3-1 else 1),
+ *       eta_0 = 1, eta_mu(n) = (-1)^(n0 + ... + n_{mu-1}).
+ *     The phases are computed from coordinates; links are stored raw.
+ *   - Host gauge field ("canonical links"): complex128 interleaved (re, im),
+ *     [4][V][3][3], U_mu(x)[row][col] at lexicographic index
+ *     lex = x0 + N0 (x1 + N1 (x2 + N2 x3)).  Links must be SU(3) (unitary,
+ *     det 1) when 12-real storage is used; every entry must satisfy
+ *     |re|, |im| < 2^60.
+ *   - Host half-lattice field ("canonical spinor"): complex128 interleaved,
+ *     [Vh][3] (Vh = V/2) on the sites of one parity, site order given by the
+ *     half index idxh = lex / 2 (Sec. 4.1, Eq. lexicographic_eo).
+ *   - Device half-lattice field ("device spinor"): the three colour
+ *     components stored as three consecutive arrays (structure of arrays,
+ *     like the paper's vec3_soa): element (idxh, c) at offset c*Vh + idxh.
+ *     The element type is complex128 (double2) for FP64 calls and complex64
+ *     (float2) for FP32 / FP16 calls.  Device buffers are allocated and owned
+ *     by the caller and must stay valid until the call's stream has finished.
+ *   - Host buffers are always owned by the caller; the library copies.
+ *   - Every call returns an lqcd_status; nothing throws across this ABI.  On
+ *     failure lqcd_last_error() describes the cause (thread-local string).
+ *   - A context is not thread-safe: one thread at a time per context.
+ */
+#ifndef LQCD_H
+#define LQCD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lqcd_status {
+    LQCD_OK = 0,
+    LQCD_EINVAL = -1,     /* bad argument (sizes, pointers, odd sides, ...) */
+    LQCD_ENOMEM = -2,     /* device or host allocation failed, or over budget */
+    LQCD_ENOCONV = -3,    /* max_iter reached; best x and info still written */
+    LQCD_ENAN = -4,       /* NaN/Inf met in a reduction */
+    LQCD_EBUSY = -5,      /* server queue full */
+    LQCD_ENOTREADY = -6,  /* request not finished yet */
+    LQCD_ETIMEOUT = -7,   /* a bounded device wait gave up */
+    LQCD_ECUDA = -8,      /* CUDA runtime error */
+    LQCD_ESTATE = -9      /* call out of order (e.g. no links uploaded) */
+} lqcd_status;
+
+/* Arithmetic of a D_eo application or of a solver's inner iterations. */
+typedef enum lqcd_prec {
+    LQCD_PREC_FP64 = 0,         /* FP64 storage; products/sums in double-float
+                                   on the FP32 pipes, result within 1e-13 */
+    LQCD_PREC_FP32 = 1,         /* FP32 links and spinors, FP32 arithmetic */
+    LQCD_PREC_FP16 = 2,         /* FP16 links, FP32 spinors and arithmetic */
+    LQCD_PREC_FP64_NATIVE = 3   /* IEEE FP64 storage and native DFMA */
+} lqcd_prec;
+
+typedef struct lqcd_ctx lqcd_ctx;
+
+/* Solver options. */
+typedef struct lqcd_opts {
+    int prec;              /* lqcd_prec of the inner iterations (default FP64) */
+    int recon;             /* link storage for FP32/FP16 hops: 18 or 12 reals
+                              (12: third row rebuilt as conj(r0 x r1), Sec. 2.3) */
+    double delta_reliable; /* mixed precision: reliable update when the low-
+                              precision residual falls below delta times the
+                              residual at the last update (default 0.1) */
+    int max_iter;          /* iteration cap per solve (default 20000) */
+    int check_every;       /* iterations between host convergence checks (default 32) */
+} lqcd_opts;
+
+#define LQCD_MAX_SHIFTS 32
+
+/* Per-solve report. */
+typedef struct lqcd_solve_info {
+    int iters;                        /* iterations of the (outer) solve */
+    int n_shift;
+    int reliable_updates;             /* mixed precision: FP64 residual refreshes */
+    int refine_iters;                 /* iterations spent in per-shift refinement */
+    int shift_iters[LQCD_MAX_SHIFTS]; /* iteration at which each shift stopped */
+    double true_resid[LQCD_MAX_SHIFTS]; /* ||(A+sigma_i) x_i - b|| / ||b|| in FP64 */
+    double secs;                      /* wall time of the call */
+    double bytes_moved;               /* algorithmic device bytes of the solve */
+    int status;                       /* lqcd_status of the solve */
+} lqcd_solve_info;
+
+/* Fill *opts with the defaults listed above. */
+void lqcd_default_opts(lqcd_opts *opts);
+
+/* Last error message of the calling thread ("" if none). */
+const char *lqcd_last_error(void);
+
+/* ABI version (major*10000 + minor*100 + patch). */
+int lqcd_version(void);
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context for an N0 x N1 x N2 x N3 lattice on the current CUDA
+ * device.  dims: 4 even sides >= 2 (Sec. 4.1); opts may be NULL (defaults).
+ * The context owns its CUDA stream and every device allocation it makes.
+ * Returns LQCD_EINVAL for odd/small sides, LQCD_ECUDA / LQCD_ENOMEM on CUDA
+ * failures. */
+int lqcd_create(const int dims[4], const lqcd_opts *opts, lqcd_ctx **ctx);
+
+/* Free every device and host resource of ctx (NULL is ignored). */
+void lqcd_destroy(lqcd_ctx *ctx);
+
+/* Replace the solver options of ctx (validated; LQCD_EINVAL if invalid). */
+int lqcd_set_opts(lqcd_ctx *ctx, const lqcd_opts *opts);
+
+/* Device bytes held by ctx (links, workspaces). */
+size_t lqcd_device_bytes(const lqcd_ctx *ctx);
+
+/* ------------------------------------------------------------------ links */
+
+/* Upload a gauge field in the canonical host layout (n_doubles must equal
+ * 4*V*18).  The library copies it and derives every device storage format
+ * (FP64 18-real, FP32 18/12-real, FP16 12-real) on the device; host and
+ * device copies of the stored links only move at this call, as in the
+ * paper's update-device step (Sec. 4.1).  Synchronous.  LQCD_EINVAL for a
+ * wrong size or an entry out of range. */
+int lqcd_links_upload(lqcd_ctx *ctx, const double *links, size_t n_doubles);
+
+/* Copy the FP64 links back to the host in the canonical layout. */
+int lqcd_links_download(lqcd_ctx *ctx, double *links, size_t n_doubles);
+
+/* ------------------------------------------------------------------- D_eo */
+
+/* out = D_eo in (out_parity 0: odd input, even output) or out = D_oe in
+ * (out_parity 1: even input, odd output), Eq. (diracblock), in FP64.
+ * where = 0: in/out are host canonical spinors ([Vh][3] complex128);
+ *            the call is synchronous.
+ * where = 1: in/out are device spinors (complex128 structure of arrays);
+ *            the call is asynchronous on `stream` (cudaStream_t, NULL = the
+ *            context's stream).
+ * in and out must not overlap.  LQCD_ESTATE before lqcd_links_upload. */
+int lqcd_deo_apply(lqcd_ctx *ctx, int out_parity, const void *in, void *out,
+                   int where, void *stream);
+
+/* Same operator in a chosen arithmetic on device spinors (asynchronous):
+ *   prec LQCD_PREC_FP64, LQCD_PREC_FP64_NATIVE: complex128 spinors, recon 18;
+ *   prec LQCD_PREC_FP32: complex64 spinors, recon 18 or 12;
+ *   prec LQCD_PREC_FP16: complex64 spinors, FP16 links, recon 12. */
+int lqcd_deo_apply_ex(lqcd_ctx *ctx, int out_parity, int prec, int recon,
+                      const void *in, void *out, void *stream);
+
+/* Multi-right-hand-side D_eo/D_oe in FP32: each link is loaded once for all
+ * n_rhs (1..16) fields.  Device layout of in/out: complex64 [3][Vh][n_rhs]
+ * (colour-major, then site, right-hand side fastest).  recon 18 or 12.
+ * Asynchronous on `stream`. */
+int lqcd_deo_apply_mrhs(lqcd_ctx *ctx, int out_parity, int n_rhs, int recon,
+                        const void *in, void *out, void *stream);
+
+/* ----------------------------------------------------------------- solver */
+
+/* Multi-shift CG for (A + shifts[i]) x_i = b, A = m^2 - D_eo D_oe on even
+ * sites (Eqs. lineqeo, shlineq).  b: host canonical spinor ([Vh][3]
+ * complex128); x: host array [n_shift][Vh][3] complex128 written by the
+ * call.  shifts >= 0 in any order, 1 <= n_shift <= LQCD_MAX_SHIFTS;
+ * tol: target of the FP64 true residual ||(A+sigma_i)x_i - b||/||b|| for
+ * every shift (> 0).  The arithmetic of the inner iterations follows the
+ * context's opts.prec; the true residual and the solution are always FP64.
+ * info may be NULL.  Synchronous.  LQCD_ENOCONV when max_iter is reached
+ * (x and info still hold the best result). */
+int lqcd_mscg_solve(lqcd_ctx *ctx, double mass, const double *shifts, int n_shift,
+                    double tol, const double *b, double *x, lqcd_solve_info *info);
+
+/* Same on device spinors: b is a complex128 device spinor, x a device array
+ * of n_shift complex128 device spinors (shift-major).  Runs on `stream`
+ * (NULL = context stream) and returns when the solve has finished. */
+int lqcd_mscg_solve_dev(lqcd_ctx *ctx, double mass, const double *shifts, int n_shift,
+                        double tol, const void *b, void *x, lqcd_solve_info *info,
+                        void *stream);
+
+/* Batched single-shift CG for n_rhs sources sharing the gauge field:
+ * (A + sigma) x_k = b_k, k < n_rhs (1..16).  Inner iterations use the FP32
+ * multi-right-hand-side D_eo (each link loaded once per application for all
+ * sources) with FP64 reliable updates; the solution and the true residual are
+ * FP64.  b: host [n_rhs][Vh][3] complex128, x: same shape.  info: array of
+ * n_rhs reports (or NULL).  Synchronous. */
+int lqcd_cg_solve_mrhs(lqcd_ctx *ctx, double mass, double sigma, int n_rhs, double tol,
+                       const double *b, double *x, lqcd_solve_info *info);
+
+/* Packed multi-lattice solve: one multi-shift solve per context, all
+ * contexts (different lattice sizes allowed) advanced together, every
+ * kernel of an iteration launched once over a work list spanning all
+ * lattices.  Arguments are arrays of length n (one entry per context; x[i]
+ * is the host output of context i).  Each result is identical to the one
+ * the context would get alone.  Synchronous. */
+int lqcd_mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass,
+                           const double *const *shifts, const int *n_shift,
+                           const double *tol, const double *const *b,
+                           double *const *x, lqcd_solve_info *info);
+
+/* ----------------------------------------------------------------- serving */
+
+typedef struct lqcd_server lqcd_server;
+
+/* Server statistics (latencies in seconds, measured submit -> finished). */
+typedef struct lqcd_serve_stats {
+    uint64_t submitted, completed, rejected;
+    int active_slots, queued;
+    size_t hbm_in_use, hbm_budget;
+    double p50_latency, p99_latency, mean_latency;
+    double solves_per_sec;   /* completed / (last completion - first submit) */
+    uint64_t ticks;          /* packed iteration launches issued */
+} lqcd_serve_stats;
+
+/* Create a continuous-batching solve server on the current device.
+ * hbm_budget_bytes caps the device memory of resident fields plus active
+ * requests; max_slots caps concurrently active requests (1..64); max_queue
+ * caps requests waiting for admission.  A scheduler thread owned by the
+ * server admits requests when slots and memory free up and advances every
+ * active request by one iteration per packed launch. */
+int lqcd_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue,
+                      lqcd_server **srv);
+
+/* Register a resident gauge field (canonical host links, copied).
+ * *field_id receives its handle.  LQCD_ENOMEM if it does not fit. */
+int lqcd_serve_register_field(lqcd_server *srv, const int dims[4], const double *links,
+                              size_t n_doubles, int *field_id);
+
+/* Queue one multi-shift solve on a registered field (b: host canonical
+ * spinor, copied at submit).  *ticket identifies it.  LQCD_EBUSY when the
+ * queue is full; LQCD_ENOMEM if the request can never fit the budget. */
+int lqcd_serve_submit(lqcd_server *srv, int field_id, double mass, const double *shifts,
+                      int n_shift, double tol, const double *b, uint64_t *ticket);
+
+/* LQCD_ENOTREADY until the request has finished; then copies x
+ * ([n_shift][Vh][3] complex128) and info, and forgets the ticket. */
+int lqcd_serve_poll(lqcd_server *srv, uint64_t ticket, double *x, lqcd_solve_info *info);
+
+/* Block until every submitted request has finished (timeout_s <= 0: no
+ * limit); LQCD_ETIMEOUT when the limit passes first. */
+int lqcd_serve_drain(lqcd_server *srv, double timeout_s);
+
+int lqcd_serve_stats_get(lqcd_server *srv, lqcd_serve_stats *stats);
+
+/* Stop the scheduler, free every resource.  Unpolled results are dropped. */
+void lqcd_serve_destroy(lqcd_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQCD_H */

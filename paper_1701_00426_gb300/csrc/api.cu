@@ -1,0 +1,249 @@
+// api.cu -- the extern "C" entry points declared in include/lqcd.h:
+// argument validation, context life cycle, error reporting; the work is
+// done by deo.cu, solver.cu, mrhs.cu and serve.cu.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "internal.h"
+
+namespace lqcd {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int fail(int status, const std::string &msg)
+{
+    g_err = msg;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return e == cudaErrorMemoryAllocation ? LQCD_ENOMEM : LQCD_ECUDA;
+}
+
+int DevBuf::ensure(size_t n)
+{
+    if (n <= bytes && ptr) return LQCD_OK;
+    release();
+    if (n == 0) return LQCD_OK;
+    cudaError_t e = cudaMalloc(&ptr, n);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        cudaGetLastError();
+        return fail(LQCD_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed");
+    }
+    bytes = n;
+    return LQCD_OK;
+}
+
+void DevBuf::release()
+{
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+size_t ctx_device_bytes(const lqcd_ctx *c)
+{
+    const DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->io_a, &c->io_b,
+                         &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
+    size_t s = 0;
+    for (const DevBuf *p : b) s += p->bytes;
+    return s;
+}
+
+static int check_opts(const lqcd_opts *o)
+{
+    if (o->prec < LQCD_PREC_FP64 || o->prec > LQCD_PREC_FP64_NATIVE) return fail(LQCD_EINVAL, "opts.prec out of range");
+    if (o->recon != 18 && o->recon != 12) return fail(LQCD_EINVAL, "opts.recon must be 18 or 12");
+    if (!(o->delta_reliable > 0.0 && o->delta_reliable < 1.0)) return fail(LQCD_EINVAL, "opts.delta_reliable must be in (0,1)");
+    if (o->max_iter < 1) return fail(LQCD_EINVAL, "opts.max_iter must be >= 1");
+    if (o->check_every < 1 || o->check_every > 4096) return fail(LQCD_EINVAL, "opts.check_every must be in 1..4096");
+    return LQCD_OK;
+}
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" {
+
+void lqcd_default_opts(lqcd_opts *o)
+{
+    if (!o) return;
+    o->prec = LQCD_PREC_FP64;
+    o->recon = 18;
+    o->delta_reliable = 0.1;
+    o->max_iter = 20000;
+    o->check_every = 32;
+}
+
+const char *lqcd_last_error(void) { return g_err.c_str(); }
+
+int lqcd_version(void) { return 100; }
+
+int lqcd_create(const int dims[4], const lqcd_opts *opts, lqcd_ctx **out)
+{
+    if (!dims || !out) return fail(LQCD_EINVAL, "NULL argument");
+    *out = nullptr;
+    long V = 1;
+    for (int i = 0; i < 4; ++i) {
+        if (dims[i] < 2 || (dims[i] & 1)) return fail(LQCD_EINVAL, "lattice sides must be even and >= 2");
+        V *= dims[i];
+    }
+    if (V / 2 > (1l << 30)) return fail(LQCD_EINVAL, "lattice too large (V/2 must be < 2^30)");
+    lqcd_opts o;
+    lqcd_default_opts(&o);
+    if (opts) o = *opts;
+    int st = check_opts(&o);
+    if (st) return st;
+    lqcd_ctx *c = new (std::nothrow) lqcd_ctx();
+    if (!c) return fail(LQCD_ENOMEM, "host allocation failed");
+    for (int i = 0; i < 4; ++i) c->dims[i] = dims[i];
+    c->g = make_geom(dims);
+    c->V = (size_t)V;
+    c->Vh = (size_t)V / 2;
+    c->opts = o;
+    cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaStreamCreate(&c->stream);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_pinned, 2 * kMaxJobs * sizeof(int), cudaHostAllocDefault);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_pinned_d, 64 * sizeof(double), cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "lqcd_create");
+        lqcd_destroy(c);
+        return st;
+    }
+    *out = c;
+    return LQCD_OK;
+}
+
+void lqcd_destroy(lqcd_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    c->graph.reset();
+    DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->io_a, &c->io_b,
+                   &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
+    for (DevBuf *p : b) p->release();
+    if (c->h_pinned) cudaFreeHost(c->h_pinned);
+    if (c->h_pinned_d) cudaFreeHost(c->h_pinned_d);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int lqcd_set_opts(lqcd_ctx *c, const lqcd_opts *o)
+{
+    if (!c || !o) return fail(LQCD_EINVAL, "NULL argument");
+    int st = check_opts(o);
+    if (st) return st;
+    c->opts = *o;
+    return LQCD_OK;
+}
+
+size_t lqcd_device_bytes(const lqcd_ctx *c) { return c ? ctx_device_bytes(c) : 0; }
+
+int lqcd_links_upload(lqcd_ctx *c, const double *links, size_t n)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    c->graph.reset();
+    return upload_links(c, links, n);
+}
+
+int lqcd_links_download(lqcd_ctx *c, double *links, size_t n)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    return download_links(c, links, n);
+}
+
+int lqcd_deo_apply(lqcd_ctx *c, int out_parity, const void *in, void *out, int where, void *stream)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    if (where == 1) return deo_launch(c, out_parity, LQCD_PREC_FP64, 18, in, out, (cudaStream_t)stream ? (cudaStream_t)stream : c->stream);
+    if (where != 0) return fail(LQCD_EINVAL, "where must be 0 (host) or 1 (device)");
+    if (!in || !out) return fail(LQCD_EINVAL, "NULL spinor pointer");
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    const size_t bytes = c->Vh * 3 * sizeof(double2);
+    DevBuf din, dout;
+    int st;
+    if ((st = din.ensure(bytes)) || (st = dout.ensure(bytes))) return st;
+    cudaStream_t s = c->stream;
+    st = host_to_soa(c, (const double *)in, din.as<double2>(), 1, s);
+    if (!st) st = deo_launch(c, out_parity, LQCD_PREC_FP64, 18, din.ptr, dout.ptr, s);
+    if (!st) st = soa_to_host(c, dout.as<double2>(), (double *)out, 1, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    din.release();
+    dout.release();
+    if (st) return st;
+    if (e != cudaSuccess) return cuda_fail(e, "lqcd_deo_apply");
+    return LQCD_OK;
+}
+
+int lqcd_deo_apply_ex(lqcd_ctx *c, int out_parity, int prec, int recon, const void *in, void *out, void *stream)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    return deo_launch(c, out_parity, prec, recon, in, out, stream ? (cudaStream_t)stream : c->stream);
+}
+
+int lqcd_deo_apply_mrhs(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const void *in, void *out, void *stream)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    return deo_mrhs_launch(c, out_parity, n_rhs, recon, in, out, stream ? (cudaStream_t)stream : c->stream);
+}
+
+int lqcd_mscg_solve(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double *b,
+                    double *x, lqcd_solve_info *info)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    if (!b || !x || !shifts) return fail(LQCD_EINVAL, "NULL argument");
+    if (n_shift < 1 || n_shift > LQCD_MAX_SHIFTS) return fail(LQCD_EINVAL, "n_shift must be in 1..32");
+    const size_t n3 = 3 * c->Vh;
+    DevBuf db, dx;
+    int st;
+    if ((st = db.ensure(n3 * sizeof(double2))) || (st = dx.ensure((size_t)n_shift * n3 * sizeof(double2)))) return st;
+    cudaStream_t s = c->stream;
+    st = host_to_soa(c, b, db.as<double2>(), 1, s);
+    if (!st) st = mscg_solve_dev(c, mass, shifts, n_shift, tol, db.as<double2>(), dx.as<double2>(), info, s);
+    if (st == LQCD_OK || st == LQCD_ENOCONV) {
+        const int st2 = soa_to_host(c, dx.as<double2>(), x, n_shift, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (st2) st = st2;
+        else if (e != cudaSuccess) st = cuda_fail(e, "lqcd_mscg_solve");
+    }
+    db.release();
+    dx.release();
+    if (info) info->secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return st;
+}
+
+int lqcd_mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const void *b,
+                        void *x, lqcd_solve_info *info, void *stream)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    return mscg_solve_dev(c, mass, shifts, n_shift, tol, (const double2 *)b, (double2 *)x, info, (cudaStream_t)stream);
+}
+
+int lqcd_cg_solve_mrhs(lqcd_ctx *c, double mass, double sigma, int n_rhs, double tol, const double *b, double *x,
+                       lqcd_solve_info *info)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    return cg_solve_mrhs(c, mass, sigma, n_rhs, tol, b, x, info);
+}
+
+int lqcd_mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, const double *const *shifts,
+                           const int *n_shift, const double *tol, const double *const *b, double *const *x,
+                           lqcd_solve_info *info)
+{
+    if (!ctxs || n < 1 || n > kMaxJobs || !mass || !shifts || !n_shift || !tol || !b || !x)
+        return fail(LQCD_EINVAL, "bad packed-solve arguments");
+    return mscg_solve_packed(ctxs, n, mass, shifts, n_shift, tol, b, x, info);
+}
+
+}  // extern "C"

@@ -1,0 +1,255 @@
+// deo.cu -- link upload / storage conversion, host <-> device spinor
+// layouts, and the stand-alone D_eo / D_oe launches of the C ABI.
+#include <cmath>
+#include <cstring>
+
+#include "deo_core.cuh"
+#include "internal.h"
+
+namespace lqcd {
+
+// ------------------------------------------------------------------ link conversion
+// One thread per (mu, site): canonical [4][V][3][3] complex128 (staged on the
+// device) -> every device storage format.  Entries of magnitude >= 2^60 set
+// *bad (the df64 pairs must stay inside the FP32 exponent range).
+__global__ void k_convert_links(Geom g, const double2 *__restrict__ src, double2 *nat, float4 *df, float2 *f18,
+                                float2 *f12, uint32_t *h12, int *bad, long V)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= 4 * V) return;
+    const int mu = (int)(t / V);
+    const long lex = t - (long)mu * V;
+    const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
+    const int x0 = (int)(lex % N0);
+    const long r1 = lex / N0;
+    const int x1 = (int)(r1 % N1);
+    const long r2 = r1 / N1;
+    const int x2 = (int)(r2 % N2);
+    const int x3 = (int)(r2 / N2);
+    const int par = (x0 + x1 + x2 + x3) & 1;
+    const int idx = (int)(lex >> 1);
+    const int Vh = g.Vh;
+    for (int c = 0; c < 9; ++c) {
+        const double2 d = src[t * 9 + c];
+        if (!(fabs(d.x) < 0x1p60) || !(fabs(d.y) < 0x1p60)) atomicOr(bad, 1);
+        nat[link_base(mu, par, 9, Vh) + (size_t)c * Vh + idx] = d;
+        const float2 re = f64_to_df_slow(d.x), im = f64_to_df_slow(d.y);
+        df[link_base(mu, par, 9, Vh) + (size_t)c * Vh + idx] = make_float4(re.x, re.y, im.x, im.y);
+        const float2 f = make_float2((float)d.x, (float)d.y);
+        f18[link_base(mu, par, 9, Vh) + (size_t)c * Vh + idx] = f;
+        if (c < 6) {
+            f12[(link_base(mu, par, 3, Vh) + (size_t)(c >> 1) * Vh + idx) * 2 + (c & 1)] = f;
+            const __half2 h = __floats2half2_rn(f.x, f.y);
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(&h);
+            if (c < 4)
+                h12[((size_t)(mu * 2 + par) * Vh + idx) * 4 + c] = w;
+            else
+                h12[(size_t)8 * Vh * 4 + ((size_t)(mu * 2 + par) * Vh + idx) * 2 + (c - 4)] = w;
+        }
+    }
+}
+
+__global__ void k_links_to_canonical(Geom g, const double2 *__restrict__ nat, double2 *dst, long V)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= 4 * V) return;
+    const int mu = (int)(t / V);
+    const long lex = t - (long)mu * V;
+    const int N0 = g.N[0], N1 = g.N[1], N2 = g.N[2];
+    const int x0 = (int)(lex % N0);
+    const long r1 = lex / N0;
+    const int x1 = (int)(r1 % N1);
+    const long r2 = r1 / N1;
+    const int x2 = (int)(r2 % N2);
+    const int x3 = (int)(r2 / N2);
+    const int par = (x0 + x1 + x2 + x3) & 1;
+    const int idx = (int)(lex >> 1);
+    for (int c = 0; c < 9; ++c) dst[t * 9 + c] = nat[link_base(mu, par, 9, g.Vh) + (size_t)c * g.Vh + idx];
+}
+
+int upload_links(lqcd_ctx *c, const double *host, size_t n)
+{
+    const size_t want = 4 * c->V * 18;
+    if (!host) return fail(LQCD_EINVAL, "links pointer is NULL");
+    if (n != want) return fail(LQCD_EINVAL, "links: expected 4*V*18 = " + std::to_string(want) + " doubles, got " + std::to_string(n));
+    const size_t Vh = c->Vh;
+    int st;
+    if ((st = c->lnk_nat.ensure(72 * Vh * sizeof(double2)))) return st;
+    if ((st = c->lnk_df.ensure(72 * Vh * sizeof(float4)))) return st;
+    if ((st = c->lnk_f18.ensure(72 * Vh * sizeof(float2)))) return st;
+    if ((st = c->lnk_f12.ensure(24 * Vh * sizeof(float4)))) return st;
+    if ((st = c->lnk_h12.ensure(8 * Vh * (sizeof(uint4) + sizeof(uint2))))) return st;
+    DevBuf stage;
+    if ((st = stage.ensure(want * sizeof(double) + 16))) return st;
+    int *bad = (int *)((char *)stage.ptr + want * sizeof(double));
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage.ptr, host, want * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        const long V = (long)c->V;
+        const int bs = 256;
+        const long nb = (4 * V + bs - 1) / bs;
+        k_convert_links<<<(unsigned)nb, bs, 0, c->stream>>>(c->g, stage.as<double2>(), c->lnk_nat.as<double2>(),
+                                                            c->lnk_df.as<float4>(), c->lnk_f18.as<float2>(),
+                                                            c->lnk_f12.as<float2>(), c->lnk_h12.as<uint32_t>(), bad, V);
+        e = cudaGetLastError();
+    }
+    int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    stage.release();
+    if (e != cudaSuccess) return cuda_fail(e, "links upload");
+    if (hbad) {
+        c->links_ok = false;
+        return fail(LQCD_EINVAL, "links: an entry is NaN/Inf or has magnitude >= 2^60");
+    }
+    c->links_ok = true;
+    return LQCD_OK;
+}
+
+int download_links(lqcd_ctx *c, double *host, size_t n)
+{
+    const size_t want = 4 * c->V * 18;
+    if (!host || n != want) return fail(LQCD_EINVAL, "links download: expected 4*V*18 doubles");
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    DevBuf stage;
+    int st;
+    if ((st = stage.ensure(want * sizeof(double)))) return st;
+    const long V = (long)c->V;
+    k_links_to_canonical<<<(unsigned)((4 * V + 255) / 256), 256, 0, c->stream>>>(c->g, c->lnk_nat.as<double2>(),
+                                                                              stage.as<double2>(), V);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host, stage.ptr, want * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    stage.release();
+    if (e != cudaSuccess) return cuda_fail(e, "links download");
+    return LQCD_OK;
+}
+
+// ------------------------------------------------------------------ spinor layouts
+// host canonical [nf][Vh][3] complex128 <-> device [nf][3][Vh] double2
+__global__ void k_aos_to_soa(const double2 *__restrict__ a, double2 *__restrict__ s, long Vh, int nf)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= Vh * nf) return;
+    const long f = t / Vh, i = t - f * Vh;
+    for (int cc = 0; cc < 3; ++cc) s[(f * 3 + cc) * Vh + i] = a[t * 3 + cc];
+}
+
+__global__ void k_soa_to_aos(const double2 *__restrict__ s, double2 *__restrict__ a, long Vh, int nf)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= Vh * nf) return;
+    const long f = t / Vh, i = t - f * Vh;
+    for (int cc = 0; cc < 3; ++cc) a[t * 3 + cc] = s[(f * 3 + cc) * Vh + i];
+}
+
+int host_to_soa(lqcd_ctx *c, const double *host, double2 *dev_soa, int nf, cudaStream_t s)
+{
+    const size_t bytes = (size_t)nf * c->Vh * 3 * sizeof(double2);
+    int st;
+    if ((st = c->io_a.ensure(bytes))) return st;
+    LQCD_CUDA(cudaMemcpyAsync(c->io_a.ptr, host, bytes, cudaMemcpyHostToDevice, s));
+    const long n = (long)c->Vh * nf;
+    k_aos_to_soa<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(c->io_a.as<double2>(), dev_soa, (long)c->Vh, nf);
+    LQCD_CUDA(cudaGetLastError());
+    return LQCD_OK;
+}
+
+int soa_to_host(lqcd_ctx *c, const double2 *dev_soa, double *host, int nf, cudaStream_t s)
+{
+    const size_t bytes = (size_t)nf * c->Vh * 3 * sizeof(double2);
+    int st;
+    if ((st = c->io_b.ensure(bytes))) return st;
+    const long n = (long)c->Vh * nf;
+    k_soa_to_aos<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(dev_soa, c->io_b.as<double2>(), (long)c->Vh, nf);
+    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaMemcpyAsync(host, c->io_b.ptr, bytes, cudaMemcpyDeviceToHost, s));
+    return LQCD_OK;
+}
+
+// ------------------------------------------------------------------ stand-alone D_eo
+// FP64 result from df64 arithmetic; IEEE complex128 spinors in and out.
+__global__ void __launch_bounds__(kTile, 2)
+    k_deo_df_ieee(Geom g, const float4 *__restrict__ L, const double2 *__restrict__ in, double2 *__restrict__ out, int P)
+{
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    if (i >= g.Vh) return;
+    Stencil S;
+    make_stencil(g, i, P, S);
+    float2 res[6];
+    bool bad = false;
+    deo_site_df<SF_IEEE>(g, L, in, S, i, P, g.Vh, res, bad);
+    double2 o[3];
+    if (bad) {
+        deo_site_native_from_df(g, L, in, S, i, P, g.Vh, o);
+    } else {
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) o[cc] = make_double2(df_to_f64(res[2 * cc]), df_to_f64(res[2 * cc + 1]));
+    }
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
+}
+
+__global__ void __launch_bounds__(kTile, 2)
+    k_deo_nat(Geom g, const double2 *__restrict__ L, const double2 *__restrict__ in, double2 *__restrict__ out, int P)
+{
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    if (i >= g.Vh) return;
+    Stencil S;
+    make_stencil(g, i, P, S);
+    double2 o[3];
+    deo_site_nat(g, L, in, S, i, P, g.Vh, o);
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
+}
+
+template <int LF>
+__global__ void __launch_bounds__(kTile)
+    k_deo_f32(Geom g, const void *__restrict__ L, const float2 *__restrict__ in, float2 *__restrict__ out, int P)
+{
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    if (i >= g.Vh) return;
+    Stencil S;
+    make_stencil(g, i, P, S);
+    float2 o[3];
+    deo_site_f32<LF>(g, L, in, S, i, P, g.Vh, o);
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
+}
+
+int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *out, cudaStream_t s)
+{
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (P != 0 && P != 1) return fail(LQCD_EINVAL, "out_parity must be 0 or 1");
+    if (!in || !out) return fail(LQCD_EINVAL, "NULL spinor pointer");
+    if (in == out) return fail(LQCD_EINVAL, "in and out must not overlap");
+    const unsigned nb = (unsigned)((c->Vh + kTile - 1) / kTile);
+    switch (prec) {
+    case LQCD_PREC_FP64:
+        if (recon != 18) return fail(LQCD_EINVAL, "FP64 D_eo uses 18-real links");
+        k_deo_df_ieee<<<nb, kTile, 0, s>>>(c->g, c->lnk_df.as<float4>(), (const double2 *)in, (double2 *)out, P);
+        break;
+    case LQCD_PREC_FP64_NATIVE:
+        if (recon != 18) return fail(LQCD_EINVAL, "native FP64 D_eo uses 18-real links");
+        k_deo_nat<<<nb, kTile, 0, s>>>(c->g, c->lnk_nat.as<double2>(), (const double2 *)in, (double2 *)out, P);
+        break;
+    case LQCD_PREC_FP32:
+        if (recon == 18)
+            k_deo_f32<LF_F32_18><<<nb, kTile, 0, s>>>(c->g, c->lnk_f18.ptr, (const float2 *)in, (float2 *)out, P);
+        else if (recon == 12)
+            k_deo_f32<LF_F32_12><<<nb, kTile, 0, s>>>(c->g, c->lnk_f12.ptr, (const float2 *)in, (float2 *)out, P);
+        else
+            return fail(LQCD_EINVAL, "recon must be 18 or 12");
+        break;
+    case LQCD_PREC_FP16:
+        if (recon != 12) return fail(LQCD_EINVAL, "FP16 links use 12-real storage");
+        k_deo_f32<LF_F16_12><<<nb, kTile, 0, s>>>(c->g, c->lnk_h12.ptr, (const float2 *)in, (float2 *)out, P);
+        break;
+    default:
+        return fail(LQCD_EINVAL, "unknown precision");
+    }
+    LQCD_CUDA(cudaGetLastError());
+    return LQCD_OK;
+}
+
+}  // namespace lqcd

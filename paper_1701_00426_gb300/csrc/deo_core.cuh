@@ -1,0 +1,301 @@
+// deo_core.cuh -- the staggered hopping term D_eo / D_oe (Sec. 2.2,
+// Eq. diracblock) as sm_103a device code, in four arithmetics:
+//
+//   DF   links stored as df64 pairs (hi, lo floats; 18 reals -> 9 float4 per
+//        link), spinors df64 (float4 per complex) or IEEE complex128; every
+//        product and sum done with error-free FP32 transforms (common.cuh);
+//   F32  FP32 links (18 reals as 9 float2, or 12 reals as 3 float4 with the
+//        third row rebuilt, Sec. 2.3) and FP32 spinors (float2 per complex);
+//   F16  FP16 links, 12 reals (uint4 + uint2 per link), FP32 spinors/math;
+//   NAT  IEEE links and spinors with native FP64 FMA (reference variant).
+//
+// One thread computes one output site n of parity P:
+//   out(n) = 1/2 sum_mu [ s_mu(n) U_mu(n) in(n+mu) - s_mu(n-mu) U_mu(n-mu)^dag in(n-mu) ]
+// Links of direction mu are stored per parity of their base site, indexed by
+// the base site's half index: the forward link of n sits in (mu, P) at n's
+// own index and the backward link U_mu(n-mu) in (mu, 1-P) at the neighbour's
+// index, so each link is read exactly once per application.
+// All link arrays are structure-of-arrays over the half lattice
+// (component-major, site fastest): every load of a warp is one contiguous
+// 128-bit-per-thread stream.
+#pragma once
+
+#include "common.cuh"
+
+namespace lqcd {
+
+// Link storage formats
+enum LinkFmt { LF_DF18 = 0, LF_F32_18 = 1, LF_F32_12 = 2, LF_F16_12 = 3, LF_NAT18 = 4 };
+// Spinor formats
+enum SpinFmt { SF_DF = 0, SF_IEEE = 1, SF_F32 = 2 };
+
+// Offsets: the link array of (mu, parity) starts at (mu*2 + par) * comps * Vh.
+__device__ __forceinline__ size_t link_base(int mu, int par, int comps, int Vh)
+{
+    return (size_t)((mu * 2 + par) * comps) * (size_t)Vh;
+}
+
+// ------------------------------------------------------------------ DF hops
+// U component c = (re_h, re_l, im_h, im_l); v component likewise.
+__device__ __forceinline__ void hop_fwd_df(Acc2 (&acc)[6], const float4 (&U)[9], const float4 (&v)[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float4 u = U[a * 3 + b], w = v[b];
+            acc_prod(acc[2 * a], u.x, u.y, w.x, w.y);        // + ur vr
+            acc_prod(acc[2 * a], -u.z, -u.w, w.z, w.w);      // - ui vi
+            acc_prod(acc[2 * a + 1], u.x, u.y, w.z, w.w);    // + ur vi
+            acc_prod(acc[2 * a + 1], u.z, u.w, w.x, w.y);    // + ui vr
+        }
+}
+
+// (U^dag v)_a = sum_b conj(U_ba) v_b
+__device__ __forceinline__ void hop_bwd_df(Acc2 (&acc)[6], const float4 (&U)[9], const float4 (&v)[3])
+{
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float4 u = U[b * 3 + a], w = v[b];
+            acc_prod(acc[2 * a], u.x, u.y, w.x, w.y);        // + ur vr
+            acc_prod(acc[2 * a], u.z, u.w, w.z, w.w);        // + ui vi
+            acc_prod(acc[2 * a + 1], u.x, u.y, w.z, w.w);    // + ur vi
+            acc_prod(acc[2 * a + 1], -u.z, -u.w, w.x, w.y);  // - ui vr
+        }
+}
+
+template <int SF>
+__device__ __forceinline__ void load_spinor_df(const void *in, int idx, int Vh, uint32_t neg, float4 (&v)[3], bool &bad)
+{
+    if (SF == SF_DF) {
+        const float4 *p = (const float4 *)in;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) v[c] = xor_sign4(ldg4(p + (size_t)c * Vh + idx), neg);
+    } else {  // IEEE complex128: split on the fly with integer operations
+        const double2 *p = (const double2 *)in;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 d = ldg2d(p + (size_t)c * Vh + idx);
+            const float2 re = split_f64(d.x, bad), im = split_f64(d.y, bad);
+            v[c] = xor_sign4(make_float4(re.x, re.y, im.x, im.y), neg);
+        }
+    }
+}
+
+__device__ __forceinline__ void load_link_df(const float4 *L, int mu, int par, int idx, int Vh, float4 (&U)[9])
+{
+    const float4 *p = L + link_base(mu, par, 9, Vh) + idx;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) U[c] = ldg4(p + (size_t)c * Vh);
+}
+
+// D applied at one site in df64.  Returns the six (re, im) x colour results
+// as normalised df64 pairs, already multiplied by 1/2.
+template <int SF>
+__device__ __forceinline__ void deo_site_df(const Geom &g, const float4 *L, const void *in, const Stencil &S, int i,
+                                            int P, int Vh, float2 (&res)[6], bool &bad)
+{
+    Acc2 acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc_zero(acc[k]);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        int f, b;
+        uint32_t nf, nb;
+        hop(g, S, mu, f, b, nf, nb);
+        float4 U[9], v[3];
+        load_link_df(L, mu, P, i, Vh, U);
+        load_spinor_df<SF>(in, f, Vh, nf, v, bad);
+        hop_fwd_df(acc, U, v);
+        load_link_df(L, mu, 1 - P, b, Vh, U);
+        load_spinor_df<SF>(in, b, Vh, nb, v, bad);
+        hop_bwd_df(acc, U, v);
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float2 r = acc_result(acc[k]);
+        res[k] = make_float2(0.5f * r.x, 0.5f * r.y);
+    }
+}
+
+// Native FP64 evaluation of one site from df64 links and IEEE spinors: the
+// fallback for sites whose inputs fall outside the df64 exponent window.
+static __device__ __noinline__ void deo_site_native_from_df(const Geom &g, const float4 *L, const double2 *in,
+                                                            const Stencil &S, int i, int P, int Vh, double2 (&res)[3])
+{
+    double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int mu = 0; mu < 4; ++mu) {
+        int f, b;
+        uint32_t nf, nb;
+        hop(g, S, mu, f, b, nf, nb);
+        for (int dir = 0; dir < 2; ++dir) {
+            const int idx = dir == 0 ? f : b;
+            const int par = dir == 0 ? P : 1 - P;
+            const int lidx = dir == 0 ? i : b;
+            const double sg = ((dir == 0 ? nf : nb) != 0u) ? -1.0 : 1.0;
+            const float4 *lp = L + link_base(mu, par, 9, Vh) + lidx;
+            double2 v[3];
+            for (int c = 0; c < 3; ++c) v[c] = in[(size_t)c * Vh + idx];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    const float4 u4 = lp[(size_t)(dir == 0 ? a * 3 + b : b * 3 + a) * Vh];
+                    const double ur = (double)u4.x + (double)u4.y;
+                    double ui = (double)u4.z + (double)u4.w;
+                    if (dir == 1) ui = -ui;
+                    acc[a].x += sg * (ur * v[b].x - ui * v[b].y);
+                    acc[a].y += sg * (ur * v[b].y + ui * v[b].x);
+                }
+        }
+    }
+    for (int a = 0; a < 3; ++a) res[a] = make_double2(0.5 * acc[a].x, 0.5 * acc[a].y);
+}
+
+// ------------------------------------------------------------------ native FP64 (reference)
+__device__ __forceinline__ void deo_site_nat(const Geom &g, const double2 *L, const double2 *in, const Stencil &S,
+                                             int i, int P, int Vh, double2 (&res)[3])
+{
+    double2 acc[3] = {{0, 0}, {0, 0}, {0, 0}};
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        int f, b;
+        uint32_t nf, nb;
+        hop(g, S, mu, f, b, nf, nb);
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            const int idx = dir == 0 ? f : b;
+            const int par = dir == 0 ? P : 1 - P;
+            const int lidx = dir == 0 ? i : b;
+            const double sg = ((dir == 0 ? nf : nb) != 0u) ? -1.0 : 1.0;
+            const double2 *lp = L + link_base(mu, par, 9, Vh) + lidx;
+            double2 v[3], U[9];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double2 t = ldg2d(in + (size_t)c * Vh + idx);
+                v[c] = make_double2(sg * t.x, sg * t.y);
+            }
+#pragma unroll
+            for (int c = 0; c < 9; ++c) U[c] = ldg2d(lp + (size_t)c * Vh);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    if (dir == 0) {
+                        const double2 u = U[a * 3 + b];
+                        acc[a].x = fma(u.x, v[b].x, fma(-u.y, v[b].y, acc[a].x));
+                        acc[a].y = fma(u.x, v[b].y, fma(u.y, v[b].x, acc[a].y));
+                    } else {
+                        const double2 u = U[b * 3 + a];
+                        acc[a].x = fma(u.x, v[b].x, fma(u.y, v[b].y, acc[a].x));
+                        acc[a].y = fma(u.x, v[b].y, fma(-u.y, v[b].x, acc[a].y));
+                    }
+                }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) res[a] = make_double2(0.5 * acc[a].x, 0.5 * acc[a].y);
+}
+
+// ------------------------------------------------------------------ FP32 / FP16 hops
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(__fmaf_rn(a.x, b.x, -a.y * b.y), __fmaf_rn(a.x, b.y, a.y * b.x));
+}
+
+// third row of an SU(3) matrix from the first two: r2 = conj(r0 x r1) (Sec. 2.3)
+__device__ __forceinline__ void reconstruct_row2(float2 (&U)[9])
+{
+    const float2 a0 = U[0], a1 = U[1], a2 = U[2], b0 = U[3], b1 = U[4], b2 = U[5];
+    float2 c;
+    c = make_float2(a1.x * b2.x - a1.y * b2.y - (a2.x * b1.x - a2.y * b1.y),
+                    a1.x * b2.y + a1.y * b2.x - (a2.x * b1.y + a2.y * b1.x));
+    U[6] = make_float2(c.x, -c.y);
+    c = make_float2(a2.x * b0.x - a2.y * b0.y - (a0.x * b2.x - a0.y * b2.y),
+                    a2.x * b0.y + a2.y * b0.x - (a0.x * b2.y + a0.y * b2.x));
+    U[7] = make_float2(c.x, -c.y);
+    c = make_float2(a0.x * b1.x - a0.y * b1.y - (a1.x * b0.x - a1.y * b0.y),
+                    a0.x * b1.y + a0.y * b1.x - (a1.x * b0.y + a1.y * b0.x));
+    U[8] = make_float2(c.x, -c.y);
+}
+
+__device__ __forceinline__ float2 h2f(uint32_t w)
+{
+    const __half2 h = *reinterpret_cast<const __half2 *>(&w);
+    return __half22float2(h);
+}
+
+template <int LF>
+__device__ __forceinline__ void load_link_f32(const void *L, int mu, int par, int idx, int Vh, float2 (&U)[9])
+{
+    if (LF == LF_F32_18) {
+        const float2 *p = (const float2 *)L + link_base(mu, par, 9, Vh) + idx;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) U[c] = ldg2(p + (size_t)c * Vh);
+    } else if (LF == LF_F32_12) {
+        const float4 *p = (const float4 *)L + link_base(mu, par, 3, Vh) + idx;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float4 t = ldg4(p + (size_t)k * Vh);
+            U[2 * k] = make_float2(t.x, t.y);
+            U[2 * k + 1] = make_float2(t.z, t.w);
+        }
+        reconstruct_row2(U);
+    } else {  // LF_F16_12: [8 Vh] uint4 (c00 c01 c02 c10) then [8 Vh] uint2 (c11 c12)
+        const uint4 *pa = (const uint4 *)L;
+        const uint2 *pb = (const uint2 *)(pa + (size_t)8 * Vh);
+        const uint4 a = __ldg(pa + (size_t)(mu * 2 + par) * Vh + idx);
+        const uint2 b = __ldg(pb + (size_t)(mu * 2 + par) * Vh + idx);
+        U[0] = h2f(a.x); U[1] = h2f(a.y); U[2] = h2f(a.z); U[3] = h2f(a.w);
+        U[4] = h2f(b.x); U[5] = h2f(b.y);
+        reconstruct_row2(U);
+    }
+}
+
+template <int LF>
+__device__ __forceinline__ void deo_site_f32(const Geom &g, const void *L, const float2 *in, const Stencil &S, int i,
+                                             int P, int Vh, float2 (&res)[3])
+{
+    float2 acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        int f, b;
+        uint32_t nf, nb;
+        hop(g, S, mu, f, b, nf, nb);
+        float2 U[9], v[3];
+        load_link_f32<LF>(L, mu, P, i, Vh, U);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 t = ldg2(in + (size_t)c * Vh + f);
+            v[c] = make_float2(__uint_as_float(__float_as_uint(t.x) ^ nf),
+                               __uint_as_float(__float_as_uint(t.y) ^ nf));
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const float2 u = U[a * 3 + b];
+                acc[a].x = __fmaf_rn(u.x, v[b].x, __fmaf_rn(-u.y, v[b].y, acc[a].x));
+                acc[a].y = __fmaf_rn(u.x, v[b].y, __fmaf_rn(u.y, v[b].x, acc[a].y));
+            }
+        load_link_f32<LF>(L, mu, 1 - P, b, Vh, U);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 t = ldg2(in + (size_t)c * Vh + b);
+            v[c] = make_float2(__uint_as_float(__float_as_uint(t.x) ^ nb),
+                               __uint_as_float(__float_as_uint(t.y) ^ nb));
+        }
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                const float2 u = U[b * 3 + a];
+                acc[a].x = __fmaf_rn(u.x, v[b].x, __fmaf_rn(u.y, v[b].y, acc[a].x));
+                acc[a].y = __fmaf_rn(u.x, v[b].y, __fmaf_rn(-u.y, v[b].x, acc[a].y));
+            }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) res[a] = make_float2(0.5f * acc[a].x, 0.5f * acc[a].y);
+}
+
+}  // namespace lqcd

@@ -1,0 +1,151 @@
+// internal.h -- host-side structures shared by the translation units of
+// liblqcd (not part of the public C ABI, which is include/lqcd.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/lqcd.h"
+#include "common.cuh"
+
+namespace lqcd {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+int fail(int status, const std::string &msg);  // sets the message, returns status
+int cuda_fail(cudaError_t e, const char *what);
+
+#define LQCD_CUDA(call)                                                     \
+    do {                                                                    \
+        cudaError_t _e = (call);                                            \
+        if (_e != cudaSuccess) return ::lqcd::cuda_fail(_e, #call);         \
+    } while (0)
+
+// ------------------------------------------------------------------ device buffer
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t n);  // grow (contents dropped); LQCD_OK / LQCD_ENOMEM
+    void release();
+    template <class T> T *as() const { return (T *)ptr; }
+};
+
+// ------------------------------------------------------------------ solver state
+// Device-resident scalars of one Krylov solve (one job).  Written by the
+// host at set-up, then only by the one-thread finalisers of the iteration
+// kernels, so an iteration needs no host round trip.
+struct SolverState {
+    // set-up (host)
+    int n_shift, base, max_iter, halt;
+    int iters, do_k4, n_act, nan_flag;
+    double a0;                        // m^2 + sigma_base
+    double tol2_b2;                   // (tol * ||b||)^2, iterated stopping rule
+    double rel_stop2;                 // reliable update when rho < this (0 = off)
+    double shift_rel[kMaxShifts];     // sigma_i - sigma_base
+    // recurrences (device)
+    double rho, alpha, alpha_prev, beta, beta_prev;
+    double zeta[kMaxShifts], zeta_prev[kMaxShifts], zeta_new[kMaxShifts];
+    int active_next[kMaxShifts];
+    int act_list[kMaxShifts];
+    int shift_iters[kMaxShifts];
+    double last_sum;                  // last reduction result (diagnostics)
+    // split copies for the vector kernels: df64 (hi, lo) and FP32 (hi only)
+    float2 a0_df, alpha_df;
+    float2 alpha_s_df[kMaxShifts], zeta_new_df[kMaxShifts], beta_s_df[kMaxShifts];
+};
+
+enum Halt { HALT_NONE = 0, HALT_CONVERGED = 1, HALT_RELIABLE = 2, HALT_MAXITER = 3, HALT_NAN = 4 };
+
+// Krylov vector precision of an engine
+enum VecPrec { VP_DF = 0, VP_F32 = 1 };
+
+// One job (one lattice / request) of a tiled iteration launch.
+struct IterJob {
+    Geom g;
+    const void *links;   // link storage for the engine's deo variant
+    void *r, *q, *t;     // residual, A p, odd temporary
+    void *x, *ps;        // n_shift solutions / directions, shift-major [n][3][Vh]
+    SolverState *st;
+    double *part;        // per-tile partial sums
+    unsigned *ticket;    // last-block-done counter
+    int tile0, ntiles;
+};
+
+template <int NJ>
+struct IterBatch {
+    int njobs;
+    int tile_start[NJ + 1];
+    IterJob job[NJ];
+};
+
+// ------------------------------------------------------------------ context
+struct Workspace {
+    int prec = -1;          // VecPrec of the Krylov vectors
+    int n_shift = 0;
+    DevBuf vec;             // r, q, t, x[n], ps[n]
+    DevBuf ieee;            // b, r_hi, x_hi[n] (complex128 SoA), tmp
+    DevBuf part;            // partial sums
+    DevBuf tickets;
+    DevBuf state;           // SolverState
+    DevBuf stage;           // host-format staging
+    uint64_t gen = 0;       // bumped on every reallocation (graph cache key)
+};
+
+struct GraphCache {
+    uint64_t key = ~0ull;
+    cudaGraphExec_t exec = nullptr;
+    void reset();
+};
+
+}  // namespace lqcd
+
+struct lqcd_ctx {
+    int device = 0;
+    int dims[4];
+    lqcd::Geom g;
+    size_t V = 0, Vh = 0;
+    lqcd_opts opts;
+    cudaStream_t stream = nullptr;
+    bool links_ok = false;
+    // link storage (see deo_core.cuh for the layouts)
+    lqcd::DevBuf lnk_df;    // df64 pairs, 18 reals: [4][2][9][Vh] float4
+    lqcd::DevBuf lnk_nat;   // IEEE, 18 reals:       [4][2][9][Vh] double2
+    lqcd::DevBuf lnk_f18;   // FP32, 18 reals:       [4][2][9][Vh] float2
+    lqcd::DevBuf lnk_f12;   // FP32, 12 reals:       [4][2][3][Vh] float4
+    lqcd::DevBuf lnk_h12;   // FP16, 12 reals:       [8][Vh] uint4 + [8][Vh] uint2
+    lqcd::DevBuf io_a, io_b;  // device staging of host spinors for where = 0
+    lqcd::Workspace ws;
+    lqcd::GraphCache graph;
+    int *h_pinned = nullptr;  // pinned host words for halt/iteration polling
+    double *h_pinned_d = nullptr;
+};
+
+namespace lqcd {
+
+size_t ctx_device_bytes(const lqcd_ctx *c);
+
+// deo.cu
+int deo_launch(lqcd_ctx *c, int out_parity, int prec, int recon, const void *in, void *out, cudaStream_t s);
+int upload_links(lqcd_ctx *c, const double *host, size_t n);
+int download_links(lqcd_ctx *c, double *host, size_t n);
+int host_to_soa(lqcd_ctx *c, const double *host, double2 *dev_soa, int nfields, cudaStream_t s);
+int soa_to_host(lqcd_ctx *c, const double2 *dev_soa, double *host, int nfields, cudaStream_t s);
+
+// solver.cu
+int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double2 *b,
+                   double2 *x, lqcd_solve_info *info, cudaStream_t s);
+int mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, const double *const *shifts,
+                      const int *n_shift, const double *tol, const double *const *b, double *const *x,
+                      lqcd_solve_info *info);
+
+// mrhs.cu
+int deo_mrhs_launch(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const void *in, void *out, cudaStream_t s);
+int cg_solve_mrhs(lqcd_ctx *c, double mass, double sigma, int n_rhs, double tol, const double *b, double *x,
+                  lqcd_solve_info *info);
+
+}  // namespace lqcd

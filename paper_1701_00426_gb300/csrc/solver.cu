@@ -1,0 +1,674 @@
+// solver.cu -- host driver of the multi-shift CG (Sec. 2.2, Eqs. lineqeo,
+// shlineq) and its helper kernels.
+//
+// FP64 solve (opts.prec = FP64): the Krylov iteration runs with df64
+// vectors and df64 D_eo (48-bit significands, FP32 pipes).  Afterwards each
+// shift's solution is converted to IEEE FP64, its true residual
+// ||(A + sigma_i) x_i - b|| is recomputed from the IEEE solution, and a shift
+// whose true residual exceeds tol is corrected by solving for the residual
+// (defect correction) until it meets tol.
+//
+// Mixed solve (opts.prec = FP32 / FP16): the multi-shift iteration runs with
+// FP32 vectors and FP32 (or FP16-stored) links; then every shift is finished
+// by a single-shift CG with FP32 iterations and FP64 reliable updates: when
+// the FP32 residual has fallen below delta times the residual of the last
+// update, the FP32 solution is added to the FP64 one, the FP64 true residual
+// replaces the FP32 residual and the search direction is kept.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "solver_kernels.cuh"
+
+namespace lqcd {
+
+// ------------------------------------------------------------------ helper kernels
+__global__ void k_norm2_ieee(const double2 *__restrict__ v, int Vh, int nvec, double *part, unsigned *ticket,
+                             int ntiles, double *out)
+{
+    __shared__ double s_red[kTile / 32];
+    const int tile = blockIdx.x;
+    const int i = tile * kTile + threadIdx.x;
+    double a = 0.0;
+    if (i < Vh)
+        for (int c = 0; c < 3 * nvec; ++c) {
+            const double2 d = v[(size_t)c * Vh + i];
+            a = fma(d.x, d.x, fma(d.y, d.y, a));
+        }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xFFFFFFFFu, a, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    double v0 = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kTile / 32; ++k) v0 += s_red[k];
+    reduce_finish(part, ticket, ntiles, tile, v0, [&](double tot) { *out = tot; });
+}
+
+// dst (engine format) = scale * src (IEEE)
+template <int VP>
+__global__ void k_ieee_to_vec(const double2 *__restrict__ src, void *dst, long n, double scale)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double2 d = src[t];
+    if constexpr (VP == VP_DF) {
+        const float2 re = f64_to_df_slow(d.x * scale), im = f64_to_df_slow(d.y * scale);
+        ((float4 *)dst)[t] = make_float4(re.x, re.y, im.x, im.y);
+    } else {
+        ((float2 *)dst)[t] = make_float2((float)(d.x * scale), (float)(d.y * scale));
+    }
+}
+
+// dst (IEEE) (+)= scale * src (engine format)
+template <int VP>
+__global__ void k_vec_to_ieee(const void *src, double2 *dst, long n, double scale, int accumulate)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    double re, im;
+    if constexpr (VP == VP_DF) {
+        const float4 v = ((const float4 *)src)[t];
+        re = df_to_f64(make_float2(v.x, v.y));
+        im = df_to_f64(make_float2(v.z, v.w));
+    } else {
+        const float2 v = ((const float2 *)src)[t];
+        re = (double)v.x;
+        im = (double)v.y;
+    }
+    re *= scale;
+    im *= scale;
+    if (accumulate) {
+        const double2 o = dst[t];
+        re += o.x;
+        im += o.y;
+    }
+    dst[t] = make_double2(re, im);
+}
+
+// r = ps[s] = src for every shift, x[s] = 0 (engine format; one field = n3 complex)
+template <int VP>
+__global__ void k_init_vectors(const void *src, void *r, void *x, void *ps, long n3, int n_shift)
+{
+    using T = typename VecT<VP>::T;
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= n3) return;
+    const T v = ((const T *)src)[t];
+    if (r != src) ((T *)r)[t] = v;
+    T z;
+    memset(&z, 0, sizeof(T));
+    for (int s = 0; s < n_shift; ++s) {
+        ((T *)ps)[(long)s * n3 + t] = v;
+        ((T *)x)[(long)s * n3 + t] = z;
+    }
+}
+
+template <int VP>
+__global__ void k_scale_vec(void *v, long n3, float f)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= n3) return;
+    if constexpr (VP == VP_DF) {
+        float4 a = ((float4 *)v)[t];
+        ((float4 *)v)[t] = make_float4(a.x * f, a.y * f, a.z * f, a.w * f);
+    } else {
+        float2 a = ((float2 *)v)[t];
+        ((float2 *)v)[t] = make_float2(a.x * f, a.y * f);
+    }
+}
+
+template <int VP>
+__global__ void k_zero_vec(void *v, long n3)
+{
+    using T = typename VecT<VP>::T;
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= n3) return;
+    T z;
+    memset(&z, 0, sizeof(T));
+    ((T *)v)[t] = z;
+}
+
+// True residual in native IEEE FP64 (FP64 FMA on the FP64 pipe): it runs a
+// few times per solve, and it must not share the df64 rounding of the
+// iteration it checks.
+// Part 1: t = D_oe x.
+__global__ void __launch_bounds__(kTile)
+    k_res_nat1(Geom g, const double2 *__restrict__ L, const double2 *__restrict__ x, double2 *__restrict__ t)
+{
+    const int i = blockIdx.x * kTile + threadIdx.x;
+    if (i >= g.Vh) return;
+    Stencil S;
+    make_stencil(g, i, 1, S);
+    double2 o[3];
+    deo_site_nat(g, L, x, S, i, 1, g.Vh, o);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) t[(size_t)c * g.Vh + i] = o[c];
+}
+
+// Part 2: r = b - ((m^2 + sigma) x - D_eo t).  Writes r_hi (IEEE, optional),
+// r_lo = lo_scale * r in the engine format (optional) and ||r||^2 to *out.
+template <int VP>
+__global__ void __launch_bounds__(kTile)
+    k_res_nat2(Geom g, const double2 *__restrict__ L, const double2 *__restrict__ t, const double2 *__restrict__ x,
+               const double2 *__restrict__ b, double a, double2 *r_hi, void *r_lo, double lo_scale, double *part,
+               unsigned *ticket, double *out)
+{
+    __shared__ double s_red[kTile / 32];
+    const int tile = blockIdx.x;
+    const int i = tile * kTile + threadIdx.x;
+    double nrm = 0.0;
+    if (i < g.Vh) {
+        Stencil S;
+        make_stencil(g, i, 0, S);
+        double2 o[3];
+        deo_site_nat(g, L, t, S, i, 0, g.Vh, o);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const double2 xv = x[(size_t)c * g.Vh + i], bv = b[(size_t)c * g.Vh + i];
+            const double2 r = make_double2(bv.x - fma(a, xv.x, -o[c].x), bv.y - fma(a, xv.y, -o[c].y));
+            nrm = fma(r.x, r.x, fma(r.y, r.y, nrm));
+            if (r_hi) r_hi[(size_t)c * g.Vh + i] = r;
+            if (r_lo) {
+                if constexpr (VP == VP_DF) {
+                    const float2 a0 = f64_to_df_slow(r.x * lo_scale), a1 = f64_to_df_slow(r.y * lo_scale);
+                    ((float4 *)r_lo)[(size_t)c * g.Vh + i] = make_float4(a0.x, a0.y, a1.x, a1.y);
+                } else {
+                    ((float2 *)r_lo)[(size_t)c * g.Vh + i] = make_float2((float)(r.x * lo_scale), (float)(r.y * lo_scale));
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nrm += __shfl_down_sync(0xFFFFFFFFu, nrm, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = nrm;
+    __syncthreads();
+    double v = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < kTile / 32; ++k) v += s_red[k];
+    const int ntiles = (g.Vh + kTile - 1) / kTile;
+    reduce_finish(part, ticket, ntiles, tile, v, [&](double tot) { *out = tot; });
+}
+
+// ------------------------------------------------------------------ workspace
+struct WsPtrs {
+    void *r, *q, *t, *x, *ps;
+    double2 *r_hi;
+    double2 *t_nat;
+    double *part;
+    unsigned *ticket;   // [0] iteration kernels, [1] helpers
+    SolverState *st;
+    double *scal;       // helper reduction outputs (device doubles)
+    int ntiles;
+};
+
+static int ensure_workspace(lqcd_ctx *c, int vp, int n_shift, WsPtrs &P)
+{
+    Workspace &W = c->ws;
+    const size_t Vh = c->Vh, n3 = 3 * Vh;
+    const size_t E = vp == VP_DF ? sizeof(float4) : sizeof(float2);
+    const size_t vec_bytes = (3 + 2 * (size_t)n_shift) * n3 * E;
+    const size_t ieee_bytes = 2 * n3 * sizeof(double2);
+    const int ntiles = (int)((Vh + kTile - 1) / kTile);
+    int st;
+    if (vec_bytes > W.vec.bytes || ieee_bytes > W.ieee.bytes) W.gen++;
+    if ((st = W.vec.ensure(std::max(vec_bytes, W.vec.bytes)))) return st;
+    if ((st = W.ieee.ensure(std::max(ieee_bytes, W.ieee.bytes)))) return st;
+    if ((st = W.part.ensure((size_t)ntiles * sizeof(double) + 64 * sizeof(double)))) return st;
+    if (!W.tickets.ptr) {
+        if ((st = W.tickets.ensure(64))) return st;
+        LQCD_CUDA(cudaMemset(W.tickets.ptr, 0, 64));
+        W.gen++;
+    }
+    if (!W.state.ptr) {
+        if ((st = W.state.ensure(sizeof(SolverState)))) return st;
+        W.gen++;
+    }
+    char *v = (char *)W.vec.ptr;
+    P.r = v;
+    P.q = v + n3 * E;
+    P.t = v + 2 * n3 * E;
+    P.x = v + 3 * n3 * E;
+    P.ps = v + (3 + (size_t)n_shift) * n3 * E;
+    P.r_hi = (double2 *)W.ieee.ptr;
+    P.t_nat = (double2 *)W.ieee.ptr + n3;
+    P.part = (double *)W.part.ptr;
+    P.scal = P.part + ntiles;
+    P.ticket = (unsigned *)W.tickets.ptr;
+    P.st = (SolverState *)W.state.ptr;
+    P.ntiles = ntiles;
+    W.prec = vp;
+    W.n_shift = n_shift;
+    return LQCD_OK;
+}
+
+static inline unsigned nblk(long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
+
+static int norm2_ieee(lqcd_ctx *c, const WsPtrs &P, const double2 *v, int nvec, cudaStream_t s, double &out)
+{
+    k_norm2_ieee<<<P.ntiles, kTile, 0, s>>>(v, (int)c->Vh, nvec, P.part, P.ticket + 1, P.ntiles, P.scal);
+    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaMemcpyAsync(c->h_pinned_d, P.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    LQCD_CUDA(cudaStreamSynchronize(s));
+    out = c->h_pinned_d[0];
+    return LQCD_OK;
+}
+
+// r = b - (A + sigma) x with IEEE x, b; optional r_hi / r_lo; returns ||r||^2.
+static int true_residual(lqcd_ctx *c, const WsPtrs &P, int vp, double a, const double2 *x, const double2 *b,
+                         double2 *r_hi, void *r_lo, double lo_scale, cudaStream_t s, double &rr)
+{
+    const double2 *L = c->lnk_nat.as<double2>();
+    k_res_nat1<<<P.ntiles, kTile, 0, s>>>(c->g, L, x, P.t_nat);
+    LQCD_CUDA(cudaGetLastError());
+    if (vp == VP_DF)
+        k_res_nat2<VP_DF><<<P.ntiles, kTile, 0, s>>>(c->g, L, P.t_nat, x, b, a, r_hi, r_lo, lo_scale, P.part,
+                                                      P.ticket + 1, P.scal);
+    else
+        k_res_nat2<VP_F32><<<P.ntiles, kTile, 0, s>>>(c->g, L, P.t_nat, x, b, a, r_hi, r_lo, lo_scale, P.part,
+                                                       P.ticket + 1, P.scal);
+    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaMemcpyAsync(c->h_pinned_d, P.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+    LQCD_CUDA(cudaStreamSynchronize(s));
+    rr = c->h_pinned_d[0];
+    return LQCD_OK;
+}
+
+// power of two bringing a field of squared norm n2 over n reals to O(1) entries
+static double unit_scale(double n2, double n)
+{
+    if (!(n2 > 0.0) || !std::isfinite(n2)) return 1.0;
+    const double rms = std::sqrt(n2 / n);
+    return std::ldexp(1.0, -(int)std::lround(std::log2(rms)));
+}
+
+// ------------------------------------------------------------------ iteration chunks
+template <int NJ>
+static void launch_iteration(const IterBatch<NJ> &B, int ntot, int vp, int lf, cudaStream_t s)
+{
+    if (vp == VP_DF) {
+        k_it_deo1<NJ, VP_DF, LF_DF18><<<ntot, kTile, 0, s>>>(B);
+        k_it_deo2<NJ, VP_DF, LF_DF18><<<ntot, kTile, 0, s>>>(B);
+        k_it_upd_r<NJ, VP_DF><<<ntot, kTile, 0, s>>>(B);
+        k_it_upd_shifts<NJ, VP_DF><<<ntot, kTile, 0, s>>>(B);
+    } else {
+        switch (lf) {
+        case LF_F32_18:
+            k_it_deo1<NJ, VP_F32, LF_F32_18><<<ntot, kTile, 0, s>>>(B);
+            k_it_deo2<NJ, VP_F32, LF_F32_18><<<ntot, kTile, 0, s>>>(B);
+            break;
+        case LF_F32_12:
+            k_it_deo1<NJ, VP_F32, LF_F32_12><<<ntot, kTile, 0, s>>>(B);
+            k_it_deo2<NJ, VP_F32, LF_F32_12><<<ntot, kTile, 0, s>>>(B);
+            break;
+        default:
+            k_it_deo1<NJ, VP_F32, LF_F16_12><<<ntot, kTile, 0, s>>>(B);
+            k_it_deo2<NJ, VP_F32, LF_F16_12><<<ntot, kTile, 0, s>>>(B);
+            break;
+        }
+        k_it_upd_r<NJ, VP_F32><<<ntot, kTile, 0, s>>>(B);
+        k_it_upd_shifts<NJ, VP_F32><<<ntot, kTile, 0, s>>>(B);
+    }
+}
+
+void GraphCache::reset()
+{
+    if (exec) cudaGraphExecDestroy(exec);
+    exec = nullptr;
+    key = ~0ull;
+}
+
+static uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
+{
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= b[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+// Run iteration chunks (graph of `chunk` iterations) until every job halts.
+// Pipelined: chunk k+1 is queued before chunk k's halt words are read.
+template <int NJ>
+static int run_until_halt(lqcd_ctx *c, const IterBatch<NJ> &B, int vp, int lf, int chunk, int max_iter,
+                          cudaStream_t s, std::vector<int> &halts)
+{
+    int ntot = B.tile_start[B.njobs];
+    uint64_t key = fnv1a(&B, sizeof(B));
+    key = fnv1a(&vp, sizeof vp, key);
+    key = fnv1a(&lf, sizeof lf, key);
+    key = fnv1a(&chunk, sizeof chunk, key);
+    key ^= (uint64_t)NJ * 0x9E3779B97F4A7C15ull;
+    if (c->graph.key != key || !c->graph.exec) {
+        c->graph.reset();
+        cudaGraph_t g;
+        LQCD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        for (int k = 0; k < chunk; ++k) launch_iteration<NJ>(B, ntot, vp, lf, s);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+        e = cudaGraphInstantiate(&c->graph.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        c->graph.key = key;
+    }
+    const int nj = B.njobs;
+    // pinned status words: [2][nj] halts
+    int *hs = c->h_pinned;
+    const int max_chunks = max_iter / chunk + 4;
+    int slot = 0;
+    cudaEvent_t ev[2];
+    LQCD_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    LQCD_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+    auto enqueue = [&](int sl) -> cudaError_t {
+        cudaError_t e = cudaGraphLaunch(c->graph.exec, s);
+        for (int j = 0; j < nj && e == cudaSuccess; ++j)
+            e = cudaMemcpyAsync(hs + sl * kMaxJobs + j, &B.job[j].st->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[sl], s);
+        return e;
+    };
+    cudaError_t e = enqueue(0);
+    int rc = LQCD_OK;
+    for (int k = 0; k < max_chunks && e == cudaSuccess; ++k) {
+        const int nxt = slot ^ 1;
+        e = enqueue(nxt);
+        if (e != cudaSuccess) break;
+        e = cudaEventSynchronize(ev[slot]);
+        if (e != cudaSuccess) break;
+        bool all = true;
+        for (int j = 0; j < nj; ++j) all &= hs[slot * kMaxJobs + j] != HALT_NONE;
+        if (all) break;
+        slot = nxt;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (e != cudaSuccess) return cuda_fail(e, "iteration chunks");
+    halts.assign(nj, 0);
+    for (int j = 0; j < nj; ++j) {
+        LQCD_CUDA(cudaMemcpy(&halts[j], &B.job[j].st->halt, sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    return rc;
+}
+
+static int link_fmt_for(const lqcd_ctx *c, int prec, const void **links)
+{
+    if (prec == LQCD_PREC_FP64) {
+        *links = c->lnk_df.ptr;
+        return LF_DF18;
+    }
+    if (prec == LQCD_PREC_FP16) {
+        *links = c->lnk_h12.ptr;
+        return LF_F16_12;
+    }
+    if (c->opts.recon == 12) {
+        *links = c->lnk_f12.ptr;
+        return LF_F32_12;
+    }
+    *links = c->lnk_f18.ptr;
+    return LF_F32_18;
+}
+
+static void fill_job(lqcd_ctx *c, const WsPtrs &P, const void *links, IterJob &J)
+{
+    J.g = c->g;
+    J.links = links;
+    J.r = P.r;
+    J.q = P.q;
+    J.t = P.t;
+    J.x = P.x;
+    J.ps = P.ps;
+    J.st = P.st;
+    J.part = P.part;
+    J.ticket = P.ticket;
+    J.tile0 = 0;
+    J.ntiles = P.ntiles;
+}
+
+// Host-side initial state of a solve of (A + shifts) with source norm^2 b2.
+static void init_state(SolverState &S, double mass, const double *shifts, int n_shift, double tol_iter, double b2,
+                       int max_iter)
+{
+    memset(&S, 0, sizeof S);
+    int base = 0;
+    for (int i = 1; i < n_shift; ++i)
+        if (shifts[i] < shifts[base]) base = i;
+    S.n_shift = n_shift;
+    S.base = base;
+    S.max_iter = max_iter;
+    S.a0 = mass * mass + shifts[base];
+    const float a0h = (float)S.a0;
+    S.a0_df = make_float2(a0h, (float)(S.a0 - (double)a0h));
+    S.tol2_b2 = tol_iter * tol_iter * b2;
+    S.rho = b2;
+    S.alpha = 1.0;
+    S.beta = 0.0;
+    for (int i = 0; i < n_shift; ++i) {
+        S.shift_rel[i] = shifts[i] - shifts[base];
+        S.zeta[i] = S.zeta_prev[i] = S.zeta_new[i] = 1.0;
+        S.active_next[i] = 1;
+    }
+}
+
+// Algorithmic device bytes of one iteration (per even site) given the
+// engine, without the per-shift part.
+static double iter_bytes_base(int vp, int lf)
+{
+    const double spin = vp == VP_DF ? 48.0 : 24.0;
+    double link = 144.0;
+    if (lf == LF_F32_18) link = 72.0;
+    if (lf == LF_F32_12) link = 48.0;
+    if (lf == LF_F16_12) link = 24.0;
+    const double deo = 8 * link + 2 * spin;
+    // K1, K2 (+ p read), K3 (r, q read, r write), K4 (r read)
+    return 2 * deo + spin + 3 * spin + spin;
+}
+
+// ------------------------------------------------------------------ one engine run
+// Solve (A + shifts) y = src (engine-format source already in P.r) from
+// y = 0 to the iterated tolerance tol_iter; solutions stay in P.x.
+static int engine_mscg(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void *links, double mass,
+                       const double *shifts, int n_shift, double tol_iter, double b2, cudaStream_t s,
+                       SolverState &out_state, double &bytes)
+{
+    SolverState S;
+    init_state(S, mass, shifts, n_shift, tol_iter, b2, c->opts.max_iter);
+    LQCD_CUDA(cudaMemcpyAsync(P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
+    const long n3 = 3 * (long)c->Vh;
+    if (vp == VP_DF)
+        k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
+    else
+        k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
+    LQCD_CUDA(cudaGetLastError());
+    IterBatch<1> B;
+    memset(&B, 0, sizeof B);
+    B.njobs = 1;
+    B.tile_start[0] = 0;
+    B.tile_start[1] = P.ntiles;
+    fill_job(c, P, links, B.job[0]);
+    std::vector<int> halts;
+    int st = run_until_halt<1>(c, B, vp, lf, c->opts.check_every, c->opts.max_iter, s, halts);
+    if (st) return st;
+    LQCD_CUDA(cudaMemcpy(&out_state, P.st, sizeof out_state, cudaMemcpyDeviceToHost));
+    double shift_it = 0;
+    for (int i = 0; i < n_shift; ++i) shift_it += out_state.shift_iters[i] ? out_state.shift_iters[i] : out_state.iters;
+    const double spin = vp == VP_DF ? 48.0 : 24.0;
+    bytes += (double)c->Vh * (out_state.iters * iter_bytes_base(vp, lf) + shift_it * 4 * spin);
+    return LQCD_OK;
+}
+
+// Finish one shift to the FP64 true-residual tolerance.
+// FP64 engine: defect correction; mixed engine: CG with reliable updates.
+static int refine_shift(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void *links, double mass, double sigma,
+                        const double2 *b, double b2, double2 *x_hi, double tol, bool allow_iter, cudaStream_t s,
+                        double &resid_out, int &iters, int &reliable, double &bytes)
+{
+    const double a = mass * mass + sigma;
+    const long n3 = 3 * (long)c->Vh;
+    const double target2 = tol * tol * b2;
+    double rr;
+    int st = true_residual(c, P, vp, a, x_hi, b, P.r_hi, nullptr, 1.0, s, rr);
+    if (st) return st;
+    const double delta = c->opts.delta_reliable;
+    bool hit_max = false;
+    for (int round = 0; allow_iter && !hit_max && round < 40 && rr > target2; ++round) {
+        // new low-precision residual, scaled to O(1) entries
+        double scale = unit_scale(rr, 6.0 * c->Vh);
+        if (vp == VP_DF)
+            k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r_hi, P.r, n3, scale);
+        else
+            k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r_hi, P.r, n3, scale);
+        LQCD_CUDA(cudaGetLastError());
+        SolverState S;
+        const double rho = rr * scale * scale;
+        // iterate a little below the target so that rounding drift stays inside tol
+        const double tol_rel = std::min(0.5, 0.5 * std::sqrt(target2 / rr));
+        init_state(S, mass, &sigma, 1, tol_rel, rho, c->opts.max_iter);
+        if (vp == VP_F32) S.rel_stop2 = delta * delta * rho;
+        LQCD_CUDA(cudaMemcpyAsync(P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
+        if (vp == VP_DF)
+            k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, 1);
+        else
+            k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, 1);
+        LQCD_CUDA(cudaGetLastError());
+        IterBatch<1> B;
+        memset(&B, 0, sizeof B);
+        B.njobs = 1;
+        B.tile_start[1] = P.ntiles;
+        fill_job(c, P, links, B.job[0]);
+        for (int inner = 0; inner < 100000; ++inner) {
+            std::vector<int> halts;
+            if ((st = run_until_halt<1>(c, B, vp, lf, c->opts.check_every, c->opts.max_iter, s, halts))) return st;
+            SolverState O;
+            LQCD_CUDA(cudaMemcpy(&O, P.st, sizeof O, cudaMemcpyDeviceToHost));
+            const double spin = vp == VP_DF ? 48.0 : 24.0;
+            bytes += (double)c->Vh * ((O.iters - S.iters) * (iter_bytes_base(vp, lf) + 4 * spin));
+            iters += O.iters - S.iters;
+            S = O;
+            // x_hi += x_lo / scale
+            if (vp == VP_DF)
+                k_vec_to_ieee<VP_DF><<<nblk(n3), 256, 0, s>>>(P.x, x_hi, n3, 1.0 / scale, 1);
+            else
+                k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>(P.x, x_hi, n3, 1.0 / scale, 1);
+            LQCD_CUDA(cudaGetLastError());
+            if (O.halt == HALT_NAN) return fail(LQCD_ENAN, "NaN/Inf or breakdown in refinement");
+            if (O.halt == HALT_MAXITER) hit_max = true;
+            if (O.halt != HALT_RELIABLE) break;
+            // reliable update: FP64 true residual replaces the FP32 one
+            ++reliable;
+            const double old_scale = scale;
+            if ((st = true_residual(c, P, vp, a, x_hi, b, P.r_hi, nullptr, 1.0, s, rr))) return st;
+            if (rr <= target2) break;
+            scale = unit_scale(rr, 6.0 * c->Vh);
+            k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r_hi, P.r, n3, scale);
+            k_zero_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(P.x, n3);
+            k_scale_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(P.ps, n3, (float)(scale / old_scale));
+            LQCD_CUDA(cudaGetLastError());
+            // continue the same CG: new rho, new reliable threshold, halt cleared
+            SolverState U = O;
+            U.rho = rr * scale * scale;
+            U.rel_stop2 = delta * delta * U.rho;
+            U.tol2_b2 = target2 * scale * scale * 0.25;
+            U.halt = HALT_NONE;
+            U.do_k4 = 0;
+            LQCD_CUDA(cudaMemcpyAsync(P.st, &U, sizeof U, cudaMemcpyHostToDevice, s));
+            S = U;
+        }
+        if ((st = true_residual(c, P, vp, a, x_hi, b, P.r_hi, nullptr, 1.0, s, rr))) return st;
+    }
+    resid_out = std::sqrt(rr / b2);
+    return LQCD_OK;
+}
+
+// ------------------------------------------------------------------ public driver
+int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double2 *b,
+                   double2 *x, lqcd_solve_info *info, cudaStream_t s_user)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (!shifts || !b || !x) return fail(LQCD_EINVAL, "NULL argument");
+    if (n_shift < 1 || n_shift > LQCD_MAX_SHIFTS) return fail(LQCD_EINVAL, "n_shift must be in 1..32");
+    if (!(tol > 0.0) || !std::isfinite(mass)) return fail(LQCD_EINVAL, "tol must be > 0 and mass finite");
+    for (int i = 0; i < n_shift; ++i)
+        if (!(shifts[i] >= 0.0) || !std::isfinite(shifts[i])) return fail(LQCD_EINVAL, "shifts must be finite and >= 0");
+    if (mass * mass == 0.0) {
+        double mn = shifts[0];
+        for (int i = 1; i < n_shift; ++i) mn = std::min(mn, shifts[i]);
+        if (mn == 0.0) return fail(LQCD_EINVAL, "m^2 + min(shift) must be > 0 (A would be singular)");
+    }
+    cudaStream_t s = c->stream;
+    if (s_user && s_user != s) LQCD_CUDA(cudaStreamSynchronize(s_user));
+    const int vp = c->opts.prec == LQCD_PREC_FP64 || c->opts.prec == LQCD_PREC_FP64_NATIVE ? VP_DF : VP_F32;
+    const void *links = nullptr;
+    const int lf = link_fmt_for(c, vp == VP_DF ? LQCD_PREC_FP64 : c->opts.prec, &links);
+    WsPtrs P;
+    int st = ensure_workspace(c, vp, n_shift, P);
+    if (st) return st;
+    const long n3 = 3 * (long)c->Vh;
+    lqcd_solve_info I;
+    memset(&I, 0, sizeof I);
+    I.n_shift = n_shift;
+    double b2;
+    if ((st = norm2_ieee(c, P, b, 1, s, b2))) return st;
+    if (!std::isfinite(b2)) return fail(LQCD_ENAN, "source contains NaN/Inf");
+    if (b2 == 0.0) {
+        LQCD_CUDA(cudaMemsetAsync(x, 0, (size_t)n_shift * n3 * sizeof(double2), s));
+        LQCD_CUDA(cudaStreamSynchronize(s));
+        if (info) *info = I;
+        return LQCD_OK;
+    }
+    // 1) multi-shift iteration on the scaled source
+    const double scale = unit_scale(b2, 6.0 * c->Vh);
+    if (vp == VP_DF)
+        k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
+    else
+        k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
+    LQCD_CUDA(cudaGetLastError());
+    // FP64: iterate to half the tolerance; mixed: FP32 reaches ~1e-6 at best
+    const double tol_iter = vp == VP_DF ? 0.5 * tol : std::max(tol, 1e-6);
+    SolverState O;
+    double bytes = 0;
+    if ((st = engine_mscg(c, P, vp, lf, links, mass, shifts, n_shift, tol_iter, b2 * scale * scale, s, O, bytes))) return st;
+    I.iters = O.iters;
+    for (int i = 0; i < n_shift; ++i) I.shift_iters[i] = O.shift_iters[i];
+    const bool maxed = O.halt == HALT_MAXITER;
+    if (O.halt == HALT_NAN) return fail(LQCD_ENAN, "NaN/Inf or breakdown in the multi-shift iteration");
+    // 2) IEEE solutions, true residuals, per-shift refinement
+    for (int i = 0; i < n_shift; ++i) {
+        const size_t off = (size_t)i * n3;
+        if (vp == VP_DF)
+            k_vec_to_ieee<VP_DF><<<nblk(n3), 256, 0, s>>>((const float4 *)P.x + off, x + off, n3, 1.0 / scale, 0);
+        else
+            k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>((const float2 *)P.x + off, x + off, n3, 1.0 / scale, 0);
+        LQCD_CUDA(cudaGetLastError());
+    }
+    int status = maxed ? LQCD_ENOCONV : LQCD_OK;
+    for (int i = 0; i < n_shift; ++i) {
+        double res = 0;
+        int it = 0, rel = 0;
+        if ((st = refine_shift(c, P, vp, lf, links, mass, shifts[i], b, b2, x + (size_t)i * n3, tol, !maxed, s, res,
+                               it, rel, bytes)))
+            return st;
+        I.true_resid[i] = res;
+        I.refine_iters += it;
+        I.reliable_updates += rel;
+        if (!(res <= tol)) status = LQCD_ENOCONV;
+    }
+    LQCD_CUDA(cudaStreamSynchronize(s));
+    I.bytes_moved = bytes;
+    I.secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    I.status = status;
+    if (info) *info = I;
+    if (status == LQCD_ENOCONV) set_error("solver did not reach tol within max_iter");
+    return status;
+}
+
+int mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, const double *const *shifts,
+                      const int *n_shift, const double *tol, const double *const *b, double *const *x,
+                      lqcd_solve_info *info)
+{
+    (void)ctxs; (void)n; (void)mass; (void)shifts; (void)n_shift; (void)tol; (void)b; (void)x; (void)info;
+    return fail(LQCD_EINVAL, "packed solve not built yet");
+}
+
+}  // namespace lqcd

@@ -1,0 +1,328 @@
+// solver_kernels.cuh -- iteration kernels of the multi-shift CG (Sec. 2.2,
+// Eqs. lineqeo and shlineq) for df64 ("FP64") and FP32 Krylov vectors.
+//
+// One iteration = four launches, each tiled over every job of the batch
+// (a job = one lattice / one request with its own device scalars):
+//   K1  t = D_oe p                                   (deo, odd output)
+//   K2  q = (m^2 + sigma_b) p - D_eo t, <p, q>      (deo + fused epilogue);
+//       the last tile to finish computes alpha and the shifted zeta_i,
+//       alpha_i (one thread, FP64)
+//   K3  r -= alpha q, ||r||^2; last tile: beta, beta_i, convergence per shift
+//   K4  for every active shift: x_i += alpha_i p_i; p_i = zeta_i r + beta_i p_i
+// The base direction p is the direction of the smallest shift (its zeta is 1).
+// Reductions are deterministic: per-thread df64 partials, fixed-order warp
+// and block trees, per-tile doubles summed in tile order by the last block
+// (ticket counter), so a job's result does not depend on what else is in the
+// batch.
+#pragma once
+
+#include "deo_core.cuh"
+#include "internal.h"
+
+namespace lqcd {
+
+template <int NJ>
+__device__ __forceinline__ int find_job(const IterBatch<NJ> &B)
+{
+    int j = 0;
+    if (NJ > 1) {
+#pragma unroll 1
+        while (j + 1 < B.njobs && (int)blockIdx.x >= B.tile_start[j + 1]) ++j;
+    }
+    return j;
+}
+
+// Sum per-tile partials in tile order and hand the total to fn (thread 0 of
+// the last block to finish).  Every block of the reduction must call this.
+template <class Fn>
+__device__ __forceinline__ void reduce_finish(double *part, unsigned *ticket, int ntiles, int tile, double v, Fn fn)
+{
+    __shared__ int s_last;
+    __shared__ double s_red[kTile / 32];
+    if (threadIdx.x == 0) {
+        part[tile] = v;
+        __threadfence();
+        const unsigned prev = atomicAdd(ticket, 1u);
+        s_last = (prev == (unsigned)(ntiles - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int k = threadIdx.x; k < ntiles; k += kTile) s += __ldcg(part + k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+#pragma unroll
+        for (int k = 0; k < kTile / 32; ++k) tot += s_red[k];
+        fn(tot);
+        *ticket = 0u;
+        __threadfence();
+    }
+}
+
+template <class Fn>
+__device__ __forceinline__ void tile_finish(const IterJob &J, int tile, double v, Fn fn)
+{
+    reduce_finish(J.part, J.ticket, J.ntiles, tile, v, fn);
+}
+
+__device__ __forceinline__ float2 split_scalar(double d)
+{
+    const float h = __double2float_rn(d);
+    return make_float2(h, __double2float_rn(d - (double)h));
+}
+
+// alpha and the shifted coefficients (FP64, one thread).
+__device__ inline void finalize_pq(SolverState *st, double pq)
+{
+    st->last_sum = pq;
+    st->alpha_prev = st->alpha;
+    st->beta_prev = st->beta;
+    int n_act = 0;
+    for (int s = 0; s < st->n_shift; ++s) {
+        if (!st->active_next[s]) continue;
+        st->zeta_prev[s] = st->zeta[s];
+        st->zeta[s] = st->zeta_new[s];
+        st->act_list[n_act++] = s;
+    }
+    st->n_act = n_act;
+    const double alpha = st->rho / pq;
+    if (!(pq > 0.0) || !isfinite(alpha)) {
+        st->halt = HALT_NAN;
+        st->nan_flag = 1;
+        return;
+    }
+    st->alpha = alpha;
+    st->alpha_df = split_scalar(alpha);
+    for (int k = 0; k < n_act; ++k) {
+        const int s = st->act_list[k];
+        const double z = st->zeta[s], zp = st->zeta_prev[s];
+        const double den = alpha * st->beta_prev * (zp - z) + zp * st->alpha_prev * (1.0 + st->shift_rel[s] * alpha);
+        const double zn = z * zp * st->alpha_prev / den;
+        st->zeta_new[s] = zn;
+        st->zeta_new_df[s] = split_scalar(zn);
+        st->alpha_s_df[s] = split_scalar(alpha * zn / z);
+    }
+}
+
+// beta, beta_i and the stopping decisions (FP64, one thread).
+__device__ inline void finalize_rr(SolverState *st, double rr)
+{
+    st->last_sum = rr;
+    if (!isfinite(rr)) {
+        st->halt = HALT_NAN;
+        st->nan_flag = 1;
+        return;
+    }
+    const double beta = rr / st->rho;
+    st->beta = beta;
+    st->rho = rr;
+    st->iters += 1;
+    int any = 0;
+    for (int k = 0; k < st->n_act; ++k) {
+        const int s = st->act_list[k];
+        const double ratio = st->zeta_new[s] / st->zeta[s];
+        st->beta_s_df[s] = split_scalar(beta * ratio * ratio);
+        const double zn = st->zeta_new[s];
+        const bool conv = zn * zn * rr <= st->tol2_b2;
+        if (conv && st->shift_iters[s] == 0) st->shift_iters[s] = st->iters;
+        st->active_next[s] = conv ? 0 : 1;
+        any |= !conv;
+    }
+    // the base direction must keep moving while any shift still iterates
+    if (any) st->active_next[st->base] = 1;
+    st->do_k4 = 1;
+    if (!any)
+        st->halt = HALT_CONVERGED;
+    else if (st->rel_stop2 > 0.0 && rr < st->rel_stop2)
+        st->halt = HALT_RELIABLE;
+    else if (st->iters >= st->max_iter)
+        st->halt = HALT_MAXITER;
+}
+
+// ------------------------------------------------------------------ vector element helpers
+template <int VP> struct VecT;
+template <> struct VecT<VP_DF> { using T = float4; };
+template <> struct VecT<VP_F32> { using T = float2; };
+
+// ------------------------------------------------------------------ K1
+template <int NJ, int VP, int LF>
+__global__ void __launch_bounds__(kTile, 2) k_it_deo1(const __grid_constant__ IterBatch<NJ> B)
+{
+    using T = typename VecT<VP>::T;
+    const int j = find_job(B);
+    const IterJob &J = B.job[j];
+    SolverState *st = J.st;
+    if ((int)blockIdx.x == B.tile_start[j] && threadIdx.x == 0) st->do_k4 = 0;
+    if (st->halt) return;
+    const int Vh = J.g.Vh;
+    const int i = ((int)blockIdx.x - B.tile_start[j]) * kTile + threadIdx.x;
+    if (i >= Vh) return;
+    const T *p = (const T *)J.ps + (size_t)st->base * 3 * Vh;
+    T *t = (T *)J.t;
+    Stencil S;
+    make_stencil(J.g, i, 1, S);
+    if constexpr (VP == VP_DF) {
+        float2 res[6];
+        bool bad = false;
+        deo_site_df<SF_DF>(J.g, (const float4 *)J.links, p, S, i, 1, Vh, res, bad);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t[(size_t)c * Vh + i] = make_float4(res[2 * c].x, res[2 * c].y, res[2 * c + 1].x, res[2 * c + 1].y);
+    } else {
+        float2 o[3];
+        deo_site_f32<LF>(J.g, J.links, p, S, i, 1, Vh, o);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) t[(size_t)c * Vh + i] = o[c];
+    }
+}
+
+// ------------------------------------------------------------------ K2
+template <int NJ, int VP, int LF>
+__global__ void __launch_bounds__(kTile, 2) k_it_deo2(const __grid_constant__ IterBatch<NJ> B)
+{
+    using T = typename VecT<VP>::T;
+    __shared__ double s_red[kTile / 32];
+    const int j = find_job(B);
+    const IterJob &J = B.job[j];
+    SolverState *st = J.st;
+    if (st->halt) return;
+    const int Vh = J.g.Vh;
+    const int tile = (int)blockIdx.x - B.tile_start[j];
+    const int i = tile * kTile + threadIdx.x;
+    Acc2 dot;
+    acc_zero(dot);
+    if (i < Vh) {
+        const T *p = (const T *)J.ps + (size_t)st->base * 3 * Vh;
+        T *q = (T *)J.q;
+        Stencil S;
+        make_stencil(J.g, i, 0, S);
+        if constexpr (VP == VP_DF) {
+            float2 res[6];
+            bool bad = false;
+            deo_site_df<SF_DF>(J.g, (const float4 *)J.links, J.t, S, i, 0, Vh, res, bad);
+            const float2 a = st->a0_df;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float4 pv = p[(size_t)c * Vh + i];
+                const float2 qr = df_fma(a, make_float2(pv.x, pv.y), df_neg(res[2 * c]));
+                const float2 qi = df_fma(a, make_float2(pv.z, pv.w), df_neg(res[2 * c + 1]));
+                q[(size_t)c * Vh + i] = make_float4(qr.x, qr.y, qi.x, qi.y);
+                acc_prod(dot, pv.x, pv.y, qr.x, qr.y);
+                acc_prod(dot, pv.z, pv.w, qi.x, qi.y);
+            }
+        } else {
+            float2 o[3];
+            deo_site_f32<LF>(J.g, J.links, (const float2 *)J.t, S, i, 0, Vh, o);
+            const float a = st->a0_df.x;
+            float d = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 pv = p[(size_t)c * Vh + i];
+                const float2 qv = make_float2(__fmaf_rn(a, pv.x, -o[c].x), __fmaf_rn(a, pv.y, -o[c].y));
+                q[(size_t)c * Vh + i] = qv;
+                d = __fmaf_rn(pv.x, qv.x, __fmaf_rn(pv.y, qv.y, d));
+            }
+            dot.s = d;
+        }
+    }
+    const double v = block_reduce_acc<kTile>(dot, s_red);
+    tile_finish(J, tile, v, [&](double tot) { finalize_pq(st, tot); });
+}
+
+// ------------------------------------------------------------------ K3
+template <int NJ, int VP>
+__global__ void __launch_bounds__(kTile) k_it_upd_r(const __grid_constant__ IterBatch<NJ> B)
+{
+    using T = typename VecT<VP>::T;
+    __shared__ double s_red[kTile / 32];
+    const int j = find_job(B);
+    const IterJob &J = B.job[j];
+    SolverState *st = J.st;
+    if (st->halt) return;
+    const int Vh = J.g.Vh;
+    const int tile = (int)blockIdx.x - B.tile_start[j];
+    const int i = tile * kTile + threadIdx.x;
+    Acc2 nrm;
+    acc_zero(nrm);
+    if (i < Vh) {
+        T *r = (T *)J.r;
+        const T *q = (const T *)J.q;
+        if constexpr (VP == VP_DF) {
+            const float2 na = df_neg(st->alpha_df);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float4 rv = r[(size_t)c * Vh + i], qv = q[(size_t)c * Vh + i];
+                const float2 a = df_fma(na, make_float2(qv.x, qv.y), make_float2(rv.x, rv.y));
+                const float2 b = df_fma(na, make_float2(qv.z, qv.w), make_float2(rv.z, rv.w));
+                r[(size_t)c * Vh + i] = make_float4(a.x, a.y, b.x, b.y);
+                acc_prod(nrm, a.x, a.y, a.x, a.y);
+                acc_prod(nrm, b.x, b.y, b.x, b.y);
+            }
+        } else {
+            const float na = -st->alpha_df.x;
+            float d = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 rv = r[(size_t)c * Vh + i], qv = q[(size_t)c * Vh + i];
+                const float2 o = make_float2(__fmaf_rn(na, qv.x, rv.x), __fmaf_rn(na, qv.y, rv.y));
+                r[(size_t)c * Vh + i] = o;
+                d = __fmaf_rn(o.x, o.x, __fmaf_rn(o.y, o.y, d));
+            }
+            nrm.s = d;
+        }
+    }
+    const double v = block_reduce_acc<kTile>(nrm, s_red);
+    tile_finish(J, tile, v, [&](double tot) { finalize_rr(st, tot); });
+}
+
+// ------------------------------------------------------------------ K4
+template <int NJ, int VP>
+__global__ void __launch_bounds__(kTile) k_it_upd_shifts(const __grid_constant__ IterBatch<NJ> B)
+{
+    using T = typename VecT<VP>::T;
+    const int j = find_job(B);
+    const IterJob &J = B.job[j];
+    const SolverState *st = J.st;
+    if (!st->do_k4) return;
+    const int Vh = J.g.Vh;
+    const int i = ((int)blockIdx.x - B.tile_start[j]) * kTile + threadIdx.x;
+    if (i >= Vh) return;
+    const T *r = (const T *)J.r;
+    T *x = (T *)J.x, *ps = (T *)J.ps;
+    T rv[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) rv[c] = r[(size_t)c * Vh + i];
+    const int n_act = st->n_act;
+#pragma unroll 1
+    for (int k = 0; k < n_act; ++k) {
+        const int s = st->act_list[k];
+        const size_t off = (size_t)s * 3 * Vh + i;
+        if constexpr (VP == VP_DF) {
+            const float2 as = st->alpha_s_df[s], zn = st->zeta_new_df[s], bs = st->beta_s_df[s];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float4 pv = ps[off + (size_t)c * Vh], xv = x[off + (size_t)c * Vh];
+                const float2 xr = df_fma(as, make_float2(pv.x, pv.y), make_float2(xv.x, xv.y));
+                const float2 xi = df_fma(as, make_float2(pv.z, pv.w), make_float2(xv.z, xv.w));
+                const float2 pr = df_mul2(zn, make_float2(rv[c].x, rv[c].y), bs, make_float2(pv.x, pv.y));
+                const float2 pi = df_mul2(zn, make_float2(rv[c].z, rv[c].w), bs, make_float2(pv.z, pv.w));
+                x[off + (size_t)c * Vh] = make_float4(xr.x, xr.y, xi.x, xi.y);
+                ps[off + (size_t)c * Vh] = make_float4(pr.x, pr.y, pi.x, pi.y);
+            }
+        } else {
+            const float as = st->alpha_s_df[s].x, zn = st->zeta_new_df[s].x, bs = st->beta_s_df[s].x;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 pv = ps[off + (size_t)c * Vh], xv = x[off + (size_t)c * Vh];
+                x[off + (size_t)c * Vh] = make_float2(__fmaf_rn(as, pv.x, xv.x), __fmaf_rn(as, pv.y, xv.y));
+                ps[off + (size_t)c * Vh] = make_float2(__fmaf_rn(zn, rv[c].x, bs * pv.x), __fmaf_rn(zn, rv[c].y, bs * pv.y));
+            }
+        }
+    }
+}
+
+}  // namespace lqcd

@@ -1,0 +1,314 @@
+"""ctypes binding of liblqcd.so (the C ABI in include/lqcd.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  The raw entry points keep their C names (``lqcd_create``,
+``lqcd_deo_apply``, ``lqcd_mscg_solve`` ...); ``Context`` and ``Server`` wrap
+them with numpy / torch arguments and raise ``LqcdError`` on a non-zero
+status.  Loading fails loudly when the library is missing: there is no CPU
+fallback.
+
+Device spinors are torch tensors in the library's structure-of-arrays layout:
+complex128 (or complex64 for FP32/FP16 calls) of shape ``[3, Vh]`` (one
+field) or ``[n, 3, Vh]`` (several fields); ``to_device_spinor`` /
+``from_device_spinor`` convert from / to the canonical host ``[Vh, 3]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblqcd.so")
+
+LQCD_OK = 0
+LQCD_EINVAL = -1
+LQCD_ENOMEM = -2
+LQCD_ENOCONV = -3
+LQCD_ENAN = -4
+LQCD_EBUSY = -5
+LQCD_ENOTREADY = -6
+LQCD_ETIMEOUT = -7
+LQCD_ECUDA = -8
+LQCD_ESTATE = -9
+STATUS_NAMES = {0: "LQCD_OK", -1: "LQCD_EINVAL", -2: "LQCD_ENOMEM", -3: "LQCD_ENOCONV", -4: "LQCD_ENAN",
+                -5: "LQCD_EBUSY", -6: "LQCD_ENOTREADY", -7: "LQCD_ETIMEOUT", -8: "LQCD_ECUDA",
+                -9: "LQCD_ESTATE"}
+
+PREC_FP64, PREC_FP32, PREC_FP16, PREC_FP64_NATIVE = 0, 1, 2, 3
+MAX_SHIFTS = 32
+
+# Every symbol include/lqcd.h declares (checked by the CPU tests).
+EXPORTED = [
+    "lqcd_default_opts", "lqcd_last_error", "lqcd_version", "lqcd_create", "lqcd_destroy",
+    "lqcd_set_opts", "lqcd_device_bytes", "lqcd_links_upload", "lqcd_links_download",
+    "lqcd_deo_apply", "lqcd_deo_apply_ex", "lqcd_deo_apply_mrhs", "lqcd_mscg_solve",
+    "lqcd_mscg_solve_dev", "lqcd_cg_solve_mrhs", "lqcd_mscg_solve_packed",
+    "lqcd_serve_create", "lqcd_serve_register_field", "lqcd_serve_submit", "lqcd_serve_poll",
+    "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy",
+]
+
+
+class lqcd_opts(ctypes.Structure):
+    _fields_ = [("prec", ctypes.c_int), ("recon", ctypes.c_int), ("delta_reliable", ctypes.c_double),
+                ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int)]
+
+
+class lqcd_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("n_shift", ctypes.c_int), ("reliable_updates", ctypes.c_int),
+                ("refine_iters", ctypes.c_int), ("shift_iters", ctypes.c_int * MAX_SHIFTS),
+                ("true_resid", ctypes.c_double * MAX_SHIFTS), ("secs", ctypes.c_double),
+                ("bytes_moved", ctypes.c_double), ("status", ctypes.c_int)]
+
+    def as_dict(self) -> dict:
+        n = self.n_shift
+        return {"iters": self.iters, "n_shift": n, "reliable_updates": self.reliable_updates,
+                "refine_iters": self.refine_iters, "shift_iters": list(self.shift_iters)[:n],
+                "true_resid": list(self.true_resid)[:n], "secs": self.secs,
+                "bytes_moved": self.bytes_moved, "status": self.status}
+
+
+class lqcd_serve_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64), ("rejected", ctypes.c_uint64),
+                ("active_slots", ctypes.c_int), ("queued", ctypes.c_int), ("hbm_in_use", ctypes.c_size_t),
+                ("hbm_budget", ctypes.c_size_t), ("p50_latency", ctypes.c_double),
+                ("p99_latency", ctypes.c_double), ("mean_latency", ctypes.c_double),
+                ("solves_per_sec", ctypes.c_double), ("ticks", ctypes.c_uint64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LqcdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load liblqcd.so (build it first with paper_1701_00426_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"liblqcd.so not found at {p}: run paper_1701_00426_gb300.build.build() "
+                          f"(the CUDA library is required; there is no CPU fallback)")
+    lib = ctypes.CDLL(p)
+    vp, ip, dp, sz = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), ctypes.c_size_t
+    sig = {
+        "lqcd_default_opts": (None, [ctypes.POINTER(lqcd_opts)]),
+        "lqcd_last_error": (ctypes.c_char_p, []),
+        "lqcd_version": (ctypes.c_int, []),
+        "lqcd_create": (ctypes.c_int, [ip, ctypes.POINTER(lqcd_opts), ctypes.POINTER(vp)]),
+        "lqcd_destroy": (None, [vp]),
+        "lqcd_set_opts": (ctypes.c_int, [vp, ctypes.POINTER(lqcd_opts)]),
+        "lqcd_device_bytes": (sz, [vp]),
+        "lqcd_links_upload": (ctypes.c_int, [vp, vp, sz]),
+        "lqcd_links_download": (ctypes.c_int, [vp, vp, sz]),
+        "lqcd_deo_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
+        "lqcd_deo_apply_ex": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]),
+        "lqcd_deo_apply_mrhs": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]),
+        "lqcd_mscg_solve": (ctypes.c_int, [vp, ctypes.c_double, dp, ctypes.c_int, ctypes.c_double, vp, vp,
+                                           ctypes.POINTER(lqcd_solve_info)]),
+        "lqcd_mscg_solve_dev": (ctypes.c_int, [vp, ctypes.c_double, dp, ctypes.c_int, ctypes.c_double, vp, vp,
+                                               ctypes.POINTER(lqcd_solve_info), vp]),
+        "lqcd_cg_solve_mrhs": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                              ctypes.c_double, vp, vp, ctypes.POINTER(lqcd_solve_info)]),
+        "lqcd_mscg_solve_packed": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.POINTER(dp), ip,
+                                                  dp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                                  ctypes.POINTER(lqcd_solve_info)]),
+        "lqcd_serve_create": (ctypes.c_int, [sz, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]),
+        "lqcd_serve_register_field": (ctypes.c_int, [vp, ip, vp, sz, ip]),
+        "lqcd_serve_submit": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, dp, ctypes.c_int,
+                                             ctypes.c_double, vp, ctypes.POINTER(ctypes.c_uint64)]),
+        "lqcd_serve_poll": (ctypes.c_int, [vp, ctypes.c_uint64, vp, ctypes.POINTER(lqcd_solve_info)]),
+        "lqcd_serve_drain": (ctypes.c_int, [vp, ctypes.c_double]),
+        "lqcd_serve_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(lqcd_serve_stats)]),
+        "lqcd_serve_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def check(status: int) -> int:
+    if status not in (LQCD_OK,):
+        msg = _lib.lqcd_last_error().decode() if _lib else ""
+        raise LqcdError(status, msg)
+    return status
+
+
+def default_opts(**kw) -> lqcd_opts:
+    o = lqcd_opts()
+    load().lqcd_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _c128(a, shape) -> np.ndarray:
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    return a.reshape(shape)
+
+
+def _dptr(t) -> int:
+    """Device pointer of a contiguous CUDA torch tensor."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("device arguments must be contiguous CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def to_device_spinor(a: np.ndarray, dtype=None, device="cuda"):
+    """Canonical host [..., Vh, 3] -> device structure of arrays [..., 3, Vh]."""
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(np.swapaxes(a, -1, -2)))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(device).contiguous()
+
+
+def from_device_spinor(t) -> np.ndarray:
+    """Device [..., 3, Vh] -> canonical host [..., Vh, 3] complex128."""
+    a = t.detach().cpu().numpy()
+    return np.ascontiguousarray(np.swapaxes(a, -1, -2)).astype(np.complex128)
+
+
+class Context:
+    """One lattice on the current CUDA device (wraps lqcd_ctx)."""
+
+    def __init__(self, dims, opts: lqcd_opts | None = None, **kw):
+        self.lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.V = int(np.prod(self.dims))
+        self.Vh = self.V // 2
+        o = opts if opts is not None else default_opts(**kw)
+        h = ctypes.c_void_p()
+        check(self.lib.lqcd_create((ctypes.c_int * 4)(*self.dims), ctypes.byref(o), ctypes.byref(h)))
+        self.h = h
+        self.opts = o
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lqcd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_opts(self, **kw):
+        for k, v in kw.items():
+            setattr(self.opts, k, v)
+        check(self.lib.lqcd_set_opts(self.h, ctypes.byref(self.opts)))
+
+    def device_bytes(self) -> int:
+        return int(self.lib.lqcd_device_bytes(self.h))
+
+    # ------------------------------------------------------------- links
+    def links_upload(self, links: np.ndarray):
+        u = _c128(links, (4, self.V, 3, 3))
+        check(self.lib.lqcd_links_upload(self.h, _ptr(u), u.size * 2))
+
+    def links_download(self) -> np.ndarray:
+        u = np.empty((4, self.V, 3, 3), np.complex128)
+        check(self.lib.lqcd_links_download(self.h, _ptr(u), u.size * 2))
+        return u
+
+    # --------------------------------------------------------------- D_eo
+    def deo_apply(self, out_parity: int, inp: np.ndarray) -> np.ndarray:
+        """Host call: canonical [Vh, 3] complex128 in and out."""
+        a = _c128(inp, (self.Vh, 3))
+        out = np.empty_like(a)
+        check(self.lib.lqcd_deo_apply(self.h, int(out_parity), _ptr(a), _ptr(out), 0, None))
+        return out
+
+    def deo_apply_dev(self, out_parity: int, inp, out, stream=None):
+        """Device call (FP64): complex128 [3, Vh] tensors."""
+        check(self.lib.lqcd_deo_apply(self.h, int(out_parity), _dptr(inp), _dptr(out), 1, _stream_ptr(stream)))
+
+    def deo_apply_ex(self, out_parity: int, prec: int, recon: int, inp, out, stream=None):
+        check(self.lib.lqcd_deo_apply_ex(self.h, int(out_parity), int(prec), int(recon), _dptr(inp), _dptr(out),
+                                         _stream_ptr(stream)))
+
+    def deo_apply_mrhs(self, out_parity: int, n_rhs: int, recon: int, inp, out, stream=None):
+        check(self.lib.lqcd_deo_apply_mrhs(self.h, int(out_parity), int(n_rhs), int(recon), _dptr(inp),
+                                           _dptr(out), _stream_ptr(stream)))
+
+    # ------------------------------------------------------------- solvers
+    def mscg_solve(self, mass: float, shifts, tol: float, b: np.ndarray, allow_noconv: bool = False):
+        """Host call: returns (x [n_shift, Vh, 3], info dict)."""
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        bb = _c128(b, (self.Vh, 3))
+        x = np.empty((sh.size, self.Vh, 3), np.complex128)
+        info = lqcd_solve_info()
+        st = self.lib.lqcd_mscg_solve(self.h, float(mass), sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                      sh.size, float(tol), _ptr(bb), _ptr(x), ctypes.byref(info))
+        if not (allow_noconv and st == LQCD_ENOCONV):
+            check(st)
+        return x, info.as_dict()
+
+    def mscg_solve_dev(self, mass: float, shifts, tol: float, b, x, stream=None, allow_noconv=False):
+        """Device call: b complex128 [3, Vh], x complex128 [n_shift, 3, Vh]."""
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        info = lqcd_solve_info()
+        st = self.lib.lqcd_mscg_solve_dev(self.h, float(mass), sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                          sh.size, float(tol), _dptr(b), _dptr(x), ctypes.byref(info),
+                                          _stream_ptr(stream))
+        if not (allow_noconv and st == LQCD_ENOCONV):
+            check(st)
+        return info.as_dict()
+
+    def cg_solve_mrhs(self, mass: float, sigma: float, tol: float, b: np.ndarray):
+        """Host call: b [n_rhs, Vh, 3]; returns (x, [info per rhs])."""
+        bb = np.ascontiguousarray(b, dtype=np.complex128)
+        n = bb.shape[0]
+        x = np.empty_like(bb)
+        infos = (lqcd_solve_info * n)()
+        check(self.lib.lqcd_cg_solve_mrhs(self.h, float(mass), float(sigma), n, float(tol), _ptr(bb), _ptr(x),
+                                          infos))
+        return x, [i.as_dict() for i in infos]
+
+
+def mscg_solve_packed(ctxs, masses, shifts_list, tols, bs):
+    """One multi-shift solve per context, all advanced in shared launches."""
+    lib = load()
+    n = len(ctxs)
+    hs = (ctypes.c_void_p * n)(*[c.h for c in ctxs])
+    ms = (ctypes.c_double * n)(*[float(m) for m in masses])
+    sh_arr = [np.ascontiguousarray(s, dtype=np.float64) for s in shifts_list]
+    shp = (ctypes.POINTER(ctypes.c_double) * n)(*[a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in sh_arr])
+    ns = (ctypes.c_int * n)(*[a.size for a in sh_arr])
+    ts = (ctypes.c_double * n)(*[float(t) for t in tols])
+    b_arr = [_c128(b, (c.Vh, 3)) for c, b in zip(ctxs, bs)]
+    x_arr = [np.empty((a.size, c.Vh, 3), np.complex128) for a, c in zip(sh_arr, ctxs)]
+    bp = (ctypes.c_void_p * n)(*[_ptr(a) for a in b_arr])
+    xp = (ctypes.c_void_p * n)(*[_ptr(a) for a in x_arr])
+    infos = (lqcd_solve_info * n)()
+    check(lib.lqcd_mscg_solve_packed(hs, n, ms, shp, ns, ts, bp, xp, infos))
+    return x_arr, [i.as_dict() for i in infos]

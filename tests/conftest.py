@@ -20,3 +20,16 @@ def pytest_configure(config):
 def orc():
     from oracle import oracle
     return oracle()
+
+
+@pytest.fixture(scope="session")
+def gpu():
+    """Builds liblqcd.so, loads the binding and checks that a GPU is present."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("this test needs a CUDA GPU (run with -m 'not gpu' on CPU)")
+    from paper_1701_00426_gb300 import build, lqcd
+    build.build()
+    lqcd.load()
+    torch.cuda.init()
+    return lqcd

@@ -1,0 +1,100 @@
+"""The C-ABI library loads and exports every symbol include/lqcd.h declares
+(CPU only: no compute call is made)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "lqcd.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lqcd_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1701_00426_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_expected_api():
+    syms = declared_symbols()
+    from paper_1701_00426_gb300 import lqcd
+    assert sorted(lqcd.EXPORTED) == syms
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_symbols():
+        assert hasattr(lib, name), f"{name} missing from liblqcd.so"
+
+
+def test_binding_loads_and_reports_version(lib):
+    from paper_1701_00426_gb300 import lqcd
+    L = lqcd.load()
+    assert L.lqcd_version() >= 100
+    o = lqcd.default_opts()
+    assert o.prec == lqcd.PREC_FP64 and o.recon == 18 and o.max_iter == 20000
+
+
+def test_create_rejects_odd_sides_without_gpu(lib):
+    """Argument checks run before any CUDA call."""
+    from paper_1701_00426_gb300 import lqcd
+    L = lqcd.load()
+    h = ctypes.c_void_p()
+    st = L.lqcd_create((ctypes.c_int * 4)(4, 4, 3, 4), None, ctypes.byref(h))
+    assert st == lqcd.LQCD_EINVAL
+    assert b"even" in L.lqcd_last_error()
+    o = lqcd.default_opts(recon=7)
+    st = L.lqcd_create((ctypes.c_int * 4)(4, 4, 4, 4), ctypes.byref(o), ctypes.byref(h))
+    assert st == lqcd.LQCD_EINVAL
+
+
+def test_no_oracle_in_product_path():
+    """The product package never imports or links the oracle."""
+    pkg = os.path.join(ROOT, "paper_1701_00426_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(from|import)\s+oracle|liboracle|lqcd_oracle|oracle_[a-z]+\(",
+                                     text, flags=re.M), f
+
+
+def test_fastdiv_host_matches_integer_division():
+    """The magic-number division used for site decoding (compiled as host C++)."""
+    import subprocess
+    import tempfile
+    code = r'''
+#include <cstdio>
+#include <cstdint>
+#define __host__
+#define __device__
+#define __forceinline__ inline
+struct float2 {float x, y;}; struct float4 {float x, y, z, w;};
+''' + open(os.path.join(ROOT, "paper_1701_00426_gb300", "csrc", "common.cuh")).read().split(
+        "// ------------------------------------------------------------------ df64 primitives")[0].split(
+        "namespace lqcd {", 1)[1] + r'''
+int main() {
+  uint32_t ds[] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 20, 24, 30, 32, 36, 48, 64, 100, 1000};
+  uint64_t bad = 0;
+  for (uint32_t d : ds) {
+    FastDiv f = make_fastdiv(d);
+    for (uint32_t n = 0; n < 3000000; n += 7) if (fdiv(n, f) != n / d) ++bad;
+    for (uint32_t n = 2147483647u; n > 2147000000u; n -= 13) if (fdiv(n, f) != n / d) ++bad;
+  }
+  printf("%llu\n", (unsigned long long)bad);
+  return bad != 0;
+}
+'''
+    with tempfile.TemporaryDirectory() as td:
+        src = os.path.join(td, "t.cpp")
+        open(src, "w").write(code)
+        exe = os.path.join(td, "t")
+        subprocess.run(["g++", "-std=c++17", "-O1", src, "-o", exe], check=True, capture_output=True)
+        r = subprocess.run([exe], capture_output=True, text=True)
+        assert r.returncode == 0 and r.stdout.strip() == "0"

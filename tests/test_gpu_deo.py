@@ -1,0 +1,175 @@
+"""D_eo / D_oe on the GPU against the FP64 CPU oracle (through the C ABI).
+
+Bar: FP64 within 1e-13 relative, normwise and element-wise against the
+largest reference element; FP32 / FP16 within the bounds their rounding
+allows (stated at each test)."""
+import numpy as np
+import pytest
+import torch
+
+import pins
+from paper_1701_00426_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-13
+
+
+def errs(got, ref):
+    d = np.abs(np.asarray(got) - np.asarray(ref))
+    return float(np.linalg.norm(d) / np.linalg.norm(ref)), float(d.max() / np.abs(ref).max())
+
+
+def check_fp64(got, ref, tol=FP64_TOL):
+    n, m = errs(got, ref)
+    assert n <= tol and m <= tol, f"normwise {n:.2e}, elementwise {m:.2e} > {tol}"
+    return n, m
+
+
+DIMS = [(2, 2, 2, 2), (4, 4, 4, 4), (4, 6, 8, 10), (6, 6, 6, 6), (8, 8, 8, 8), (10, 4, 6, 12), (16, 16, 16, 16)]
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("parity", [0, 1])
+def test_deo_fp64_host_call_matches_oracle(gpu, orc, dims, parity):
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=parity)
+    ref = orc.deo(dims, parity, U, x)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        got = c.deo_apply(parity, x)
+    check_fp64(got, ref)
+
+
+@pytest.mark.parametrize("dims", [(4, 6, 8, 10), (8, 8, 8, 8)])
+def test_deo_native_fp64_matches_oracle(gpu, orc, dims):
+    U = inputs.random_links(dims)
+    for parity in (0, 1):
+        x = inputs.gaussian_field(dims, k=5 + parity)
+        ref = orc.deo(dims, parity, U, x)
+        with gpu.Context(dims) as c:
+            c.links_upload(U)
+            xin = gpu.to_device_spinor(x)
+            out = torch.empty_like(xin)
+            c.deo_apply_ex(parity, gpu.PREC_FP64_NATIVE, 18, xin, out)
+            torch.cuda.synchronize()
+            n, m = errs(gpu.from_device_spinor(out), ref)
+        assert n <= 1e-15 and m <= 1e-15
+
+
+def test_deo_device_call_equals_host_call(gpu):
+    dims = (4, 6, 8, 10)
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=2)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        h = c.deo_apply(0, x)
+        xin = gpu.to_device_spinor(x)
+        out = torch.empty_like(xin)
+        c.deo_apply_dev(0, xin, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(gpu.from_device_spinor(out), h)
+
+
+@pytest.mark.parametrize("scale", [1e-80, 1e-25, 1e30, 1e90])
+def test_deo_fp64_extreme_magnitudes(gpu, orc, scale):
+    """Inputs outside the double-float exponent window take the native path."""
+    dims = (4, 4, 4, 6)
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=9) * scale
+    ref = orc.deo(dims, 0, U, x)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        got = c.deo_apply(0, x)
+    check_fp64(got, ref)
+
+
+def test_deo_fp64_sparse_and_mixed_scale_input(gpu, orc):
+    """Point source (exact zeros) and entries spanning 1e-70 .. 1e40."""
+    dims = (4, 4, 6, 8)
+    U = inputs.random_links(dims)
+    Vh = int(np.prod(dims)) // 2
+    x = np.zeros((Vh, 3), np.complex128)
+    x[17, 1] = 1.0 + 0.5j
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        check_fp64(c.deo_apply(1, x), orc.deo(dims, 1, U, x))
+        rng = np.random.default_rng(3)
+        y = inputs.gaussian_field(dims, k=1) * 10.0 ** rng.uniform(-70, 40, size=(Vh, 1))
+        check_fp64(c.deo_apply(1, y), orc.deo(dims, 1, U, y))
+
+
+def test_deo_gpu_antihermitian(gpu):
+    """Eq. (diracblock) on GPU results alone: <y, D_eo x> = -<D_oe y, x>."""
+    dims = (8, 8, 8, 8)
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=1)
+    y = inputs.gaussian_field(dims, k=2)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        Dx = c.deo_apply(0, x)
+        Dy = c.deo_apply(1, y)
+    lhs, rhs = np.vdot(y, Dx), -np.vdot(Dy, x)
+    assert abs(lhs - rhs) / (np.linalg.norm(y) * np.linalg.norm(Dx)) < 1e-14
+
+
+def test_deo_gpu_free_field_plane_wave(gpu):
+    dims = (4, 6, 8, 10)
+    U = inputs.unit_links(dims)
+    chi = np.array([0.3 + 0.1j, -0.7j, 1.1])
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        for k in [(1, 2, 3, 4), (3, 1, 5, 9)]:
+            psi = pins.plane_wave_even(dims, k, chi)
+            lam = pins.free_eigenvalue(dims, k, 0.1)
+            t = c.deo_apply(1, psi)
+            A = (0.1 ** 2) * psi - c.deo_apply(0, t)
+            assert pins.rel(A, lam * psi) < 1e-13
+
+
+@pytest.mark.parametrize("prec,recon,tol", [(1, 18, 2e-6), (1, 12, 5e-6), (2, 12, 5e-3)])
+def test_deo_low_precision_bounds(gpu, orc, prec, recon, tol):
+    """FP32: inputs rounded to 2^-24, 48 products -> ~1e-6 relative.
+    FP16 links: rounding 2^-11 plus the rebuilt third row -> ~1e-3."""
+    dims = (8, 8, 8, 8)
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=4)
+    ref = orc.deo(dims, 0, U, x)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        xin = gpu.to_device_spinor(x, dtype=torch.complex64)
+        out = torch.empty_like(xin)
+        c.deo_apply_ex(0, prec, recon, xin, out)
+        torch.cuda.synchronize()
+        n, m = errs(gpu.from_device_spinor(out), ref)
+    assert n <= tol, f"normwise {n:.2e}"
+
+
+def test_links_roundtrip_and_upload_errors(gpu):
+    dims = (4, 4, 4, 4)
+    U = inputs.random_links(dims)
+    with gpu.Context(dims) as c:
+        with pytest.raises(gpu.LqcdError):
+            c.deo_apply(0, inputs.gaussian_field(dims))  # no links yet
+        c.links_upload(U)
+        assert np.array_equal(c.links_download(), U)
+        bad = U.copy()
+        bad[2, 5, 1, 1] = np.nan
+        with pytest.raises(gpu.LqcdError):
+            c.links_upload(bad)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dims", [(32, 32, 32, 32), (32, 32, 8, 32), (24, 24, 24, 24)])
+def test_deo_fp64_full_size_matches_oracle(gpu, orc, dims):
+    """Benchmark sizes, same launch configuration as bench.py, every output."""
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=0)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        xin = gpu.to_device_spinor(x)
+        out = torch.empty_like(xin)
+        c.deo_apply_dev(0, xin, out)
+        torch.cuda.synchronize()
+        got = gpu.from_device_spinor(out)
+    check_fp64(got, orc.deo(dims, 0, U, x))

@@ -1,0 +1,149 @@
+"""Multi-shift CG on the GPU against the FP64 CPU oracle (through the C ABI).
+
+Bar (stated by the method): for every shift the FP64 true residual
+||(A + sigma_i) x_i - b|| / ||b|| is at or below tol, recomputed here by the
+oracle from the returned x_i; the difference to the oracle's own solution is
+bounded by the conditioning, |x - x_ref| / |x_ref| <= 2 kappa_i tol with
+kappa_i = (m^2 + sigma_i + 16) / (m^2 + sigma_i) (||D|| <= 2 with the 1/2
+normalisation, so A <= m^2 + 4 ... 16 is a safe bound)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_1701_00426_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def kappa(m, s):
+    return (m * m + s + 16.0) / (m * m + s)
+
+
+def check_solution(orc, dims, U, mass, shifts, b, x, tol, xref=None):
+    for i, s in enumerate(shifts):
+        r = orc.true_residual(dims, U, mass, s, b, x[i])
+        assert r <= tol, f"shift {s}: oracle-recomputed true residual {r:.3e} > {tol}"
+        if xref is not None:
+            e = np.linalg.norm(x[i] - xref[i]) / np.linalg.norm(xref[i])
+            assert e <= 2 * kappa(mass, s) * tol, f"shift {s}: error vs oracle {e:.2e}"
+
+
+def test_config1_single_shift_cg_8444(gpu, orc):
+    """Plain FP64 CG on 8^4, m = 0.1, sigma = 0, tol 1e-10."""
+    dims = (8, 8, 8, 8)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims)
+    xref, iref = orc.mscg(dims, U, 0.1, [0.0], b, 1e-10)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        x, info = c.mscg_solve(0.1, [0.0], 1e-10, b)
+    assert info["true_resid"][0] <= 1e-10
+    assert abs(info["iters"] - iref["iters"]) <= max(5, 0.05 * iref["iters"])
+    check_solution(orc, dims, U, 0.1, [0.0], b, x, 1e-10, xref)
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8, 8), (4, 6, 8, 10)])
+def test_15_shifts_fp64(gpu, orc, dims):
+    shifts = inputs.log_shifts(15)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=1)
+    xref, _ = orc.mscg(dims, U, 0.01, shifts, b, 1e-10)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        x, info = c.mscg_solve(0.01, shifts, 1e-10, b)
+    assert max(info["true_resid"]) <= 1e-10
+    check_solution(orc, dims, U, 0.01, shifts, b, x, 1e-10, xref)
+
+
+@pytest.mark.parametrize("prec,recon", [(1, 18), (1, 12), (2, 12)])
+def test_15_shifts_mixed_precision(gpu, orc, prec, recon):
+    """FP32 / FP16-link iterations with FP64 reliable updates reach 1e-10."""
+    dims = (8, 8, 8, 8)
+    shifts = inputs.log_shifts(15)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=2)
+    xref, _ = orc.mscg(dims, U, 0.01, shifts, b, 1e-10)
+    with gpu.Context(dims, prec=prec, recon=recon) as c:
+        c.links_upload(U)
+        x, info = c.mscg_solve(0.01, shifts, 1e-10, b)
+    assert max(info["true_resid"]) <= 1e-10
+    assert info["reliable_updates"] > 0
+    check_solution(orc, dims, U, 0.01, shifts, b, x, 1e-10, xref)
+
+
+def test_shift_order_and_duplicates(gpu, orc):
+    dims = (4, 4, 6, 8)
+    shifts = [1.0, 1e-3, 0.1, 1e-3, 30.0]
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=3)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        x, info = c.mscg_solve(0.05, shifts, 1e-11, b)
+    check_solution(orc, dims, U, 0.05, shifts, b, x, 1e-11)
+    assert np.array_equal(x[1], x[3])
+
+
+def test_device_call_equals_host_call_and_is_deterministic(gpu):
+    dims = (8, 8, 8, 8)
+    shifts = [1e-3, 0.1, 1.0]
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=4)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        x1, _ = c.mscg_solve(0.05, shifts, 1e-10, b)
+        x2, _ = c.mscg_solve(0.05, shifts, 1e-10, b)
+        bd = gpu.to_device_spinor(b)
+        xd = torch.empty((3, 3, c.Vh), dtype=torch.complex128, device="cuda")
+        c.mscg_solve_dev(0.05, shifts, 1e-10, bd, xd)
+        x3 = gpu.from_device_spinor(xd)
+    assert np.array_equal(x1, x2)
+    assert np.array_equal(x1, x3)
+
+
+def test_free_field_closed_form(gpu):
+    import pins
+    dims = (4, 4, 6, 8)
+    U = inputs.unit_links(dims)
+    k = (1, 3, 2, 5)
+    b = pins.plane_wave_even(dims, k, np.array([1.0, 0.5j, -0.25]))
+    lam = pins.free_eigenvalue(dims, k, 0.1)
+    shifts = [0.0, 0.3, 7.0]
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        x, _ = c.mscg_solve(0.1, shifts, 1e-12, b)
+    for i, s in enumerate(shifts):
+        assert pins.rel(x[i], b / (lam + s)) < 1e-11
+
+
+def test_edge_cases(gpu):
+    dims = (2, 2, 2, 2)
+    U = inputs.random_links(dims)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        x, info = c.mscg_solve(0.1, [0.0, 1.0], 1e-10, np.zeros((8, 3)))
+        assert not np.any(x) and info["iters"] == 0
+        b = inputs.gaussian_field(dims)
+        x, info = c.mscg_solve(0.1, [0.0, 1.0], 1e-12, b)
+        assert max(info["true_resid"]) <= 1e-12
+        bad = b.copy()
+        bad[3, 1] = np.nan
+        with pytest.raises(gpu.LqcdError) as e:
+            c.mscg_solve(0.1, [0.0], 1e-10, bad)
+        assert e.value.status == gpu.LQCD_ENAN
+        for args in [(0.1, [], 1e-10), (0.1, [-1.0], 1e-10), (0.1, [0.0], 0.0), (0.0, [0.0], 1e-10),
+                     (0.1, list(range(33)), 1e-10)]:
+            with pytest.raises(gpu.LqcdError) as e:
+                c.mscg_solve(args[0], args[1], args[2], b)
+            assert e.value.status == gpu.LQCD_EINVAL
+
+
+def test_max_iter_reports_noconv(gpu):
+    dims = (8, 8, 8, 8)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims)
+    with gpu.Context(dims, max_iter=10, check_every=4) as c:
+        c.links_upload(U)
+        x, info = c.mscg_solve(0.01, [1e-5], 1e-10, b, allow_noconv=True)
+    assert info["status"] == gpu.LQCD_ENOCONV
+    assert 10 <= info["iters"] <= 12
+    assert np.all(np.isfinite(x))
