@@ -1,0 +1,382 @@
+"""Benchmark: multi-shift CG solves/s on a 32^4 lattice (15 shifts, m = 0.01,
+tol 1e-10, FP64), plus the FP64 D_eo ns/site and HBM GB/s sweep and the
+mixed-precision speed-up, through the C ABI of liblqcd.
+
+One "step" = one complete multi-shift solve (every kernel of the path:
+D_oe, D_eo with the normal-operator epilogue, the deterministic FP64
+reductions, the shifted updates, the FP64 true-residual check).  Inputs are
+resident in HBM when the timed region starts and are larger than L2 (links
+604 MB, Krylov vectors 0.8 GB), so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the plain C FP64 oracle (the reference arm of this
+build) on bounded samples of the same workload on the host cores.
+Multi-GPU: replicas only (every rank solves its own source; no collective
+on the data path); value = solves of all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "D_eo ns/site & HBM GB/s; mshift-CG solves/s at 1e-10 (mixed/batched vs FP64)"
+DIMS = (32, 32, 32, 32)
+MASS = 0.01
+N_SHIFT = 15
+TOL = 1e-10
+WORKLOAD = "mscg 32^4, m=0.01, 15 shifts log-spaced 1e-5..1e2, tol 1e-10, FP64 (hot random SU(3) links)"
+COUNTS_KEY = "mscg_32x32x32x32_m0.01_15shifts_tol1e-10"
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup(n_gpus: int):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v: float, world: int) -> float:
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+def oracle_iteration_count():
+    p = os.path.join(ROOT, "tests", "golden", "oracle_counts.json")
+    if os.path.exists(p):
+        d = json.load(open(p)).get(COUNTS_KEY)
+        if d:
+            return d["iters"] + d["refine_iters"], "oracle's own full solve (tests/golden/oracle_counts.json)"
+    return None, None
+
+
+def oracle_sample(U, b, shifts, k_lo=2, k_hi=12):
+    """Times the oracle's multi-shift CG stopped after k_lo and k_hi iterations;
+    returns (seconds per iteration, seconds for the k_lo run, threads)."""
+    from oracle import oracle
+    orc = oracle()
+    threads = orc.set_threads(0)
+    t0 = time.time()
+    orc.mscg(DIMS, U, MASS, shifts, b, TOL, max_iter=k_lo)
+    t1 = time.time()
+    orc.mscg(DIMS, U, MASS, shifts, b, TOL, max_iter=k_hi)
+    t2 = time.time()
+    per_iter = ((t2 - t1) - (t1 - t0)) / (k_hi - k_lo)
+    return per_iter, t1 - t0, threads, k_lo, k_hi
+
+
+def cpu_solves_per_sec(per_iter, fixed, k_lo, n_iter):
+    return 1.0 / (fixed + per_iter * max(n_iter - k_lo, 0))
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the plain C oracle on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    from paper_1701_00426_gb300 import inputs
+    U = inputs.random_links(DIMS)
+    b = inputs.gaussian_field(DIMS, k=0)
+    shifts = inputs.log_shifts(N_SHIFT)
+    n_iter, src = oracle_iteration_count()
+    if n_iter is None:
+        n_iter, src = 3000, "assumed 3000 iterations (oracle count file missing)"
+    for _ in range(args.warmup):
+        oracle_sample(U, b, shifts, 1, 2)
+    vals, wall = [], time.time()
+    for _ in range(args.steps):
+        per_iter, fixed, thr, klo, khi = oracle_sample(U, b, shifts, 1, 4)
+        vals.append(cpu_solves_per_sec(per_iter, fixed, klo, n_iter))
+    wall = time.time() - wall
+    v = float(np.median(vals))
+    line = {"metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 / v, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": thr, "kind": "oracle",
+                             "sample": f"each step: oracle multi-shift CG stopped after 1 and 4 iterations; "
+                                       f"per-iteration time x {n_iter} iterations ({src})"},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "sample_wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- ours
+def deo_sweep(lqcd, inputs, torch, flush, hbm_peak, sizes):
+    """ns/site and algorithmic GB/s of one D_eo, median of reps with L2 flushed."""
+    out = {}
+    variants = [("fp64", 0, 18, torch.complex128, 1248.0), ("fp64_native_dfma", 3, 18, torch.complex128, 1248.0),
+                ("fp32_12r", 1, 12, torch.complex64, 432.0), ("fp16_12r", 2, 12, torch.complex64, 240.0)]
+    for L in sizes:
+        dims = (L,) * 4
+        U = inputs.random_links(dims)
+        with lqcd.Context(dims) as c:
+            c.links_upload(U)
+            del U
+            res = {}
+            for name, prec, recon, dt, bps in variants:
+                x = lqcd.to_device_spinor(inputs.gaussian_field(dims), dtype=dt)
+                o = torch.empty_like(x)
+                s = torch.cuda.current_stream()
+                for _ in range(3):
+                    c.deo_apply_ex(0, prec, recon, x, o, s)
+                ts = []
+                reps = 10 if L >= 48 else 20
+                for _ in range(reps):
+                    flush.fill_(1.0)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    c.deo_apply_ex(0, prec, recon, x, o, s)
+                    e1.record(s)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                med = float(np.median(ts))
+                gbs = bps * c.Vh / (med * 1e-3) / 1e9
+                res[name] = {"ns_per_site": round(med * 1e6 / c.Vh, 4), "GB_s": round(gbs, 1),
+                             "frac_hbm": round(gbs / hbm_peak, 3), "bytes_per_site": bps}
+                del x, o
+        out[f"{L}^4"] = res
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_ours(args, rank, world, local):
+    global DIMS, WORKLOAD
+    if args.lattice != 32:
+        DIMS = (args.lattice,) * 4
+        WORKLOAD = WORKLOAD.replace("32^4", f"{args.lattice}^4")
+    import torch
+    from paper_1701_00426_gb300 import build, inputs, lqcd
+    torch.cuda.set_device(local)
+    if rank == 0 or world > 1:
+        build.build()
+    barrier(world)
+    lqcd.load()
+    hbm_peak, peak_src = peaks()
+    U = inputs.random_links(DIMS)
+    b = inputs.gaussian_field(DIMS, k=rank)
+    shifts = inputs.log_shifts(N_SHIFT)
+    ctx = lqcd.Context(DIMS)
+    ctx.links_upload(U)
+    bd = lqcd.to_device_spinor(b)
+    xd = torch.empty((N_SHIFT, 3, ctx.Vh), dtype=torch.complex128, device="cuda")
+    info = None
+    for _ in range(args.warmup):
+        info = ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)
+    torch.cuda.synchronize()
+    barrier(world)
+    s = torch.cuda.current_stream()
+    infos = []
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            infos.append(ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd, stream=s))
+        e1.record(s)
+        torch.cuda.synchronize()
+    barrier(world)
+    t_ms = e0.elapsed_time(e1)
+    t_max = max_over_ranks(t_ms, world)
+    value = world * args.steps / (t_max * 1e-3)
+    clocks = clk.summary()
+    launches = int(sum(i["kernel_launches"] for i in infos))
+    worst_res = float(max(max(i["true_resid"]) for i in infos))
+    it = infos[-1]
+    if args.only_solve:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+                              "iters": it["iters"], "max_true_resid": worst_res, "gpu_launches": launches,
+                              "config": {"workload": WORKLOAD, "only_solve": True}}), flush=True)
+        ctx.close()
+        return
+
+    # end to end through the host API (pinned-free numpy buffers; copies inside)
+    e2e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        xh, _ = ctx.mscg_solve(MASS, shifts, TOL, b)
+    torch.cuda.synchronize()
+    e2e_t = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": world * e2e_steps / e2e_t, "unit": "solves/s", "h2d_bytes_per_step": int(b.nbytes),
+           "d2h_bytes_per_step": int(xh.nbytes)}
+    if rank != 0:
+        ctx.close()
+        return
+
+    # per-kernel times of the iteration (same kernels, launched one by one)
+    n_it = it["iters"]
+    ms, nact = ctx.profile_iteration(MASS, shifts, bd, iters=min(n_it, 4000))
+    Vh = ctx.Vh
+    kbytes = [Vh * 1248.0, Vh * 1296.0, Vh * 144.0, Vh * (48.0 + 192.0 * nact)]
+    knames = ["D_oe (t = D_oe p)", "D_eo + normal-operator epilogue + <p,q>", "r -= alpha q, ||r||^2",
+              "shifted updates x_i, p_i"]
+    shares = [m / sum(ms) for m in ms]
+    kdom = int(np.argmax(ms))
+    achieved = kbytes[kdom] / (ms[kdom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 3), "traffic": None, "kernel": knames[kdom],
+                "peak_source": peak_src, "note": "of measured"}
+    kernels = {knames[k]: {"ms": round(ms[k], 4), "share": round(shares[k], 3),
+                           "GB_s": round(kbytes[k] / (ms[k] * 1e-3) / 1e9, 1)} for k in range(4)}
+
+    # mixed precision on the same workload
+    mixed = {}
+    for name, prec, recon in [("fp32_12r", 1, 12), ("fp16_12r", 2, 12)]:
+        ctx.set_opts(prec=prec, recon=recon)
+        ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        mi = ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        mixed[name] = {"solves_per_s": round(1.0 / dt, 4), "speedup_vs_fp64": round((1.0 / dt) / value, 3),
+                       "max_true_resid": max(mi["true_resid"]), "iters": mi["iters"],
+                       "refine_iters": mi["refine_iters"], "reliable_updates": mi["reliable_updates"]}
+    ctx.set_opts(prec=0, recon=18)
+    ctx.close()
+    del bd, xd
+    torch.cuda.empty_cache()
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    sweep = deo_sweep(lqcd, inputs, torch, flush, hbm_peak, args.sweep)
+
+    # CPU baseline: the oracle on a bounded sample of the same workload
+    n_iter, src = oracle_iteration_count()
+    if n_iter is None:
+        n_iter, src = it["iters"] + it["refine_iters"], "iteration count of the GPU solve"
+    per_iter, fixed, thr, klo, khi = oracle_sample(U, b, shifts)
+    cpu_v = cpu_solves_per_sec(per_iter, fixed, klo, n_iter)
+    cpu = {"value": cpu_v, "unit": "solves/s", "cores": thr, "kind": "oracle",
+           "sample": f"oracle multi-shift CG on the same 32^4 workload stopped after {klo} and {khi} "
+                     f"iterations; per-iteration time x {n_iter} iterations ({src})"}
+
+    line = {"metric": METRIC, "value": round(value, 5), "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "lattice": list(DIMS), "mass": MASS, "n_shift": N_SHIFT, "tol": TOL,
+                       "prec": "fp64 (df64 iteration, IEEE FP64 true residual)", "parallelism": "replicas",
+                       "l2": "inputs larger than L2 (links 604 MB, vectors 0.8 GB); no flush"},
+            "iters": it["iters"], "refine_iters": it["refine_iters"], "max_true_resid": worst_res,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
+            "cpu_baseline": cpu, "kernels": kernels, "n_active_avg": round(nact, 2),
+            "mixed": mixed, "deo": sweep}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--sweep", type=int, nargs="*", default=[16, 24, 32, 48])
+    ap.add_argument("--lattice", type=int, default=32, help="side of the solve lattice (default 32)")
+    ap.add_argument("--only-solve", action="store_true",
+                    help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        # the oracle runs on the host; ranks other than 0 exit without work
+        run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
+        return
+    rank, world, local = dist_setup(args.gpus)
+    run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -373,10 +373,12 @@ int oracle_mscg(const int N[4], const cplx *links, double mass,
     iters_out[0] = k;
     iters_out[1] = 0;
 
-    /* true residual per shift; finish any shift above tol with plain CG */
+    /* true residual per shift; finish any shift above tol with plain CG
+     * (only after the shifted iteration converged: a run stopped by
+     * max_iter reports its residuals as they are) */
     for (int s = 0; s < n_shift; ++s) {
         true_resid[s] = oracle_true_residual(N, links, mass, shifts[s], b, x + s * n);
-        if (true_resid[s] > tol) {
+        if (status == 0 && true_resid[s] > tol) {
             int it = oracle_cg(N, links, mass, shifts[s], b, x + s * n, tol, max_iter);
             if (it < 0) status = -1; else iters_out[1] += it;
             true_resid[s] = oracle_true_residual(N, links, mass, shifts[s], b, x + s * n);

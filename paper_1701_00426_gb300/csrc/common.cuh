@@ -164,15 +164,39 @@ struct Acc2 {
 __device__ __forceinline__ void acc_zero(Acc2 &A) { A.s = 0.f; A.c = 0.f; }
 
 // A += (ah + al) * (bh + bl); the al*bl term (relative 2^-48) is dropped.
+// The rounding errors of the product and of the sum and the two cross terms
+// (all ~2^-24 of the product) are first added together, then once into c.
 __device__ __forceinline__ void acc_prod(Acc2 &A, float ah, float al, float bh, float bl)
 {
     float p, e, s, t;
     two_prod(ah, bh, p, e);
     two_sum(A.s, p, s, t);
     A.s = s;
-    A.c = __fadd_rn(A.c, __fadd_rn(t, e));
-    A.c = __fmaf_rn(ah, bl, A.c);
-    A.c = __fmaf_rn(al, bh, A.c);
+    float tmp = __fadd_rn(t, e);
+    tmp = __fmaf_rn(ah, bl, tmp);
+    tmp = __fmaf_rn(al, bh, tmp);
+    A.c = __fadd_rn(A.c, tmp);
+}
+
+// Same, with the small terms collected in a separate per-hop accumulator
+// ch (added into A.c once per hop by acc_flush): fewer roundings at the
+// magnitude of the running error sum.
+__device__ __forceinline__ void acc_prod_h(Acc2 &A, float &ch, float ah, float al, float bh, float bl)
+{
+    float p, e, s, t;
+    two_prod(ah, bh, p, e);
+    two_sum(A.s, p, s, t);
+    A.s = s;
+    float tmp = __fadd_rn(t, e);
+    tmp = __fmaf_rn(ah, bl, tmp);
+    tmp = __fmaf_rn(al, bh, tmp);
+    ch = __fadd_rn(ch, tmp);
+}
+
+__device__ __forceinline__ void acc_flush(Acc2 &A, float &ch)
+{
+    A.c = __fadd_rn(A.c, ch);
+    ch = 0.f;
 }
 
 // A += (bh + bl) (plain df64 value, no product)
@@ -262,10 +286,10 @@ __device__ __forceinline__ float2 df_mul2(float2 a, float2 b, float2 c, float2 d
 
 // ------------------------------------------------------------------ FP64 <-> df64
 // Split an IEEE double into hi + lo floats with integer operations only (no
-// FP64 instruction).  hi = d truncated to 24 significant bits, lo = the next
-// 23 bits rounded; |d - hi - lo| <= 2^-47 |d|.  Exact zero and FP64
-// subnormals give 0.  Magnitudes outside [2^-60, 2^64) set *bad (the caller
-// then recomputes that site in native FP64).
+// FP64 instruction).  hi = d rounded to 24 significant bits, lo = the signed
+// remainder rounded to 24 bits; |d - hi - lo| <= 2^-48 |d|.  Exact zero and
+// FP64 subnormals give 0.  Magnitudes outside [2^-60, 2^64) set *bad (the
+// caller then recomputes that site in native FP64).
 __device__ __forceinline__ float2 split_f64(double d, bool &bad)
 {
     const uint32_t hi = (uint32_t)__double2hiint(d);
@@ -273,9 +297,18 @@ __device__ __forceinline__ float2 split_f64(double d, bool &bad)
     const uint32_t e = (hi >> 20) & 0x7FFu;
     const bool zero = (e == 0u);
     bad |= (!zero) && ((e - 963u) > (1086u - 963u));
-    const uint32_t hb = (__funnelshift_l(lo, hi - (896u << 20), 3) & 0x7FFFFFFFu) | (hi & 0x80000000u);
-    const uint32_t yb = (hb & 0xFF800000u) - (23u << 23);
-    const uint32_t xb = yb + (((lo & 0x1FFFFFFFu) + 32u) >> 6);
+    const uint32_t rb = (lo >> 28) & 1u;  // first dropped significand bit
+    // |hi|: exponent rebased 1023 -> 127, 23 fraction bits, rounded to nearest
+    const uint32_t hmag = (__funnelshift_l(lo, hi - (896u << 20), 3) & 0x7FFFFFFFu) + rb;
+    const uint32_t hb = hmag | (hi & 0x80000000u);
+    // remainder in units of 2^(e-1075): the 29 dropped bits, or 2^29 minus them
+    // (opposite sign) when hi was rounded up; |rem| <= 2^28.
+    const uint32_t m = lo & 0x1FFFFFFFu;
+    const uint32_t mag = rb ? (0x20000000u - m) : m;
+    // lo = Y + round(mag / 32) ulp(Y) - Y with Y = 2^(e-1047), ulp(Y) = 2^(e-1070):
+    // the integer add builds the float exactly, the subtraction is exact.
+    const uint32_t yb = ((hi & 0x80000000u) ^ (rb << 31)) | ((e - 920u) << 23);
+    const uint32_t xb = yb + ((mag + 16u) >> 5);
     const float h = __uint_as_float(hb);
     const float l = __fsub_rn(__uint_as_float(xb), __uint_as_float(yb));
     return zero ? make_float2(0.f, 0.f) : make_float2(h, l);

@@ -37,32 +37,32 @@ __device__ __forceinline__ size_t link_base(int mu, int par, int comps, int Vh)
 
 // ------------------------------------------------------------------ DF hops
 // U component c = (re_h, re_l, im_h, im_l); v component likewise.
-__device__ __forceinline__ void hop_fwd_df(Acc2 (&acc)[6], const float4 (&U)[9], const float4 (&v)[3])
+__device__ __forceinline__ void hop_fwd_df(Acc2 (&acc)[6], float (&ch)[6], const float4 (&U)[9], const float4 (&v)[3])
 {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const float4 u = U[a * 3 + b], w = v[b];
-            acc_prod(acc[2 * a], u.x, u.y, w.x, w.y);        // + ur vr
-            acc_prod(acc[2 * a], -u.z, -u.w, w.z, w.w);      // - ui vi
-            acc_prod(acc[2 * a + 1], u.x, u.y, w.z, w.w);    // + ur vi
-            acc_prod(acc[2 * a + 1], u.z, u.w, w.x, w.y);    // + ui vr
+            acc_prod_h(acc[2 * a], ch[2 * a], u.x, u.y, w.x, w.y);          // + ur vr
+            acc_prod_h(acc[2 * a], ch[2 * a], -u.z, -u.w, w.z, w.w);        // - ui vi
+            acc_prod_h(acc[2 * a + 1], ch[2 * a + 1], u.x, u.y, w.z, w.w);  // + ur vi
+            acc_prod_h(acc[2 * a + 1], ch[2 * a + 1], u.z, u.w, w.x, w.y);  // + ui vr
         }
 }
 
 // (U^dag v)_a = sum_b conj(U_ba) v_b
-__device__ __forceinline__ void hop_bwd_df(Acc2 (&acc)[6], const float4 (&U)[9], const float4 (&v)[3])
+__device__ __forceinline__ void hop_bwd_df(Acc2 (&acc)[6], float (&ch)[6], const float4 (&U)[9], const float4 (&v)[3])
 {
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int b = 0; b < 3; ++b) {
             const float4 u = U[b * 3 + a], w = v[b];
-            acc_prod(acc[2 * a], u.x, u.y, w.x, w.y);        // + ur vr
-            acc_prod(acc[2 * a], u.z, u.w, w.z, w.w);        // + ui vi
-            acc_prod(acc[2 * a + 1], u.x, u.y, w.z, w.w);    // + ur vi
-            acc_prod(acc[2 * a + 1], -u.z, -u.w, w.x, w.y);  // - ui vr
+            acc_prod_h(acc[2 * a], ch[2 * a], u.x, u.y, w.x, w.y);          // + ur vr
+            acc_prod_h(acc[2 * a], ch[2 * a], u.z, u.w, w.z, w.w);          // + ui vi
+            acc_prod_h(acc[2 * a + 1], ch[2 * a + 1], u.x, u.y, w.z, w.w);  // + ur vi
+            acc_prod_h(acc[2 * a + 1], ch[2 * a + 1], -u.z, -u.w, w.x, w.y); // - ui vr
         }
 }
 
@@ -106,12 +106,15 @@ __device__ __forceinline__ void deo_site_df(const Geom &g, const float4 *L, cons
         uint32_t nf, nb;
         hop(g, S, mu, f, b, nf, nb);
         float4 U[9], v[3];
+        float ch[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         load_link_df(L, mu, P, i, Vh, U);
         load_spinor_df<SF>(in, f, Vh, nf, v, bad);
-        hop_fwd_df(acc, U, v);
+        hop_fwd_df(acc, ch, U, v);
         load_link_df(L, mu, 1 - P, b, Vh, U);
         load_spinor_df<SF>(in, b, Vh, nb, v, bad);
-        hop_bwd_df(acc, U, v);
+        hop_bwd_df(acc, ch, U, v);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc_flush(acc[k], ch[k]);
     }
 #pragma unroll
     for (int k = 0; k < 6; ++k) {

@@ -123,6 +123,7 @@ struct lqcd_ctx {
     lqcd::GraphCache graph;
     int *h_pinned = nullptr;  // pinned host words for halt/iteration polling
     double *h_pinned_d = nullptr;
+    uint64_t launches = 0;    // library kernels launched on behalf of this context
 };
 
 namespace lqcd {
@@ -139,13 +140,25 @@ int soa_to_host(lqcd_ctx *c, const double2 *dev_soa, double *host, int nfields, 
 // solver.cu
 int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double2 *b,
                    double2 *x, lqcd_solve_info *info, cudaStream_t s);
+int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, const double2 *b, int iters,
+                      double ms[4], double *n_act_avg);
 int mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, const double *const *shifts,
                       const int *n_shift, const double *tol, const double *const *b, double *const *x,
                       lqcd_solve_info *info);
+
+// helpers shared by solver.cu and mrhs.cu
+void k_res_nat1_ext(const Geom &g, const double2 *L, const double2 *x, double2 *t, int ntiles, cudaStream_t s);
+void k_res_nat2_ext(const Geom &g, const double2 *L, const double2 *t, const double2 *x, const double2 *b, double a,
+                    double2 *r_hi, double *part, unsigned *ticket, double *out, int ntiles, cudaStream_t s);
+double unit_scale_pub(double n2, double n);
+void init_state_pub(SolverState &S, double mass, const double *shifts, int n_shift, double tol_iter, double b2,
+                    int max_iter);
 
 // mrhs.cu
 int deo_mrhs_launch(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const void *in, void *out, cudaStream_t s);
 int cg_solve_mrhs(lqcd_ctx *c, double mass, double sigma, int n_rhs, double tol, const double *b, double *x,
                   lqcd_solve_info *info);
+int mrhs_cg_core(lqcd_ctx *c, double mass, const double *sigma, int n, double tol, const double2 *b, int b_stride,
+                 double2 *xh, int lf, lqcd_solve_info *infos, double &bytes);
 
 }  // namespace lqcd

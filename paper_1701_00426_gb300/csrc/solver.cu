@@ -190,6 +190,18 @@ __global__ void __launch_bounds__(kTile)
     reduce_finish(part, ticket, ntiles, tile, v, [&](double tot) { *out = tot; });
 }
 
+// Host wrappers used by the batched solver (mrhs.cu).
+void k_res_nat1_ext(const Geom &g, const double2 *L, const double2 *x, double2 *t, int ntiles, cudaStream_t s)
+{
+    k_res_nat1<<<ntiles, kTile, 0, s>>>(g, L, x, t);
+}
+
+void k_res_nat2_ext(const Geom &g, const double2 *L, const double2 *t, const double2 *x, const double2 *b, double a,
+                    double2 *r_hi, double *part, unsigned *ticket, double *out, int ntiles, cudaStream_t s)
+{
+    k_res_nat2<VP_F32><<<ntiles, kTile, 0, s>>>(g, L, t, x, b, a, r_hi, nullptr, 1.0, part, ticket, out);
+}
+
 // ------------------------------------------------------------------ workspace
 struct WsPtrs {
     void *r, *q, *t, *x, *ps;
@@ -248,6 +260,7 @@ static int norm2_ieee(lqcd_ctx *c, const WsPtrs &P, const double2 *v, int nvec, 
 {
     k_norm2_ieee<<<P.ntiles, kTile, 0, s>>>(v, (int)c->Vh, nvec, P.part, P.ticket + 1, P.ntiles, P.scal);
     LQCD_CUDA(cudaGetLastError());
+    c->launches += 1;
     LQCD_CUDA(cudaMemcpyAsync(c->h_pinned_d, P.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
     LQCD_CUDA(cudaStreamSynchronize(s));
     out = c->h_pinned_d[0];
@@ -261,6 +274,7 @@ static int true_residual(lqcd_ctx *c, const WsPtrs &P, int vp, double a, const d
     const double2 *L = c->lnk_nat.as<double2>();
     k_res_nat1<<<P.ntiles, kTile, 0, s>>>(c->g, L, x, P.t_nat);
     LQCD_CUDA(cudaGetLastError());
+    c->launches += 2;
     if (vp == VP_DF)
         k_res_nat2<VP_DF><<<P.ntiles, kTile, 0, s>>>(c->g, L, P.t_nat, x, b, a, r_hi, r_lo, lo_scale, P.part,
                                                       P.ticket + 1, P.scal);
@@ -275,7 +289,9 @@ static int true_residual(lqcd_ctx *c, const WsPtrs &P, int vp, double a, const d
 }
 
 // power of two bringing a field of squared norm n2 over n reals to O(1) entries
-static double unit_scale(double n2, double n)
+double unit_scale_pub(double n2, double n);
+static double unit_scale(double n2, double n) { return unit_scale_pub(n2, n); }
+double unit_scale_pub(double n2, double n)
 {
     if (!(n2 > 0.0) || !std::isfinite(n2)) return 1.0;
     const double rms = std::sqrt(n2 / n);
@@ -362,6 +378,7 @@ static int run_until_halt(lqcd_ctx *c, const IterBatch<NJ> &B, int vp, int lf, i
     LQCD_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     auto enqueue = [&](int sl) -> cudaError_t {
         cudaError_t e = cudaGraphLaunch(c->graph.exec, s);
+        c->launches += 4 * (uint64_t)chunk;
         for (int j = 0; j < nj && e == cudaSuccess; ++j)
             e = cudaMemcpyAsync(hs + sl * kMaxJobs + j, &B.job[j].st->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaEventRecord(ev[sl], s);
@@ -426,7 +443,14 @@ static void fill_job(lqcd_ctx *c, const WsPtrs &P, const void *links, IterJob &J
 }
 
 // Host-side initial state of a solve of (A + shifts) with source norm^2 b2.
+void init_state_pub(SolverState &S, double mass, const double *shifts, int n_shift, double tol_iter, double b2,
+                    int max_iter);
 static void init_state(SolverState &S, double mass, const double *shifts, int n_shift, double tol_iter, double b2,
+                       int max_iter)
+{
+    init_state_pub(S, mass, shifts, n_shift, tol_iter, b2, max_iter);
+}
+void init_state_pub(SolverState &S, double mass, const double *shifts, int n_shift, double tol_iter, double b2,
                        int max_iter)
 {
     memset(&S, 0, sizeof S);
@@ -479,7 +503,8 @@ static int engine_mscg(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void 
         k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
     else
         k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
-    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaGetLastError());    LQCD_CUDA(cudaGetLastError());
+    c->launches += 1;
     IterBatch<1> B;
     memset(&B, 0, sizeof B);
     B.njobs = 1;
@@ -518,7 +543,8 @@ static int refine_shift(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void
             k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r_hi, P.r, n3, scale);
         else
             k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r_hi, P.r, n3, scale);
-        LQCD_CUDA(cudaGetLastError());
+        LQCD_CUDA(cudaGetLastError());        LQCD_CUDA(cudaGetLastError());
+        c->launches += 1;
         SolverState S;
         const double rho = rr * scale * scale;
         // iterate a little below the target so that rounding drift stays inside tol
@@ -530,7 +556,8 @@ static int refine_shift(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void
             k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, 1);
         else
             k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, 1);
-        LQCD_CUDA(cudaGetLastError());
+        LQCD_CUDA(cudaGetLastError());        LQCD_CUDA(cudaGetLastError());
+        c->launches += 1;
         IterBatch<1> B;
         memset(&B, 0, sizeof B);
         B.njobs = 1;
@@ -550,7 +577,8 @@ static int refine_shift(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void
                 k_vec_to_ieee<VP_DF><<<nblk(n3), 256, 0, s>>>(P.x, x_hi, n3, 1.0 / scale, 1);
             else
                 k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>(P.x, x_hi, n3, 1.0 / scale, 1);
-            LQCD_CUDA(cudaGetLastError());
+            LQCD_CUDA(cudaGetLastError());            LQCD_CUDA(cudaGetLastError());
+            c->launches += 1;
             if (O.halt == HALT_NAN) return fail(LQCD_ENAN, "NaN/Inf or breakdown in refinement");
             if (O.halt == HALT_MAXITER) hit_max = true;
             if (O.halt != HALT_RELIABLE) break;
@@ -563,7 +591,8 @@ static int refine_shift(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void
             k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r_hi, P.r, n3, scale);
             k_zero_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(P.x, n3);
             k_scale_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(P.ps, n3, (float)(scale / old_scale));
-            LQCD_CUDA(cudaGetLastError());
+            LQCD_CUDA(cudaGetLastError());            LQCD_CUDA(cudaGetLastError());
+            c->launches += 1;
             // continue the same CG: new rho, new reliable threshold, halt cleared
             SolverState U = O;
             U.rho = rr * scale * scale;
@@ -585,6 +614,7 @@ int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, 
                    double2 *x, lqcd_solve_info *info, cudaStream_t s_user)
 {
     const auto t0 = std::chrono::steady_clock::now();
+    const uint64_t launches0 = c->launches;
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
     if (!shifts || !b || !x) return fail(LQCD_EINVAL, "NULL argument");
     if (n_shift < 1 || n_shift > LQCD_MAX_SHIFTS) return fail(LQCD_EINVAL, "n_shift must be in 1..32");
@@ -623,7 +653,8 @@ int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, 
         k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
     else
         k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
-    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaGetLastError());    LQCD_CUDA(cudaGetLastError());
+    c->launches += 1;
     // FP64: iterate to half the tolerance; mixed: FP32 reaches ~1e-6 at best
     const double tol_iter = vp == VP_DF ? 0.5 * tol : std::max(tol, 1e-6);
     SolverState O;
@@ -640,27 +671,149 @@ int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, 
             k_vec_to_ieee<VP_DF><<<nblk(n3), 256, 0, s>>>((const float4 *)P.x + off, x + off, n3, 1.0 / scale, 0);
         else
             k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>((const float2 *)P.x + off, x + off, n3, 1.0 / scale, 0);
-        LQCD_CUDA(cudaGetLastError());
+        LQCD_CUDA(cudaGetLastError());        LQCD_CUDA(cudaGetLastError());
+        c->launches += 1;
     }
     int status = maxed ? LQCD_ENOCONV : LQCD_OK;
-    for (int i = 0; i < n_shift; ++i) {
-        double res = 0;
-        int it = 0, rel = 0;
-        if ((st = refine_shift(c, P, vp, lf, links, mass, shifts[i], b, b2, x + (size_t)i * n3, tol, !maxed, s, res,
-                               it, rel, bytes)))
-            return st;
-        I.true_resid[i] = res;
-        I.refine_iters += it;
-        I.reliable_updates += rel;
-        if (!(res <= tol)) status = LQCD_ENOCONV;
+    if (vp == VP_DF || maxed) {
+        // FP64: the df64 iteration already ran to tol/2; check each shift in
+        // native FP64 and correct the rare one above tol
+        for (int i = 0; i < n_shift; ++i) {
+            double res = 0;
+            int it = 0, rel = 0;
+            if ((st = refine_shift(c, P, vp, lf, links, mass, shifts[i], b, b2, x + (size_t)i * n3, tol, !maxed, s,
+                                   res, it, rel, bytes)))
+                return st;
+            I.true_resid[i] = res;
+            I.refine_iters += it;
+            I.reliable_updates += rel;
+            if (!(res <= tol)) status = LQCD_ENOCONV;
+        }
+    } else {
+        // mixed: every shift finished together by the batched CG (FP32
+        // iterations, links read once per application for all shifts, FP64
+        // reliable updates); the FP16 variant uses FP32 links here because
+        // FP16 rounding times the condition number of the smallest shifts
+        // exceeds one and would stall the reliable updates
+        const int lf2 = c->opts.recon == 12 || lf == LF_F16_12 ? LF_F32_12 : LF_F32_18;
+        for (int g0 = 0; g0 < n_shift; g0 += 16) {
+            const int ng = std::min(16, n_shift - g0);
+            lqcd_solve_info J[16];
+            memset(J, 0, sizeof J);
+            const int rc = mrhs_cg_core(c, mass, shifts + g0, ng, tol, b, 0, x + (size_t)g0 * n3, lf2, J, bytes);
+            if (rc != LQCD_OK && rc != LQCD_ENOCONV) return rc;
+            int mx = 0;
+            for (int k = 0; k < ng; ++k) {
+                I.true_resid[g0 + k] = J[k].true_resid[0];
+                I.reliable_updates += J[k].reliable_updates;
+                mx = std::max(mx, J[k].iters);
+                if (!(J[k].true_resid[0] <= tol)) status = LQCD_ENOCONV;
+            }
+            I.refine_iters += mx;
+        }
     }
     LQCD_CUDA(cudaStreamSynchronize(s));
     I.bytes_moved = bytes;
+    I.kernel_launches = (int)(c->launches - launches0);
     I.secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     I.status = status;
     if (info) *info = I;
     if (status == LQCD_ENOCONV) set_error("solver did not reach tol within max_iter");
     return status;
+}
+
+int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, const double2 *b, int iters,
+                      double ms[4], double *n_act_avg)
+{
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (!shifts || !b || n_shift < 1 || n_shift > LQCD_MAX_SHIFTS || iters < 1 || iters > 100000)
+        return fail(LQCD_EINVAL, "bad profile arguments");
+    cudaStream_t s = c->stream;
+    const int vp = c->opts.prec == LQCD_PREC_FP64 || c->opts.prec == LQCD_PREC_FP64_NATIVE ? VP_DF : VP_F32;
+    const void *links = nullptr;
+    const int lf = link_fmt_for(c, vp == VP_DF ? LQCD_PREC_FP64 : c->opts.prec, &links);
+    WsPtrs P;
+    int st = ensure_workspace(c, vp, n_shift, P);
+    if (st) return st;
+    const long n3 = 3 * (long)c->Vh;
+    double b2;
+    if ((st = norm2_ieee(c, P, b, 1, s, b2))) return st;
+    const double scale = unit_scale(b2, 6.0 * c->Vh);
+    if (vp == VP_DF)
+        k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
+    else
+        k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
+    SolverState S;
+    init_state(S, mass, shifts, n_shift, 1e-300, b2 * scale * scale, iters + 1);
+    LQCD_CUDA(cudaMemcpyAsync(P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
+    if (vp == VP_DF)
+        k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
+    else
+        k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
+    LQCD_CUDA(cudaGetLastError());    LQCD_CUDA(cudaGetLastError());
+    c->launches += 1;
+    IterBatch<1> B;
+    memset(&B, 0, sizeof B);
+    B.njobs = 1;
+    B.tile_start[1] = P.ntiles;
+    fill_job(c, P, links, B.job[0]);
+    std::vector<cudaEvent_t> ev(5 * (size_t)iters);
+    for (auto &e : ev) LQCD_CUDA(cudaEventCreate(&e));
+    std::vector<int> nact(iters, 0);
+    int *hn = c->h_pinned;
+    const int ntot = P.ntiles;
+    for (int k = 0; k < iters; ++k) {
+        cudaEvent_t *E = &ev[5 * (size_t)k];
+        cudaEventRecord(E[0], s);
+        if (vp == VP_DF) {
+            k_it_deo1<1, VP_DF, LF_DF18><<<ntot, kTile, 0, s>>>(B);
+            cudaEventRecord(E[1], s);
+            k_it_deo2<1, VP_DF, LF_DF18><<<ntot, kTile, 0, s>>>(B);
+            cudaEventRecord(E[2], s);
+            k_it_upd_r<1, VP_DF><<<ntot, kTile, 0, s>>>(B);
+            cudaEventRecord(E[3], s);
+            k_it_upd_shifts<1, VP_DF><<<ntot, kTile, 0, s>>>(B);
+        } else {
+            if (lf == LF_F32_18) {
+                k_it_deo1<1, VP_F32, LF_F32_18><<<ntot, kTile, 0, s>>>(B);
+                cudaEventRecord(E[1], s);
+                k_it_deo2<1, VP_F32, LF_F32_18><<<ntot, kTile, 0, s>>>(B);
+            } else if (lf == LF_F32_12) {
+                k_it_deo1<1, VP_F32, LF_F32_12><<<ntot, kTile, 0, s>>>(B);
+                cudaEventRecord(E[1], s);
+                k_it_deo2<1, VP_F32, LF_F32_12><<<ntot, kTile, 0, s>>>(B);
+            } else {
+                k_it_deo1<1, VP_F32, LF_F16_12><<<ntot, kTile, 0, s>>>(B);
+                cudaEventRecord(E[1], s);
+                k_it_deo2<1, VP_F32, LF_F16_12><<<ntot, kTile, 0, s>>>(B);
+            }
+            cudaEventRecord(E[2], s);
+            k_it_upd_r<1, VP_F32><<<ntot, kTile, 0, s>>>(B);
+            cudaEventRecord(E[3], s);
+            k_it_upd_shifts<1, VP_F32><<<ntot, kTile, 0, s>>>(B);
+        }
+        cudaEventRecord(E[4], s);
+        c->launches += 4;
+        if (k < 2 * kMaxJobs) cudaMemcpyAsync(hn + k, &P.st->n_act, sizeof(int), cudaMemcpyDeviceToHost, s);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    double acc[4] = {0, 0, 0, 0};
+    if (e == cudaSuccess)
+        for (int k = 0; k < iters; ++k)
+            for (int j = 0; j < 4; ++j) {
+                float t = 0.f;
+                cudaEventElapsedTime(&t, ev[5 * (size_t)k + j], ev[5 * (size_t)k + j + 1]);
+                acc[j] += t;
+            }
+    double na = 0;
+    const int kn = std::min(iters, 2 * kMaxJobs);
+    for (int k = 0; k < kn; ++k) na += hn[k];
+    for (auto &ee : ev) cudaEventDestroy(ee);
+    if (e != cudaSuccess) return cuda_fail(e, "profile iteration");
+    for (int j = 0; j < 4; ++j) ms[j] = acc[j] / iters;
+    *n_act_avg = na / kn;
+    return LQCD_OK;
 }
 
 int mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, const double *const *shifts,

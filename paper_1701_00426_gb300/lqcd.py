@@ -44,7 +44,7 @@ EXPORTED = [
     "lqcd_default_opts", "lqcd_last_error", "lqcd_version", "lqcd_create", "lqcd_destroy",
     "lqcd_set_opts", "lqcd_device_bytes", "lqcd_links_upload", "lqcd_links_download",
     "lqcd_deo_apply", "lqcd_deo_apply_ex", "lqcd_deo_apply_mrhs", "lqcd_mscg_solve",
-    "lqcd_mscg_solve_dev", "lqcd_cg_solve_mrhs", "lqcd_mscg_solve_packed",
+    "lqcd_mscg_solve_dev", "lqcd_cg_solve_mrhs", "lqcd_mscg_solve_packed", "lqcd_profile_iteration",
     "lqcd_serve_create", "lqcd_serve_register_field", "lqcd_serve_submit", "lqcd_serve_poll",
     "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy",
 ]
@@ -59,14 +59,15 @@ class lqcd_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("n_shift", ctypes.c_int), ("reliable_updates", ctypes.c_int),
                 ("refine_iters", ctypes.c_int), ("shift_iters", ctypes.c_int * MAX_SHIFTS),
                 ("true_resid", ctypes.c_double * MAX_SHIFTS), ("secs", ctypes.c_double),
-                ("bytes_moved", ctypes.c_double), ("status", ctypes.c_int)]
+                ("bytes_moved", ctypes.c_double), ("status", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
 
     def as_dict(self) -> dict:
         n = self.n_shift
         return {"iters": self.iters, "n_shift": n, "reliable_updates": self.reliable_updates,
                 "refine_iters": self.refine_iters, "shift_iters": list(self.shift_iters)[:n],
                 "true_resid": list(self.true_resid)[:n], "secs": self.secs,
-                "bytes_moved": self.bytes_moved, "status": self.status}
+                "bytes_moved": self.bytes_moved, "status": self.status,
+                "kernel_launches": self.kernel_launches}
 
 
 class lqcd_serve_stats(ctypes.Structure):
@@ -122,6 +123,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_mscg_solve_packed": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.POINTER(dp), ip,
                                                   dp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                   ctypes.POINTER(lqcd_solve_info)]),
+        "lqcd_profile_iteration": (ctypes.c_int, [vp, ctypes.c_double, dp, ctypes.c_int, vp, ctypes.c_int, dp, dp]),
         "lqcd_serve_create": (ctypes.c_int, [sz, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]),
         "lqcd_serve_register_field": (ctypes.c_int, [vp, ip, vp, sz, ip]),
         "lqcd_serve_submit": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, dp, ctypes.c_int,
@@ -283,6 +285,15 @@ class Context:
         if not (allow_noconv and st == LQCD_ENOCONV):
             check(st)
         return info.as_dict()
+
+    def profile_iteration(self, mass: float, shifts, b, iters: int = 20):
+        """Per-kernel average ms of one solver iteration (see lqcd_profile_iteration)."""
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        ms = (ctypes.c_double * 4)()
+        nact = ctypes.c_double()
+        check(self.lib.lqcd_profile_iteration(self.h, float(mass), sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                              sh.size, _dptr(b), int(iters), ms, ctypes.byref(nact)))
+        return list(ms), nact.value
 
     def cg_solve_mrhs(self, mass: float, sigma: float, tol: float, b: np.ndarray):
         """Host call: b [n_rhs, Vh, 3]; returns (x, [info per rhs])."""

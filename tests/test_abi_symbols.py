@@ -98,3 +98,66 @@ int main() {
         subprocess.run(["g++", "-std=c++17", "-O1", src, "-o", exe], check=True, capture_output=True)
         r = subprocess.run([exe], capture_output=True, text=True)
         assert r.returncode == 0 and r.stdout.strip() == "0"
+
+
+def test_integer_fp64_split_host():
+    """split_f64 (hi + lo floats from an IEEE double with integer operations)
+    compiled as host C++: |d - hi - lo| <= 2^-48 |d| inside the exponent
+    window, exact zero, and the out-of-window flag."""
+    import subprocess
+    import tempfile
+    common = open(os.path.join(ROOT, "paper_1701_00426_gb300", "csrc", "common.cuh")).read()
+    start = common.index("// Split an IEEE double into hi + lo floats")
+    end = common.index("// df64 -> nearest-ish IEEE double")
+    code = r'''
+#include <cstdio>
+#include <cstdint>
+#include <cstring>
+#include <cmath>
+#include <random>
+#define __device__
+#define __forceinline__ inline
+struct float2 { float x, y; };
+static inline float2 make_float2(float a, float b) { return {a, b}; }
+static inline int __double2hiint(double d) { uint64_t u; memcpy(&u, &d, 8); return (int)(uint32_t)(u >> 32); }
+static inline int __double2loint(double d) { uint64_t u; memcpy(&u, &d, 8); return (int)(uint32_t)u; }
+static inline uint32_t __funnelshift_l(uint32_t lo, uint32_t hi, unsigned s) {
+  return (uint32_t)((((uint64_t)hi << 32) | lo) << s >> 32); }
+static inline float __uint_as_float(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+static inline float __fsub_rn(float a, float b) { volatile float r = a - b; return r; }
+''' + common[start:end] + r'''
+int main() {
+  std::mt19937_64 g(7);
+  long bad_err = 0, n = 0; double worst = 0;
+  auto check = [&](double d) {
+    bool bad = false; float2 s = split_f64(d, bad);
+    if (bad) { ++bad_err; return; }
+    double err = std::fabs(d - ((double)s.x + (double)s.y));
+    double rel = d == 0 ? err : err / std::fabs(d);
+    if (rel > worst) worst = rel;
+    ++n;
+  };
+  std::uniform_real_distribution<double> u(-50, 50);
+  for (int i = 0; i < 2000000; ++i) { double m = (g() >> 11) * 0x1p-53 + 0.5; double d = std::ldexp(m, (int)u(g)); if (g() & 1) d = -d; check(d); }
+  for (int k = -55; k < 60; ++k) {              // powers of two, all-ones significands, ties
+    check(std::ldexp(1.0, k)); check(-std::ldexp(1.0, k));
+    check(std::nextafter(std::ldexp(1.0, k), 0.0)); check(std::nextafter(std::ldexp(1.0, k), 1e300));
+    check(std::ldexp(1.0 + 0x1p-24, k)); check(std::ldexp(1.0 + 0x1p-24 + 0x1p-52, k));
+    check(std::ldexp(1.0 + 3 * 0x1p-25, k)); check(std::ldexp(2.0 - 0x1p-24, k));
+  }
+  bool b0 = false; float2 z = split_f64(0.0, b0);
+  bool b1 = false; split_f64(1e30, b1);
+  bool b2 = false; split_f64(1e-30, b2);
+  bool b3 = false; split_f64(-0.0, b3);
+  printf("%ld %ld %.3e %d %d %d %d %g %g\n", n, bad_err, worst, (int)b0, (int)b1, (int)b2, (int)b3, z.x, z.y);
+  return !(bad_err == 0 && worst <= 0x1p-48 && !b0 && b1 && b2 && !b3 && z.x == 0 && z.y == 0);
+}
+'''
+    with tempfile.TemporaryDirectory() as td:
+        src = os.path.join(td, "t.cpp")
+        open(src, "w").write(code)
+        exe = os.path.join(td, "t")
+        subprocess.run(["g++", "-std=c++17", "-O1", "-ffp-contract=off", src, "-o", exe], check=True,
+                       capture_output=True)
+        r = subprocess.run([exe], capture_output=True, text=True)
+        assert r.returncode == 0, r.stdout
