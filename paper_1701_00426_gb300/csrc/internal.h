@@ -96,6 +96,17 @@ struct Workspace {
     uint64_t gen = 0;       // bumped on every reallocation (graph cache key)
 };
 
+struct WsPtrs {
+    void *r, *q, *t, *x, *ps;
+    double2 *r_hi;
+    double2 *t_nat;
+    double *part;
+    unsigned *ticket;   // [0] iteration kernels, [1] helpers
+    SolverState *st;
+    double *scal;       // helper reduction outputs (device doubles)
+    int ntiles;
+};
+
 struct GraphCache {
     uint64_t key = ~0ull;
     cudaGraphExec_t exec = nullptr;
@@ -142,6 +153,31 @@ int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, 
                    double2 *x, lqcd_solve_info *info, cudaStream_t s);
 int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, const double2 *b, int iters,
                       double ms[4], double *n_act_avg);
+// One multi-shift solve in flight (single, packed or served).
+struct JobRun {
+    lqcd_ctx *c = nullptr;
+    WsPtrs P;
+    int vp = 0, lf = 0;
+    const void *links = nullptr;
+    double mass = 0, tol = 0;
+    double shifts[kMaxShifts];
+    int n_shift = 0;
+    const double2 *b = nullptr;   // IEEE device source [3][Vh]
+    double2 *x = nullptr;         // IEEE device solutions [n][3][Vh]
+    double b2 = 0, scale = 1, bytes = 0;
+    bool zero = false;
+    uint64_t launches0 = 0;
+    lqcd_solve_info I;
+};
+int validate_solve(const lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol);
+int ensure_workspace_in(lqcd_ctx *c, Workspace &W, int vp, int n_shift, WsPtrs &P);
+int job_init(JobRun &J, lqcd_ctx *c, Workspace *W, double mass, const double *shifts, int n_shift, double tol,
+             const double2 *b, double2 *x);
+int job_setup(JobRun &J, cudaStream_t s);
+void job_fill(const JobRun &J, IterJob &out);
+int job_finish(JobRun &J, cudaStream_t s);
+void launch_iteration_packed(const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s);
+int run_packed_until_halt(lqcd_ctx *c, const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s);
 int mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, const double *const *shifts,
                       const int *n_shift, const double *tol, const double *const *b, double *const *x,
                       lqcd_solve_info *info);

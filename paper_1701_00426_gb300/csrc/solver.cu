@@ -203,20 +203,10 @@ void k_res_nat2_ext(const Geom &g, const double2 *L, const double2 *t, const dou
 }
 
 // ------------------------------------------------------------------ workspace
-struct WsPtrs {
-    void *r, *q, *t, *x, *ps;
-    double2 *r_hi;
-    double2 *t_nat;
-    double *part;
-    unsigned *ticket;   // [0] iteration kernels, [1] helpers
-    SolverState *st;
-    double *scal;       // helper reduction outputs (device doubles)
-    int ntiles;
-};
 
-static int ensure_workspace(lqcd_ctx *c, int vp, int n_shift, WsPtrs &P)
+
+int ensure_workspace_in(lqcd_ctx *c, Workspace &W, int vp, int n_shift, WsPtrs &P)
 {
-    Workspace &W = c->ws;
     const size_t Vh = c->Vh, n3 = 3 * Vh;
     const size_t E = vp == VP_DF ? sizeof(float4) : sizeof(float2);
     const size_t vec_bytes = (3 + 2 * (size_t)n_shift) * n3 * E;
@@ -252,6 +242,11 @@ static int ensure_workspace(lqcd_ctx *c, int vp, int n_shift, WsPtrs &P)
     W.prec = vp;
     W.n_shift = n_shift;
     return LQCD_OK;
+}
+
+static int ensure_workspace(lqcd_ctx *c, int vp, int n_shift, WsPtrs &P)
+{
+    return ensure_workspace_in(c, c->ws, vp, n_shift, P);
 }
 
 static inline unsigned nblk(long n, int bs = 256) { return (unsigned)((n + bs - 1) / bs); }
@@ -503,7 +498,7 @@ static int engine_mscg(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void 
         k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
     else
         k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
-    LQCD_CUDA(cudaGetLastError());    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaGetLastError());
     c->launches += 1;
     IterBatch<1> B;
     memset(&B, 0, sizeof B);
@@ -543,7 +538,7 @@ static int refine_shift(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void
             k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r_hi, P.r, n3, scale);
         else
             k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r_hi, P.r, n3, scale);
-        LQCD_CUDA(cudaGetLastError());        LQCD_CUDA(cudaGetLastError());
+        LQCD_CUDA(cudaGetLastError());
         c->launches += 1;
         SolverState S;
         const double rho = rr * scale * scale;
@@ -556,7 +551,7 @@ static int refine_shift(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void
             k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, 1);
         else
             k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, 1);
-        LQCD_CUDA(cudaGetLastError());        LQCD_CUDA(cudaGetLastError());
+        LQCD_CUDA(cudaGetLastError());
         c->launches += 1;
         IterBatch<1> B;
         memset(&B, 0, sizeof B);
@@ -609,85 +604,111 @@ static int refine_shift(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void
     return LQCD_OK;
 }
 
-// ------------------------------------------------------------------ public driver
-int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double2 *b,
-                   double2 *x, lqcd_solve_info *info, cudaStream_t s_user)
+// ------------------------------------------------------------------ jobs
+int validate_solve(const lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol)
 {
-    const auto t0 = std::chrono::steady_clock::now();
-    const uint64_t launches0 = c->launches;
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
-    if (!shifts || !b || !x) return fail(LQCD_EINVAL, "NULL argument");
+    if (!shifts) return fail(LQCD_EINVAL, "NULL shifts");
     if (n_shift < 1 || n_shift > LQCD_MAX_SHIFTS) return fail(LQCD_EINVAL, "n_shift must be in 1..32");
     if (!(tol > 0.0) || !std::isfinite(mass)) return fail(LQCD_EINVAL, "tol must be > 0 and mass finite");
-    for (int i = 0; i < n_shift; ++i)
+    double mn = shifts[0];
+    for (int i = 0; i < n_shift; ++i) {
         if (!(shifts[i] >= 0.0) || !std::isfinite(shifts[i])) return fail(LQCD_EINVAL, "shifts must be finite and >= 0");
-    if (mass * mass == 0.0) {
-        double mn = shifts[0];
-        for (int i = 1; i < n_shift; ++i) mn = std::min(mn, shifts[i]);
-        if (mn == 0.0) return fail(LQCD_EINVAL, "m^2 + min(shift) must be > 0 (A would be singular)");
+        mn = std::min(mn, shifts[i]);
     }
-    cudaStream_t s = c->stream;
-    if (s_user && s_user != s) LQCD_CUDA(cudaStreamSynchronize(s_user));
-    const int vp = c->opts.prec == LQCD_PREC_FP64 || c->opts.prec == LQCD_PREC_FP64_NATIVE ? VP_DF : VP_F32;
-    const void *links = nullptr;
-    const int lf = link_fmt_for(c, vp == VP_DF ? LQCD_PREC_FP64 : c->opts.prec, &links);
-    WsPtrs P;
-    int st = ensure_workspace(c, vp, n_shift, P);
-    if (st) return st;
+    if (!(mass * mass + mn > 0.0)) return fail(LQCD_EINVAL, "m^2 + min(shift) must be > 0 (A would be singular)");
+    return LQCD_OK;
+}
+
+// Prepare one multi-shift solve: ||b||, power-of-two scaling, engine-format
+// source, zero solutions, device scalars.  No iteration is launched.
+int job_setup(JobRun &J, cudaStream_t s)
+{
+    lqcd_ctx *c = J.c;
     const long n3 = 3 * (long)c->Vh;
-    lqcd_solve_info I;
-    memset(&I, 0, sizeof I);
-    I.n_shift = n_shift;
-    double b2;
-    if ((st = norm2_ieee(c, P, b, 1, s, b2))) return st;
-    if (!std::isfinite(b2)) return fail(LQCD_ENAN, "source contains NaN/Inf");
-    if (b2 == 0.0) {
-        LQCD_CUDA(cudaMemsetAsync(x, 0, (size_t)n_shift * n3 * sizeof(double2), s));
-        LQCD_CUDA(cudaStreamSynchronize(s));
-        if (info) *info = I;
+    memset(&J.I, 0, sizeof J.I);
+    J.I.n_shift = J.n_shift;
+    J.bytes = 0;
+    J.launches0 = c->launches;
+    int st;
+    if ((st = norm2_ieee(c, J.P, J.b, 1, s, J.b2))) return st;
+    if (!std::isfinite(J.b2)) return fail(LQCD_ENAN, "source contains NaN/Inf");
+    J.zero = J.b2 == 0.0;
+    SolverState S;
+    if (J.zero) {
+        memset(&S, 0, sizeof S);
+        S.halt = HALT_CONVERGED;
+        LQCD_CUDA(cudaMemcpyAsync(J.P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
+        LQCD_CUDA(cudaMemsetAsync(J.x, 0, (size_t)J.n_shift * n3 * sizeof(double2), s));
         return LQCD_OK;
     }
-    // 1) multi-shift iteration on the scaled source
-    const double scale = unit_scale(b2, 6.0 * c->Vh);
-    if (vp == VP_DF)
-        k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
+    J.scale = unit_scale(J.b2, 6.0 * c->Vh);
+    if (J.vp == VP_DF)
+        k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(J.b, J.P.r, n3, J.scale);
     else
-        k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
-    LQCD_CUDA(cudaGetLastError());    LQCD_CUDA(cudaGetLastError());
-    c->launches += 1;
+        k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(J.b, J.P.r, n3, J.scale);
+    LQCD_CUDA(cudaGetLastError());
     // FP64: iterate to half the tolerance; mixed: FP32 reaches ~1e-6 at best
-    const double tol_iter = vp == VP_DF ? 0.5 * tol : std::max(tol, 1e-6);
+    const double tol_iter = J.vp == VP_DF ? 0.5 * J.tol : std::max(J.tol, 1e-6);
+    init_state(S, J.mass, J.shifts, J.n_shift, tol_iter, J.b2 * J.scale * J.scale, c->opts.max_iter);
+    LQCD_CUDA(cudaMemcpyAsync(J.P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
+    if (J.vp == VP_DF)
+        k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(J.P.r, J.P.r, J.P.x, J.P.ps, n3, J.n_shift);
+    else
+        k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(J.P.r, J.P.r, J.P.x, J.P.ps, n3, J.n_shift);
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += 2;
+    return LQCD_OK;
+}
+
+void job_fill(const JobRun &J, IterJob &out) { fill_job(J.c, J.P, J.links, out); }
+
+// After the iterations: IEEE solutions, FP64 true residuals, refinement.
+int job_finish(JobRun &J, cudaStream_t s)
+{
+    lqcd_ctx *c = J.c;
+    const long n3 = 3 * (long)c->Vh;
+    int st;
+    if (J.zero) {
+        J.I.status = LQCD_OK;
+        return LQCD_OK;
+    }
     SolverState O;
-    double bytes = 0;
-    if ((st = engine_mscg(c, P, vp, lf, links, mass, shifts, n_shift, tol_iter, b2 * scale * scale, s, O, bytes))) return st;
-    I.iters = O.iters;
-    for (int i = 0; i < n_shift; ++i) I.shift_iters[i] = O.shift_iters[i];
-    const bool maxed = O.halt == HALT_MAXITER;
+    LQCD_CUDA(cudaMemcpyAsync(&O, J.P.st, sizeof O, cudaMemcpyDeviceToHost, s));
+    LQCD_CUDA(cudaStreamSynchronize(s));
     if (O.halt == HALT_NAN) return fail(LQCD_ENAN, "NaN/Inf or breakdown in the multi-shift iteration");
-    // 2) IEEE solutions, true residuals, per-shift refinement
-    for (int i = 0; i < n_shift; ++i) {
+    J.I.iters = O.iters;
+    double shift_it = 0;
+    for (int i = 0; i < J.n_shift; ++i) {
+        J.I.shift_iters[i] = O.shift_iters[i];
+        shift_it += O.shift_iters[i] ? O.shift_iters[i] : O.iters;
+    }
+    const double spin = J.vp == VP_DF ? 48.0 : 24.0;
+    J.bytes += (double)c->Vh * (O.iters * iter_bytes_base(J.vp, J.lf) + shift_it * 4 * spin);
+    const bool maxed = O.halt == HALT_MAXITER;
+    for (int i = 0; i < J.n_shift; ++i) {
         const size_t off = (size_t)i * n3;
-        if (vp == VP_DF)
-            k_vec_to_ieee<VP_DF><<<nblk(n3), 256, 0, s>>>((const float4 *)P.x + off, x + off, n3, 1.0 / scale, 0);
+        if (J.vp == VP_DF)
+            k_vec_to_ieee<VP_DF><<<nblk(n3), 256, 0, s>>>((const float4 *)J.P.x + off, J.x + off, n3, 1.0 / J.scale, 0);
         else
-            k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>((const float2 *)P.x + off, x + off, n3, 1.0 / scale, 0);
-        LQCD_CUDA(cudaGetLastError());        LQCD_CUDA(cudaGetLastError());
+            k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>((const float2 *)J.P.x + off, J.x + off, n3, 1.0 / J.scale, 0);
+        LQCD_CUDA(cudaGetLastError());
         c->launches += 1;
     }
     int status = maxed ? LQCD_ENOCONV : LQCD_OK;
-    if (vp == VP_DF || maxed) {
+    if (J.vp == VP_DF || maxed) {
         // FP64: the df64 iteration already ran to tol/2; check each shift in
         // native FP64 and correct the rare one above tol
-        for (int i = 0; i < n_shift; ++i) {
+        for (int i = 0; i < J.n_shift; ++i) {
             double res = 0;
             int it = 0, rel = 0;
-            if ((st = refine_shift(c, P, vp, lf, links, mass, shifts[i], b, b2, x + (size_t)i * n3, tol, !maxed, s,
-                                   res, it, rel, bytes)))
+            if ((st = refine_shift(c, J.P, J.vp, J.lf, J.links, J.mass, J.shifts[i], J.b, J.b2, J.x + (size_t)i * n3,
+                                   J.tol, !maxed, s, res, it, rel, J.bytes)))
                 return st;
-            I.true_resid[i] = res;
-            I.refine_iters += it;
-            I.reliable_updates += rel;
-            if (!(res <= tol)) status = LQCD_ENOCONV;
+            J.I.true_resid[i] = res;
+            J.I.refine_iters += it;
+            J.I.reliable_updates += rel;
+            if (!(res <= J.tol)) status = LQCD_ENOCONV;
         }
     } else {
         // mixed: every shift finished together by the batched CG (FP32
@@ -695,31 +716,86 @@ int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, 
         // reliable updates); the FP16 variant uses FP32 links here because
         // FP16 rounding times the condition number of the smallest shifts
         // exceeds one and would stall the reliable updates
-        const int lf2 = c->opts.recon == 12 || lf == LF_F16_12 ? LF_F32_12 : LF_F32_18;
-        for (int g0 = 0; g0 < n_shift; g0 += 16) {
-            const int ng = std::min(16, n_shift - g0);
-            lqcd_solve_info J[16];
-            memset(J, 0, sizeof J);
-            const int rc = mrhs_cg_core(c, mass, shifts + g0, ng, tol, b, 0, x + (size_t)g0 * n3, lf2, J, bytes);
+        const int lf2 = c->opts.recon == 12 || J.lf == LF_F16_12 ? LF_F32_12 : LF_F32_18;
+        for (int g0 = 0; g0 < J.n_shift; g0 += 16) {
+            const int ng = std::min(16, J.n_shift - g0);
+            lqcd_solve_info K[16];
+            memset(K, 0, sizeof K);
+            const int rc = mrhs_cg_core(c, J.mass, J.shifts + g0, ng, J.tol, J.b, 0, J.x + (size_t)g0 * n3, lf2, K,
+                                        J.bytes);
             if (rc != LQCD_OK && rc != LQCD_ENOCONV) return rc;
             int mx = 0;
             for (int k = 0; k < ng; ++k) {
-                I.true_resid[g0 + k] = J[k].true_resid[0];
-                I.reliable_updates += J[k].reliable_updates;
-                mx = std::max(mx, J[k].iters);
-                if (!(J[k].true_resid[0] <= tol)) status = LQCD_ENOCONV;
+                J.I.true_resid[g0 + k] = K[k].true_resid[0];
+                J.I.reliable_updates += K[k].reliable_updates;
+                mx = std::max(mx, K[k].iters);
+                if (!(K[k].true_resid[0] <= J.tol)) status = LQCD_ENOCONV;
             }
-            I.refine_iters += mx;
+            J.I.refine_iters += mx;
         }
     }
     LQCD_CUDA(cudaStreamSynchronize(s));
-    I.bytes_moved = bytes;
-    I.kernel_launches = (int)(c->launches - launches0);
-    I.secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-    I.status = status;
-    if (info) *info = I;
-    if (status == LQCD_ENOCONV) set_error("solver did not reach tol within max_iter");
+    J.I.bytes_moved = J.bytes;
+    J.I.kernel_launches = (int)(c->launches - J.launches0);
+    J.I.status = status;
     return status;
+}
+
+int job_init(JobRun &J, lqcd_ctx *c, Workspace *W, double mass, const double *shifts, int n_shift, double tol,
+             const double2 *b, double2 *x)
+{
+    int st = validate_solve(c, mass, shifts, n_shift, tol);
+    if (st) return st;
+    J.c = c;
+    J.vp = c->opts.prec == LQCD_PREC_FP64 || c->opts.prec == LQCD_PREC_FP64_NATIVE ? VP_DF : VP_F32;
+    J.lf = link_fmt_for(c, J.vp == VP_DF ? LQCD_PREC_FP64 : c->opts.prec, &J.links);
+    J.mass = mass;
+    J.n_shift = n_shift;
+    for (int i = 0; i < n_shift; ++i) J.shifts[i] = shifts[i];
+    J.tol = tol;
+    J.b = b;
+    J.x = x;
+    return ensure_workspace_in(c, W ? *W : c->ws, J.vp, n_shift, J.P);
+}
+
+// One packed iteration launch over several jobs (serving ticks).
+void launch_iteration_packed(const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s)
+{
+    launch_iteration<kMaxJobs>(B, B.tile_start[B.njobs], vp, lf, s);
+}
+
+int run_packed_until_halt(lqcd_ctx *c, const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s)
+{
+    std::vector<int> halts;
+    return run_until_halt<kMaxJobs>(c, B, vp, lf, c->opts.check_every, c->opts.max_iter, s, halts);
+}
+
+// ------------------------------------------------------------------ public drivers
+int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double2 *b,
+                   double2 *x, lqcd_solve_info *info, cudaStream_t s_user)
+{
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!b || !x) return fail(LQCD_EINVAL, "NULL argument");
+    JobRun J;
+    int st = job_init(J, c, nullptr, mass, shifts, n_shift, tol, b, x);
+    if (st) return st;
+    cudaStream_t s = c->stream;
+    if (s_user && s_user != s) LQCD_CUDA(cudaStreamSynchronize(s_user));
+    if ((st = job_setup(J, s))) return st;
+    if (!J.zero) {
+        IterBatch<1> B;
+        memset(&B, 0, sizeof B);
+        B.njobs = 1;
+        B.tile_start[1] = J.P.ntiles;
+        job_fill(J, B.job[0]);
+        std::vector<int> halts;
+        if ((st = run_until_halt<1>(c, B, J.vp, J.lf, c->opts.check_every, c->opts.max_iter, s, halts))) return st;
+    }
+    st = job_finish(J, s);
+    J.I.secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (info) *info = J.I;
+    if (st == LQCD_ENOCONV) set_error("solver did not reach tol within max_iter");
+    return st;
 }
 
 int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, const double2 *b, int iters,
@@ -750,7 +826,7 @@ int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shif
         k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
     else
         k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
-    LQCD_CUDA(cudaGetLastError());    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaGetLastError());
     c->launches += 1;
     IterBatch<1> B;
     memset(&B, 0, sizeof B);
@@ -820,8 +896,56 @@ int mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, const do
                       const int *n_shift, const double *tol, const double *const *b, double *const *x,
                       lqcd_solve_info *info)
 {
-    (void)ctxs; (void)n; (void)mass; (void)shifts; (void)n_shift; (void)tol; (void)b; (void)x; (void)info;
-    return fail(LQCD_EINVAL, "packed solve not built yet");
+    const auto t0 = std::chrono::steady_clock::now();
+    lqcd_ctx *c0 = ctxs[0];
+    cudaStream_t s = c0->stream;
+    std::vector<JobRun> J(n);
+    std::vector<DevBuf> bd(n), xd(n);
+    int st;
+    for (int i = 0; i < n; ++i) {
+        lqcd_ctx *c = ctxs[i];
+        if (!c || !b[i] || !x[i]) return fail(LQCD_EINVAL, "NULL context or buffer in packed solve");
+        if (c->device != c0->device) return fail(LQCD_EINVAL, "packed contexts must share a device");
+        for (int k = 0; k < i; ++k)
+            if (ctxs[k] == c) return fail(LQCD_EINVAL, "a context appears twice in a packed solve");
+        const size_t n3 = 3 * c->Vh;
+        if ((st = bd[i].ensure(n3 * sizeof(double2))) || (st = xd[i].ensure((size_t)n_shift[i] * n3 * sizeof(double2))))
+            return st;
+        if ((st = job_init(J[i], c, nullptr, mass[i], shifts[i], n_shift[i], tol[i], bd[i].as<double2>(),
+                           xd[i].as<double2>())))
+            return st;
+        if (i > 0 && J[i].vp != J[0].vp) return fail(LQCD_EINVAL, "packed contexts must use the same precision");
+        if (i > 0 && J[i].lf != J[0].lf) return fail(LQCD_EINVAL, "packed contexts must use the same link storage");
+        LQCD_CUDA(cudaStreamSynchronize(c->stream));
+        if ((st = host_to_soa(c, b[i], bd[i].as<double2>(), 1, s))) return st;
+        if ((st = job_setup(J[i], s))) return st;
+    }
+    IterBatch<kMaxJobs> B;
+    memset(&B, 0, sizeof B);
+    int nj = 0, tiles = 0;
+    for (int i = 0; i < n; ++i) {
+        if (J[i].zero) continue;
+        B.tile_start[nj] = tiles;
+        job_fill(J[i], B.job[nj]);
+        tiles += J[i].P.ntiles;
+        ++nj;
+    }
+    B.njobs = nj;
+    B.tile_start[nj] = tiles;
+    if (nj > 0 && (st = run_packed_until_halt(c0, B, J[0].vp, J[0].lf, s))) return st;
+    int status = LQCD_OK;
+    const double secs_iter = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int i = 0; i < n; ++i) {
+        st = job_finish(J[i], s);
+        if (st != LQCD_OK && st != LQCD_ENOCONV) return st;
+        if (st == LQCD_ENOCONV) status = st;
+        if ((st = soa_to_host(ctxs[i], xd[i].as<double2>(), x[i], n_shift[i], s))) return st;
+        LQCD_CUDA(cudaStreamSynchronize(s));
+        J[i].I.secs = secs_iter;
+        if (info) info[i] = J[i].I;
+    }
+    if (status == LQCD_ENOCONV) set_error("a packed solve did not reach tol within max_iter");
+    return status;
 }
 
 }  // namespace lqcd

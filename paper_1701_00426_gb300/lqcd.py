@@ -323,3 +323,71 @@ def mscg_solve_packed(ctxs, masses, shifts_list, tols, bs):
     infos = (lqcd_solve_info * n)()
     check(lib.lqcd_mscg_solve_packed(hs, n, ms, shp, ns, ts, bp, xp, infos))
     return x_arr, [i.as_dict() for i in infos]
+
+
+class Server:
+    """Continuous-batching solve server (wraps lqcd_server)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 16, max_queue: int = 1024):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        check(self.lib.lqcd_serve_create(int(hbm_budget_bytes), int(max_slots), int(max_queue), ctypes.byref(h)))
+        self.h = h
+        self.fields = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lqcd_serve_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def register_field(self, dims, links: np.ndarray) -> int:
+        dims = tuple(int(d) for d in dims)
+        V = int(np.prod(dims))
+        u = _c128(links, (4, V, 3, 3))
+        fid = ctypes.c_int()
+        check(self.lib.lqcd_serve_register_field(self.h, (ctypes.c_int * 4)(*dims), _ptr(u), u.size * 2,
+                                                 ctypes.byref(fid)))
+        self.fields[fid.value] = dims
+        return fid.value
+
+    def submit(self, field_id: int, mass: float, shifts, tol: float, b: np.ndarray) -> int:
+        """Returns a ticket; raises LqcdError(LQCD_EBUSY / LQCD_ENOMEM) on rejection."""
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        dims = self.fields.get(field_id)
+        bb = _c128(b, (int(np.prod(dims)) // 2, 3) if dims else np.shape(b))
+        t = ctypes.c_uint64()
+        check(self.lib.lqcd_serve_submit(self.h, int(field_id), float(mass),
+                                         sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), sh.size, float(tol),
+                                         _ptr(bb), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, field_id: int, n_shift: int):
+        """(x, info) when finished, None while running."""
+        V = int(np.prod(self.fields[field_id]))
+        x = np.empty((n_shift, V // 2, 3), np.complex128)
+        info = lqcd_solve_info()
+        st = self.lib.lqcd_serve_poll(self.h, ctypes.c_uint64(ticket), _ptr(x), ctypes.byref(info))
+        if st == LQCD_ENOTREADY:
+            return None
+        check(st)
+        return x, info.as_dict()
+
+    def drain(self, timeout_s: float = 0.0):
+        check(self.lib.lqcd_serve_drain(self.h, float(timeout_s)))
+
+    def stats(self) -> dict:
+        st = lqcd_serve_stats()
+        check(self.lib.lqcd_serve_stats_get(self.h, ctypes.byref(st)))
+        return st.as_dict()

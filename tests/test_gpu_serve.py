@@ -1,0 +1,135 @@
+"""Packed multi-lattice solves and the continuous-batching server (GPU).
+
+* a packed solve over lattices of different sizes gives, for each lattice,
+  exactly (bit for bit) the result of that lattice solved alone;
+* a served request gives the same solution alone and in a mix of
+  concurrent requests (bitwise: per-request reductions never mix);
+* admission never exceeds the HBM budget; rejection paths report
+  LQCD_ENOMEM / LQCD_EBUSY / LQCD_EINVAL / LQCD_ENOTREADY."""
+import time
+
+import numpy as np
+import pytest
+
+from paper_1701_00426_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(8, 8, 8, 8), (4, 6, 8, 10), (6, 6, 6, 6), (12, 12, 12, 12)]
+
+
+def test_packed_equals_solo(gpu, orc):
+    shifts = [inputs.log_shifts(15), [1e-3, 0.1], inputs.log_shifts(5, 1e-4, 10.0), [0.01]]
+    masses = [0.01, 0.05, 0.02, 0.1]
+    ctxs, bs, solo = [], [], []
+    for k, d in enumerate(SIZES):
+        c = gpu.Context(d)
+        c.links_upload(inputs.random_links(d, seed=100 + k))
+        b = inputs.gaussian_field(d, k=k)
+        x, _ = c.mscg_solve(masses[k], shifts[k], 1e-10, b)
+        ctxs.append(c)
+        bs.append(b)
+        solo.append(x)
+    xs, infos = gpu.mscg_solve_packed(ctxs, masses, shifts, [1e-10] * 4, bs)
+    for k, d in enumerate(SIZES):
+        assert np.array_equal(xs[k], solo[k]), f"lattice {d}"
+        assert max(infos[k]["true_resid"]) <= 1e-10
+        U = inputs.random_links(d, seed=100 + k)
+        assert orc.true_residual(d, U, masses[k], shifts[k][0], bs[k], xs[k][0]) <= 1e-10
+    for c in ctxs:
+        c.close()
+
+
+def _wait(srv, ticket, fid, n, timeout=120):
+    t0 = time.time()
+    while time.time() - t0 < timeout:
+        r = srv.poll(ticket, fid, n)
+        if r is not None:
+            return r
+        time.sleep(0.002)
+    raise TimeoutError
+
+
+def test_served_request_alone_equals_in_mix(gpu, orc):
+    with gpu.Server(8 << 30, max_slots=8, max_queue=64) as srv:
+        fids = [srv.register_field(d, inputs.random_links(d, seed=200 + k)) for k, d in enumerate(SIZES)]
+        target = (fids[0], 0.01, inputs.log_shifts(8), 1e-10, inputs.gaussian_field(SIZES[0], k=7))
+        t = srv.submit(*target)
+        x_alone, info_alone = _wait(srv, t, fids[0], 8)
+        # the same request among others arriving before and after it
+        others = []
+        rng = np.random.default_rng(3)
+        for k in range(6):
+            f = int(rng.integers(0, len(fids)))
+            n = int(rng.integers(1, 9))
+            others.append((srv.submit(fids[f], 0.02, inputs.log_shifts(n, 1e-4, 1.0), 1e-8,
+                                      inputs.gaussian_field(SIZES[f], k=20 + k)), f, n))
+            if k == 2:
+                t2 = srv.submit(*target)
+        x_mix, info_mix = _wait(srv, t2, fids[0], 8)
+        for tk, f, n in others:
+            x, info = _wait(srv, tk, fids[f], n)
+            assert max(info["true_resid"]) <= 1e-8
+        srv.drain(60)
+        st = srv.stats()
+    assert np.array_equal(x_alone, x_mix)
+    assert info_alone["iters"] == info_mix["iters"]
+    U = inputs.random_links(SIZES[0], seed=200)
+    for i, s in enumerate(inputs.log_shifts(8)):
+        assert orc.true_residual(SIZES[0], U, 0.01, s, target[4], x_mix[i]) <= 1e-10
+    assert st["completed"] == 8 and st["p99_latency"] >= st["p50_latency"] > 0
+    assert st["hbm_in_use"] <= st["hbm_budget"]
+
+
+def test_admission_respects_budget(gpu):
+    d = (8, 8, 8, 8)
+    with gpu.Server(64 << 20, max_slots=8, max_queue=64) as srv:
+        fid = srv.register_field(d, inputs.random_links(d))
+        tickets = [srv.submit(fid, 0.05, [1e-3, 0.1, 1.0], 1e-9, inputs.gaussian_field(d, k=k)) for k in range(10)]
+        peak = 0
+        done = {}
+        t0 = time.time()
+        while len(done) < len(tickets) and time.time() - t0 < 120:
+            st = srv.stats()
+            peak = max(peak, st["hbm_in_use"])
+            assert st["hbm_in_use"] <= st["hbm_budget"]
+            for t in tickets:
+                if t not in done:
+                    r = srv.poll(t, fid, 3)
+                    if r is not None:
+                        done[t] = r
+        assert len(done) == len(tickets)
+        for x, info in done.values():
+            assert max(info["true_resid"]) <= 1e-9
+
+
+def test_rejections(gpu):
+    d = (4, 4, 4, 4)
+    with gpu.Server(16 << 20, max_slots=1, max_queue=2) as srv:
+        with pytest.raises(gpu.LqcdError) as e:  # 12^4 links in every storage format exceed 16 MB
+            srv.register_field((12, 12, 12, 12), inputs.random_links((12, 12, 12, 12)))
+        assert e.value.status == gpu.LQCD_ENOMEM
+        fid = srv.register_field(d, inputs.random_links(d))
+        b = inputs.gaussian_field(d)
+        with pytest.raises(gpu.LqcdError) as e:
+            srv.submit(fid, 0.1, [-1.0], 1e-8, b)
+        assert e.value.status == gpu.LQCD_EINVAL
+        with pytest.raises(gpu.LqcdError) as e:
+            srv.submit(99, 0.1, [0.0], 1e-8, b)
+        assert e.value.status == gpu.LQCD_EINVAL
+        with pytest.raises(gpu.LqcdError) as e:
+            srv.poll(12345, fid, 1)
+        assert e.value.status == gpu.LQCD_EINVAL
+        got_busy = False
+        tickets = []
+        for k in range(50):
+            try:
+                tickets.append(srv.submit(fid, 0.01, inputs.log_shifts(8), 1e-10, b))
+            except gpu.LqcdError as ex:
+                assert ex.status == gpu.LQCD_EBUSY
+                got_busy = True
+                break
+        assert got_busy
+        srv.drain(120)
+        for t in tickets:
+            assert srv.poll(t, fid, 8) is not None
