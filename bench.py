@@ -123,9 +123,17 @@ def max_over_ranks(v: float, world: int) -> float:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_throughput(steps: int, t_ms_local: float, world: int):
+    """Replicas: every rank ran `steps` solves; the job's time is the slowest
+    rank's.  Returns (solves/s of the whole job, max-over-ranks ms)."""
+    t_max = max_over_ranks(t_ms_local, world)
+    return world * steps / (t_max * 1e-3), t_max
 
 
 # ---------------------------------------------------------------- oracle (CPU)
@@ -186,6 +194,137 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "sample_wall_s": round(wall, 1)}
     print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- extra configs
+def batched_bench(lqcd, inputs, torch, hbm_peak):
+    """24^4: multi-RHS D_eo (ns per field-site, link loads shared by 1/4/8/16
+    fields) and the batched CG (m = 0.1, one shift, FP32 iterations with FP64
+    reliable updates) against n single-field solves."""
+    dims = (24, 24, 24, 24)
+    U = inputs.random_links(dims)
+    out = {"lattice": list(dims), "deo_fp32_12r": {}, "cg": {}}
+    with lqcd.Context(dims, prec=lqcd.PREC_FP32, recon=12) as c:
+        c.links_upload(U)
+        del U
+        s = torch.cuda.current_stream()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        for n in (1, 4, 8, 16):
+            x = torch.randn((3, c.Vh, n), dtype=torch.complex64, device="cuda")
+            o = torch.empty_like(x)
+            for _ in range(3):
+                c.deo_apply_mrhs(0, n, 12, x, o, s)
+            ts = []
+            for _ in range(10):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                c.deo_apply_mrhs(0, n, 12, x, o, s)
+                e1.record(s)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            med = float(np.median(ts))
+            bps = 384.0 + 48.0 * n
+            out["deo_fp32_12r"][str(n)] = {"ns_per_field_site": round(med * 1e6 / (c.Vh * n), 4),
+                                           "GB_s": round(bps * c.Vh / (med * 1e-3) / 1e9, 1)}
+        b = np.stack([inputs.gaussian_field(dims, k=j) for j in range(16)])
+        t0 = time.perf_counter()
+        for j in range(4):
+            c.cg_solve_mrhs(0.1, 0.0, 1e-10, b[j:j + 1])
+        t1 = time.perf_counter()
+        x16, inf16 = c.cg_solve_mrhs(0.1, 0.0, 1e-10, b)
+        t2 = time.perf_counter()
+        single = 4 / (t1 - t0)
+        out["cg"] = {"single_solves_per_s": round(single, 2), "batched16_solves_per_s": round(16 / (t2 - t1), 2),
+                     "speedup": round((16 / (t2 - t1)) / single, 2),
+                     "max_true_resid": max(i["true_resid"][0] for i in inf16),
+                     "iters": max(i["iters"] for i in inf16)}
+    return out
+
+
+def packed_bench(lqcd, inputs):
+    """8^4, 12^4, 16^4, 20^4 solved together in shared launches vs one after
+    another (15 shifts, m = 0.01, tol 1e-10, FP64); results compared bitwise."""
+    sizes = [(8,) * 4, (12,) * 4, (16,) * 4, (20,) * 4]
+    shifts = inputs.log_shifts(15)
+    ctxs, bs = [], []
+    for k, d in enumerate(sizes):
+        c = lqcd.Context(d)
+        c.links_upload(inputs.random_links(d))
+        ctxs.append(c)
+        bs.append(inputs.gaussian_field(d, k=k))
+    for c, b in zip(ctxs, bs):  # warm
+        c.mscg_solve(MASS, shifts, TOL, b)
+    t0 = time.perf_counter()
+    solo = [c.mscg_solve(MASS, shifts, TOL, b)[0] for c, b in zip(ctxs, bs)]
+    t1 = time.perf_counter()
+    xs, infos = lqcd.mscg_solve_packed(ctxs, [MASS] * 4, [shifts] * 4, [TOL] * 4, bs)
+    t2 = time.perf_counter()
+    same = all(np.array_equal(a, b) for a, b in zip(xs, solo))
+    for c in ctxs:
+        c.close()
+    return {"lattices": ["8^4", "12^4", "16^4", "20^4"], "separate_s": round(t1 - t0, 4),
+            "packed_s": round(t2 - t1, 4), "speedup": round((t1 - t0) / (t2 - t1), 3),
+            "bitwise_equal_to_separate": same, "max_true_resid": max(max(i["true_resid"]) for i in infos)}
+
+
+def serving_bench(lqcd, inputs, n_req=40):
+    """Poisson stream of multi-shift requests over resident 8^4/16^4/24^4/32^4
+    fields (1..16 shifts log-spaced in [1e-5, 1e2], tol 1e-8 or 1e-10,
+    m = 0.01), 16 GB budget.  A burst run measures capacity; a Poisson run at
+    ~70% of it measures latency."""
+    sizes = [(8,) * 4, (16,) * 4, (24,) * 4, (32,) * 4]
+    rng = np.random.default_rng(inputs.ARRIVAL_SEED)
+    reqs = []
+    for k in range(n_req):
+        f = int(rng.integers(0, 4))
+        ns = int(rng.integers(1, 17))
+        tol = [1e-8, 1e-10][int(rng.integers(0, 2))]
+        reqs.append((f, ns, tol, k))
+    res = {}
+    with lqcd.Server(16 << 30, max_slots=16, max_queue=4096) as srv:
+        fids = [srv.register_field(d, inputs.random_links(d)) for d in sizes]
+        srcs = {f: inputs.gaussian_field(sizes[f], k=100 + f) for f in range(4)}
+
+        def run(arrivals):
+            """Submit at the given offsets; returns (wall, per-request latencies)."""
+            t0 = time.perf_counter()
+            pend, lat = [], []
+            i = 0
+            while i < len(reqs) or pend:
+                now = time.perf_counter() - t0
+                while i < len(reqs) and arrivals[i] <= now:
+                    f, ns, tol, k = reqs[i]
+                    pend.append((srv.submit(fids[f], MASS, inputs.log_shifts(ns), tol, srcs[f]), f, ns,
+                                 time.perf_counter()))
+                    i += 1
+                keep = []
+                for t, f, ns, ts in pend:
+                    r = srv.poll(t, fids[f], ns)
+                    if r is None:
+                        keep.append((t, f, ns, ts))
+                    else:
+                        lat.append(time.perf_counter() - ts)
+                        assert max(r[1]["true_resid"]) <= 1e-8
+                pend = keep
+                time.sleep(0.0005)
+            return time.perf_counter() - t0, np.array(lat)
+
+        wall, lat = run(np.zeros(len(reqs)))
+        cap = len(reqs) / wall
+        res["burst"] = {"requests": len(reqs), "solves_per_s": round(cap, 3), "wall_s": round(wall, 2),
+                        "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+                        "p99_latency_s": round(float(np.percentile(lat, 99)), 4)}
+        rate = 0.7 * cap
+        wall, lat = run(inputs.poisson_arrivals(rate, len(reqs)))
+        res["poisson"] = {"rate_hz": round(rate, 3), "requests": len(reqs),
+                          "solves_per_s": round(len(reqs) / wall, 3),
+                          "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+                          "p99_latency_s": round(float(np.percentile(lat, 99)), 4)}
+        st = srv.stats()
+        res["hbm_budget"] = st["hbm_budget"]
+        res["ticks"] = st["ticks"]
+    return res
 
 
 # ---------------------------------------------------------------- ours
@@ -266,8 +405,7 @@ def run_ours(args, rank, world, local):
         torch.cuda.synchronize()
     barrier(world)
     t_ms = e0.elapsed_time(e1)
-    t_max = max_over_ranks(t_ms, world)
-    value = world * args.steps / (t_max * 1e-3)
+    value, t_max = job_throughput(args.steps, t_ms, world)
     clocks = clk.summary()
     launches = int(sum(i["kernel_launches"] for i in infos))
     worst_res = float(max(max(i["true_resid"]) for i in infos))
@@ -315,16 +453,19 @@ def run_ours(args, rank, world, local):
     # mixed precision on the same workload
     mixed = {}
     for name, prec, recon in [("fp32_12r", 1, 12), ("fp16_12r", 2, 12)]:
-        ctx.set_opts(prec=prec, recon=recon)
-        ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        mi = ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        mixed[name] = {"solves_per_s": round(1.0 / dt, 4), "speedup_vs_fp64": round((1.0 / dt) / value, 3),
-                       "max_true_resid": max(mi["true_resid"]), "iters": mi["iters"],
-                       "refine_iters": mi["refine_iters"], "reliable_updates": mi["reliable_updates"]}
+        try:
+            ctx.set_opts(prec=prec, recon=recon)
+            ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mi = ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            mixed[name] = {"solves_per_s": round(1.0 / dt, 4), "speedup_vs_fp64": round((1.0 / dt) / value, 3),
+                           "max_true_resid": max(mi["true_resid"]), "iters": mi["iters"],
+                           "refine_iters": mi["refine_iters"], "reliable_updates": mi["reliable_updates"]}
+        except Exception as exc:  # reported, never hidden
+            mixed[name] = {"error": repr(exc)}
     ctx.set_opts(prec=0, recon=18)
     ctx.close()
     del bd, xd
@@ -332,6 +473,19 @@ def run_ours(args, rank, world, local):
 
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     sweep = deo_sweep(lqcd, inputs, torch, flush, hbm_peak, args.sweep)
+    del flush
+    torch.cuda.empty_cache()
+    extras = {}
+    for name, fn in [("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
+                     ("packed", lambda: packed_bench(lqcd, inputs)),
+                     ("serving", lambda: serving_bench(lqcd, inputs))]:
+        if name in args.skip:
+            continue
+        try:
+            extras[name] = fn()
+        except Exception as exc:  # reported, never hidden
+            extras[name] = {"error": repr(exc)}
+        torch.cuda.empty_cache()
 
     # CPU baseline: the oracle on a bounded sample of the same workload
     n_iter, src = oracle_iteration_count()
@@ -352,7 +506,7 @@ def run_ours(args, rank, world, local):
             "iters": it["iters"], "refine_iters": it["refine_iters"], "max_true_resid": worst_res,
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "roofline": roofline,
             "cpu_baseline": cpu, "kernels": kernels, "n_active_avg": round(nact, 2),
-            "mixed": mixed, "deo": sweep}
+            "mixed": mixed, "deo": sweep, **extras}
     print(json.dumps(line), flush=True)
 
 
@@ -364,6 +518,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sweep", type=int, nargs="*", default=[16, 24, 32, 48])
     ap.add_argument("--lattice", type=int, default=32, help="side of the solve lattice (default 32)")
+    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: batched packed serving")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
     args = ap.parse_args()

@@ -1,7 +1,12 @@
 // deo.cu -- link upload / storage conversion, host <-> device spinor
 // layouts, and the stand-alone D_eo / D_oe launches of the C ABI.
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
 
 #include "deo_core.cuh"
 #include "internal.h"
@@ -172,7 +177,7 @@ int soa_to_host(lqcd_ctx *c, const double2 *dev_soa, double *host, int nf, cudaS
 __global__ void __launch_bounds__(kTile, 2)
     k_deo_df_ieee(Geom g, const float4 *__restrict__ L, const double2 *__restrict__ in, double2 *__restrict__ out, int P)
 {
-    const int i = blockIdx.x * kTile + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.Vh) return;
     Stencil S;
     make_stencil(g, i, P, S);
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(kTile, 2)
 __global__ void __launch_bounds__(kTile, 2)
     k_deo_nat(Geom g, const double2 *__restrict__ L, const double2 *__restrict__ in, double2 *__restrict__ out, int P)
 {
-    const int i = blockIdx.x * kTile + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.Vh) return;
     Stencil S;
     make_stencil(g, i, P, S);
@@ -207,7 +212,7 @@ template <int LF>
 __global__ void __launch_bounds__(kTile)
     k_deo_f32(Geom g, const void *__restrict__ L, const float2 *__restrict__ in, float2 *__restrict__ out, int P)
 {
-    const int i = blockIdx.x * kTile + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.Vh) return;
     Stencil S;
     make_stencil(g, i, P, S);
@@ -217,37 +222,152 @@ __global__ void __launch_bounds__(kTile)
     for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
 }
 
+// ------------------------------------------------------------------ autotuner
+// Threads per block of the stand-alone D_eo kernels, chosen per (variant,
+// lattice) by timing 64, 128 and 256 on the first call (CUDA events on the
+// call's stream; D_eo does not depend on the block size, so the tuning runs
+// produce the right output).  Cached for the process and, when the
+// environment variable LQCD_TUNE_CACHE names a file, across processes.
+// During stream capture the default (256) is used without tuning.
+static std::mutex g_tune_mu;
+static std::map<std::string, int> g_tune;
+static bool g_tune_loaded = false;
+
+static std::string tune_key(const lqcd_ctx *c, int variant)
+{
+    char buf[128];
+    snprintf(buf, sizeof buf, "deo v%d %dx%dx%dx%d", variant, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
+    return buf;
+}
+
+static void tune_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char *f = getenv("LQCD_TUNE_CACHE");
+    if (!f) return;
+    FILE *fp = fopen(f, "r");
+    if (!fp) return;
+    char line[256];
+    while (fgets(line, sizeof line, fp)) {
+        char k1[16];
+        int v, d0, d1, d2, d3, bs;
+        if (sscanf(line, "%15s v%d %dx%dx%dx%d %d", k1, &v, &d0, &d1, &d2, &d3, &bs) == 7) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "%s v%d %dx%dx%dx%d", k1, v, d0, d1, d2, d3);
+            g_tune[buf] = bs;
+        }
+    }
+    fclose(fp);
+}
+
+static void tune_save(const std::string &key, int bs)
+{
+    const char *f = getenv("LQCD_TUNE_CACHE");
+    if (!f) return;
+    FILE *fp = fopen(f, "a");
+    if (!fp) return;
+    fprintf(fp, "%s %d\n", key.c_str(), bs);
+    fclose(fp);
+}
+
+template <class Launch>
+static int tuned_launch(lqcd_ctx *c, int variant, cudaStream_t s, Launch launch)
+{
+    const std::string key = tune_key(c, variant);
+    int bs = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        tune_load();
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) bs = it->second;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    if (bs == 0 && cap != cudaStreamCaptureStatusNone) bs = kTile;
+    if (bs == 0) {
+        const int cand[3] = {64, 128, 256};
+        float best = 1e30f;
+        cudaEvent_t e0, e1;
+        LQCD_CUDA(cudaEventCreate(&e0));
+        LQCD_CUDA(cudaEventCreate(&e1));
+        for (int k = 0; k < 3; ++k) {
+            launch(cand[k]);  // warm
+            float t = 0.f;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < 3; ++r) launch(cand[k]);
+            cudaEventRecord(e1, s);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&t, e0, e1);
+            c->launches += 4;
+            if (t < best) {
+                best = t;
+                bs = cand[k];
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        LQCD_CUDA(cudaGetLastError());
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = bs;
+        tune_save(key, bs);
+    }
+    launch(bs);
+    c->launches += 1;
+    return LQCD_OK;
+}
+
+int deo_tuned_block(const lqcd_ctx *c, int variant)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(c, variant));
+    return it == g_tune.end() ? 0 : it->second;
+}
+
 int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *out, cudaStream_t s)
 {
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
     if (P != 0 && P != 1) return fail(LQCD_EINVAL, "out_parity must be 0 or 1");
     if (!in || !out) return fail(LQCD_EINVAL, "NULL spinor pointer");
     if (in == out) return fail(LQCD_EINVAL, "in and out must not overlap");
-    const unsigned nb = (unsigned)((c->Vh + kTile - 1) / kTile);
+    const Geom g = c->g;
+    auto nb = [&](int bs) { return (unsigned)((c->Vh + bs - 1) / bs); };
+    int st = LQCD_OK;
     switch (prec) {
     case LQCD_PREC_FP64:
         if (recon != 18) return fail(LQCD_EINVAL, "FP64 D_eo uses 18-real links");
-        k_deo_df_ieee<<<nb, kTile, 0, s>>>(c->g, c->lnk_df.as<float4>(), (const double2 *)in, (double2 *)out, P);
+        st = tuned_launch(c, 0, s, [&](int bs) {
+            k_deo_df_ieee<<<nb(bs), bs, 0, s>>>(g, c->lnk_df.as<float4>(), (const double2 *)in, (double2 *)out, P);
+        });
         break;
     case LQCD_PREC_FP64_NATIVE:
         if (recon != 18) return fail(LQCD_EINVAL, "native FP64 D_eo uses 18-real links");
-        k_deo_nat<<<nb, kTile, 0, s>>>(c->g, c->lnk_nat.as<double2>(), (const double2 *)in, (double2 *)out, P);
+        st = tuned_launch(c, 1, s, [&](int bs) {
+            k_deo_nat<<<nb(bs), bs, 0, s>>>(g, c->lnk_nat.as<double2>(), (const double2 *)in, (double2 *)out, P);
+        });
         break;
     case LQCD_PREC_FP32:
         if (recon == 18)
-            k_deo_f32<LF_F32_18><<<nb, kTile, 0, s>>>(c->g, c->lnk_f18.ptr, (const float2 *)in, (float2 *)out, P);
+            st = tuned_launch(c, 2, s, [&](int bs) {
+                k_deo_f32<LF_F32_18><<<nb(bs), bs, 0, s>>>(g, c->lnk_f18.ptr, (const float2 *)in, (float2 *)out, P);
+            });
         else if (recon == 12)
-            k_deo_f32<LF_F32_12><<<nb, kTile, 0, s>>>(c->g, c->lnk_f12.ptr, (const float2 *)in, (float2 *)out, P);
+            st = tuned_launch(c, 3, s, [&](int bs) {
+                k_deo_f32<LF_F32_12><<<nb(bs), bs, 0, s>>>(g, c->lnk_f12.ptr, (const float2 *)in, (float2 *)out, P);
+            });
         else
             return fail(LQCD_EINVAL, "recon must be 18 or 12");
         break;
     case LQCD_PREC_FP16:
         if (recon != 12) return fail(LQCD_EINVAL, "FP16 links use 12-real storage");
-        k_deo_f32<LF_F16_12><<<nb, kTile, 0, s>>>(c->g, c->lnk_h12.ptr, (const float2 *)in, (float2 *)out, P);
+        st = tuned_launch(c, 4, s, [&](int bs) {
+            k_deo_f32<LF_F16_12><<<nb(bs), bs, 0, s>>>(g, c->lnk_h12.ptr, (const float2 *)in, (float2 *)out, P);
+        });
         break;
     default:
         return fail(LQCD_EINVAL, "unknown precision");
     }
+    if (st) return st;
     LQCD_CUDA(cudaGetLastError());
     return LQCD_OK;
 }
