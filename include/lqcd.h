@@ -153,6 +153,24 @@ int lqcd_links_download(lqcd_ctx *ctx, double *links, size_t n_doubles);
 int lqcd_deo_apply(lqcd_ctx *ctx, int out_parity, const void *in, void *out,
                    int where, void *stream);
 
+/* Same operation as lqcd_deo_apply with host buffers (where = 0), for
+ * callers that cannot allocate device memory -- for example a process whose
+ * device memory is handed out by another framework's pool allocator, or a
+ * loop that cannot pay for the device-wide synchronisation of cudaMalloc and
+ * cudaFree.  The paper has no counterpart of this call.
+ * It allocates nothing: the host input and output are staged through a
+ * fixed array inside the library (a device global of 3 x 3 x 131072
+ * complex128 = 18.9 MB), which every device that loads the library holds
+ * until the process exits.  in / out: host canonical spinors ([Vh][3]
+ * complex128), as for lqcd_deo_apply.  Lattices with V/2 > 131072 sites are
+ * rejected with LQCD_EINVAL.  The first call on a device looks up the
+ * array's device address (with that device current); make that first call
+ * before capturing work on any stream.  Every call uses the same array and
+ * leaves its contents behind, so calls that overlap on the GPU (from
+ * several threads, contexts or streams at once) race.  Synchronous, on the
+ * context's stream. */
+int lqcd_deo_apply_host_noalloc(lqcd_ctx *ctx, int out_parity, const double *in, double *out);
+
 /* Same operator in a chosen arithmetic on device spinors (asynchronous):
  *   prec LQCD_PREC_FP64, LQCD_PREC_FP64_NATIVE: complex128 spinors, recon 18;
  *   prec LQCD_PREC_FP32: complex64 spinors, recon 18 or 12;

@@ -142,6 +142,10 @@ namespace lqcd {
 size_t ctx_device_bytes(const lqcd_ctx *c);
 
 // deo.cu
+__global__ void k_aos_to_soa(const double2 *__restrict__ a, double2 *__restrict__ s, long Vh, int nf);
+__global__ void k_soa_to_aos(const double2 *__restrict__ s, double2 *__restrict__ a, long Vh, int nf);
+__global__ void k_deo_df_ieee(Geom g, const float4 *__restrict__ L, const double2 *__restrict__ in,
+                              double2 *__restrict__ out, int P);
 int deo_launch(lqcd_ctx *c, int out_parity, int prec, int recon, const void *in, void *out, cudaStream_t s);
 int upload_links(lqcd_ctx *c, const double *host, size_t n);
 int download_links(lqcd_ctx *c, double *host, size_t n);

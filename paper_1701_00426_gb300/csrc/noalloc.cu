@@ -1,0 +1,87 @@
+// noalloc.cu -- host-buffer D_eo / D_oe that allocates no device memory.
+//
+// lqcd_deo_apply with host buffers stages its input and output through
+// device buffers that it allocates.  Some callers cannot allow that: a
+// process whose device memory is handed out by another framework's pool
+// allocator, or a loop that cannot pay for the device-wide synchronisation
+// of cudaMalloc / cudaFree.  This variant runs the same kernels through one
+// fixed staging area that lives in the library itself: a file-scope device
+// array, created when the library is loaded on a device and kept until the
+// process exits.
+//
+// Host code cannot use the array's name as a device address: on the host it
+// names a stand-in object, and a kernel handed it would fault or, where the
+// GPU can reach host memory, use the wrong memory.  The device address is
+// therefore looked up once per device with cudaGetSymbolAddress, with that
+// device current, on the first call made on that device.
+#include <mutex>
+
+#include "internal.h"
+
+namespace lqcd {
+
+// Largest half lattice served: V/2 <= 131072 sites (16^4 is 32768, 20^4 is
+// 80000).  Layout: three regions of 3 * kNoAllocMaxVh complex128 each --
+// host-format staging, structure-of-arrays input, structure-of-arrays output.
+constexpr long kNoAllocMaxVh = 131072;
+constexpr size_t kNoAllocRegion = 3 * (size_t)kNoAllocMaxVh;  // double2 elements per region
+
+static __device__ __align__(256) double2 g_noalloc_stage[3 * kNoAllocRegion];
+
+static std::mutex g_noalloc_mu;
+static double2 *g_noalloc_ptr[64];  // device address per device ordinal (set up on first use)
+
+// Device address of the staging array on the current device.
+static int noalloc_stage(double2 **out)
+{
+    int dev = 0;
+    LQCD_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(LQCD_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation staging array");
+        g_noalloc_ptr[dev] = (double2 *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return LQCD_OK;
+}
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" int lqcd_deo_apply_host_noalloc(lqcd_ctx *c, int out_parity, const double *in, double *out)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    if (!in || !out) return fail(LQCD_EINVAL, "NULL host buffer");
+    if (out_parity != 0 && out_parity != 1) return fail(LQCD_EINVAL, "out_parity must be 0 or 1");
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if ((long)c->Vh > kNoAllocMaxVh)
+        return fail(LQCD_EINVAL, "lattice too large for lqcd_deo_apply_host_noalloc: V/2 = " +
+                                     std::to_string(c->Vh) + " exceeds its fixed staging of " +
+                                     std::to_string(kNoAllocMaxVh) + " sites");
+    double2 *stage = nullptr;
+    int st = noalloc_stage(&stage);
+    if (st) return st;
+    // Every element read below is written earlier in the same call, so the
+    // contents left by a previous call need no clearing.
+    double2 *aos = stage, *soa_in = stage + kNoAllocRegion, *soa_out = stage + 2 * kNoAllocRegion;
+    const size_t bytes = 3 * c->Vh * sizeof(double2);
+    const long Vh = (long)c->Vh;
+    const unsigned nb = (unsigned)((Vh + 255) / 256);
+    cudaStream_t s = c->stream;
+    LQCD_CUDA(cudaMemcpyAsync(aos, in, bytes, cudaMemcpyHostToDevice, s));
+    k_aos_to_soa<<<nb, 256, 0, s>>>(aos, soa_in, Vh, 1);
+    LQCD_CUDA(cudaGetLastError());
+    k_deo_df_ieee<<<(unsigned)((Vh + kTile - 1) / kTile), kTile, 0, s>>>(c->g, c->lnk_df.as<float4>(), soa_in,
+                                                                        soa_out, out_parity);
+    LQCD_CUDA(cudaGetLastError());
+    k_soa_to_aos<<<nb, 256, 0, s>>>(soa_out, aos, Vh, 1);
+    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaMemcpyAsync(out, aos, bytes, cudaMemcpyDeviceToHost, s));
+    LQCD_CUDA(cudaStreamSynchronize(s));
+    c->launches += 3;
+    return LQCD_OK;
+}

@@ -43,7 +43,7 @@ MAX_SHIFTS = 32
 EXPORTED = [
     "lqcd_default_opts", "lqcd_last_error", "lqcd_version", "lqcd_create", "lqcd_destroy",
     "lqcd_set_opts", "lqcd_device_bytes", "lqcd_links_upload", "lqcd_links_download",
-    "lqcd_deo_apply", "lqcd_deo_apply_ex", "lqcd_deo_apply_mrhs", "lqcd_mscg_solve",
+    "lqcd_deo_apply", "lqcd_deo_apply_host_noalloc", "lqcd_deo_apply_ex", "lqcd_deo_apply_mrhs", "lqcd_mscg_solve",
     "lqcd_mscg_solve_dev", "lqcd_cg_solve_mrhs", "lqcd_mscg_solve_packed", "lqcd_profile_iteration",
     "lqcd_serve_create", "lqcd_serve_register_field", "lqcd_serve_submit", "lqcd_serve_poll",
     "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy",
@@ -112,6 +112,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_links_upload": (ctypes.c_int, [vp, vp, sz]),
         "lqcd_links_download": (ctypes.c_int, [vp, vp, sz]),
         "lqcd_deo_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, ctypes.c_int, vp]),
+        "lqcd_deo_apply_host_noalloc": (ctypes.c_int, [vp, ctypes.c_int, vp, vp]),
         "lqcd_deo_apply_ex": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]),
         "lqcd_deo_apply_mrhs": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp]),
         "lqcd_mscg_solve": (ctypes.c_int, [vp, ctypes.c_double, dp, ctypes.c_int, ctypes.c_double, vp, vp,
@@ -248,6 +249,14 @@ class Context:
         a = _c128(inp, (self.Vh, 3))
         out = np.empty_like(a)
         check(self.lib.lqcd_deo_apply(self.h, int(out_parity), _ptr(a), _ptr(out), 0, None))
+        return out
+
+    def deo_apply_host_noalloc(self, out_parity: int, inp: np.ndarray) -> np.ndarray:
+        """Host call staged through the library's fixed device array (no device
+        allocation; lattices with V/2 <= 131072 sites)."""
+        a = _c128(inp, (self.Vh, 3))
+        out = np.empty_like(a)
+        check(self.lib.lqcd_deo_apply_host_noalloc(self.h, int(out_parity), _ptr(a), _ptr(out)))
         return out
 
     def deo_apply_dev(self, out_parity: int, inp, out, stream=None):
