@@ -226,17 +226,20 @@ int lqcd_mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass,
                            const double *tol, const double *const *b,
                            double *const *x, lqcd_solve_info *info);
 
-/* Diagnostics: run `iters` iterations of the multi-shift iteration of
- * lqcd_mscg_solve (same kernels, same precision as opts.prec) on the device
- * source b (complex128 device spinor), launching the four kernels of an
- * iteration one by one with CUDA events between them on the context's
- * stream.  ms_out[0..3] receive the average device time (ms) of
+/* Diagnostics: run up to `iters` iterations of the multi-shift iteration of
+ * lqcd_mscg_solve (same kernels, same precision as opts.prec, same stopping
+ * rule for tol, so shifts drop out as in a solve) on the device source b
+ * (complex128 device spinor), launching the four kernels of an iteration
+ * one by one with CUDA events between them on the context's stream.
+ * ms_out[0..3] receive the average device time (ms) over the iterations
+ * that ran of
  *   0: t = D_oe p            1: q = (m^2+sigma) p - D_eo t and <p,q>
  *   2: r -= alpha q, ||r||^2  3: x_i += alpha_i p_i, p_i = zeta_i r + beta_i p_i
  * and *n_active_avg the mean number of shifts updated by kernel 3.
  * Synchronous. */
 int lqcd_profile_iteration(lqcd_ctx *ctx, double mass, const double *shifts, int n_shift,
-                           const void *b, int iters, double ms_out[4], double *n_active_avg);
+                           double tol, const void *b, int iters, double ms_out[4],
+                           double *n_active_avg);
 
 /* ----------------------------------------------------------------- serving */
 

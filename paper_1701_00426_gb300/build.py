@@ -23,6 +23,8 @@ UNITS = ["api.cu", "deo.cu", "solver.cu", "mrhs.cu", "serve.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]
+# Extra preprocessor definitions for tuning builds (e.g. "-DLQCD_TILE_SITES=64").
+EXTRA = os.environ.get("LQCD_NVCC_DEFINES", "").split()
 
 
 def nvcc() -> str:
@@ -46,7 +48,7 @@ def _compile(unit: str, hdr_mtime: float, verbose: bool) -> str:
     obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_mtime):
         return obj
-    cmd = [nvcc(), *ARCH, *FLAGS, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *FLAGS, *EXTRA, "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

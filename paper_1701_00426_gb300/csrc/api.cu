@@ -230,11 +230,11 @@ int lqcd_mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_sh
     return mscg_solve_dev(c, mass, shifts, n_shift, tol, (const double2 *)b, (double2 *)x, info, (cudaStream_t)stream);
 }
 
-int lqcd_profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, const void *b, int iters,
-                           double ms_out[4], double *n_active_avg)
+int lqcd_profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const void *b,
+                           int iters, double ms_out[4], double *n_active_avg)
 {
     if (!c || !ms_out || !n_active_avg) return fail(LQCD_EINVAL, "NULL argument");
-    return profile_iteration(c, mass, shifts, n_shift, (const double2 *)b, iters, ms_out, n_active_avg);
+    return profile_iteration(c, mass, shifts, n_shift, tol, (const double2 *)b, iters, ms_out, n_active_avg);
 }
 
 int lqcd_cg_solve_mrhs(lqcd_ctx *c, double mass, double sigma, int n_rhs, double tol, const double *b, double *x,

@@ -369,6 +369,34 @@ __device__ __forceinline__ double block_reduce_acc(Acc2 A, double *smem /* NT/32
 
 // ------------------------------------------------------------------ load helpers
 __device__ __forceinline__ float4 ldg4(const float4 *p) { return __ldg(p); }
+
+// Loads of data streamed once per kernel (links): read-only path with an L2
+// evict-first policy, so that the neighbour spinors and Krylov vectors that
+// are re-read stay in L2.  Compiled out with -DLQCD_NO_L2_HINTS.
+__device__ __forceinline__ uint64_t l2_evict_first_policy()
+{
+#ifdef LQCD_NO_L2_HINTS
+    return 0;
+#else
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+#endif
+}
+
+__device__ __forceinline__ float4 ldg4_stream(const float4 *p, uint64_t pol)
+{
+#ifdef LQCD_NO_L2_HINTS
+    (void)pol;
+    return __ldg(p);
+#else
+    float4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+#endif
+}
 __device__ __forceinline__ float2 ldg2(const float2 *p) { return __ldg(p); }
 __device__ __forceinline__ double2 ldg2d(const double2 *p) { return __ldg(p); }
 

@@ -87,8 +87,9 @@ __device__ __forceinline__ void load_spinor_df(const void *in, int idx, int Vh, 
 __device__ __forceinline__ void load_link_df(const float4 *L, int mu, int par, int idx, int Vh, float4 (&U)[9])
 {
     const float4 *p = L + link_base(mu, par, 9, Vh) + idx;
+    const uint64_t pol = l2_evict_first_policy();
 #pragma unroll
-    for (int c = 0; c < 9; ++c) U[c] = ldg4(p + (size_t)c * Vh);
+    for (int c = 0; c < 9; ++c) U[c] = ldg4_stream(p + (size_t)c * Vh, pol);
 }
 
 // D applied at one site in df64.  Returns the six (re, im) x colour results

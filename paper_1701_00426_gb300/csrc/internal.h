@@ -79,6 +79,7 @@ struct IterJob {
 template <int NJ>
 struct IterBatch {
     int njobs;
+    int max_shift;              // largest n_shift of the jobs (grid height of the shift update)
     int tile_start[NJ + 1];
     IterJob job[NJ];
 };
@@ -104,7 +105,8 @@ struct WsPtrs {
     unsigned *ticket;   // [0] iteration kernels, [1] helpers
     SolverState *st;
     double *scal;       // helper reduction outputs (device doubles)
-    int ntiles;
+    int ntiles;         // tiles of the iteration kernels
+    int ntiles256;      // tiles (blocks) of the 256-thread helper kernels
 };
 
 struct GraphCache {
@@ -155,8 +157,8 @@ int soa_to_host(lqcd_ctx *c, const double2 *dev_soa, double *host, int nfields, 
 // solver.cu
 int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double2 *b,
                    double2 *x, lqcd_solve_info *info, cudaStream_t s);
-int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, const double2 *b, int iters,
-                      double ms[4], double *n_act_avg);
+int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double2 *b,
+                      int iters, double ms[4], double *n_act_avg);
 // One multi-shift solve in flight (single, packed or served).
 struct JobRun {
     lqcd_ctx *c = nullptr;

@@ -182,6 +182,7 @@ int lqcd_server::tick()
         B.tile_start[i] = tiles;
         job_fill(active[i]->job, B.job[i]);
         tiles += active[i]->job.P.ntiles;
+        B.max_shift = std::max(B.max_shift, active[i]->job.n_shift);
     }
     B.njobs = (int)std::min<size_t>(active.size(), kMaxJobs);
     B.tile_start[B.njobs] = tiles;

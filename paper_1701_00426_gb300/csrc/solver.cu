@@ -211,7 +211,8 @@ int ensure_workspace_in(lqcd_ctx *c, Workspace &W, int vp, int n_shift, WsPtrs &
     const size_t E = vp == VP_DF ? sizeof(float4) : sizeof(float2);
     const size_t vec_bytes = (3 + 2 * (size_t)n_shift) * n3 * E;
     const size_t ieee_bytes = 2 * n3 * sizeof(double2);
-    const int ntiles = (int)((Vh + kTile - 1) / kTile);
+    const int ntiles = (int)((Vh + kSites - 1) / kSites);
+    const int ntiles256 = (int)((Vh + kTile - 1) / kTile);
     int st;
     if (vec_bytes > W.vec.bytes || ieee_bytes > W.ieee.bytes) W.gen++;
     if ((st = W.vec.ensure(std::max(vec_bytes, W.vec.bytes)))) return st;
@@ -239,6 +240,7 @@ int ensure_workspace_in(lqcd_ctx *c, Workspace &W, int vp, int n_shift, WsPtrs &
     P.ticket = (unsigned *)W.tickets.ptr;
     P.st = (SolverState *)W.state.ptr;
     P.ntiles = ntiles;
+    P.ntiles256 = ntiles256;
     W.prec = vp;
     W.n_shift = n_shift;
     return LQCD_OK;
@@ -253,7 +255,7 @@ static inline unsigned nblk(long n, int bs = 256) { return (unsigned)((n + bs - 
 
 static int norm2_ieee(lqcd_ctx *c, const WsPtrs &P, const double2 *v, int nvec, cudaStream_t s, double &out)
 {
-    k_norm2_ieee<<<P.ntiles, kTile, 0, s>>>(v, (int)c->Vh, nvec, P.part, P.ticket + 1, P.ntiles, P.scal);
+    k_norm2_ieee<<<P.ntiles256, kTile, 0, s>>>(v, (int)c->Vh, nvec, P.part, P.ticket + 1, P.ntiles256, P.scal);
     LQCD_CUDA(cudaGetLastError());
     c->launches += 1;
     LQCD_CUDA(cudaMemcpyAsync(c->h_pinned_d, P.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -267,14 +269,14 @@ static int true_residual(lqcd_ctx *c, const WsPtrs &P, int vp, double a, const d
                          double2 *r_hi, void *r_lo, double lo_scale, cudaStream_t s, double &rr)
 {
     const double2 *L = c->lnk_nat.as<double2>();
-    k_res_nat1<<<P.ntiles, kTile, 0, s>>>(c->g, L, x, P.t_nat);
+    k_res_nat1<<<P.ntiles256, kTile, 0, s>>>(c->g, L, x, P.t_nat);
     LQCD_CUDA(cudaGetLastError());
     c->launches += 2;
     if (vp == VP_DF)
-        k_res_nat2<VP_DF><<<P.ntiles, kTile, 0, s>>>(c->g, L, P.t_nat, x, b, a, r_hi, r_lo, lo_scale, P.part,
+        k_res_nat2<VP_DF><<<P.ntiles256, kTile, 0, s>>>(c->g, L, P.t_nat, x, b, a, r_hi, r_lo, lo_scale, P.part,
                                                       P.ticket + 1, P.scal);
     else
-        k_res_nat2<VP_F32><<<P.ntiles, kTile, 0, s>>>(c->g, L, P.t_nat, x, b, a, r_hi, r_lo, lo_scale, P.part,
+        k_res_nat2<VP_F32><<<P.ntiles256, kTile, 0, s>>>(c->g, L, P.t_nat, x, b, a, r_hi, r_lo, lo_scale, P.part,
                                                        P.ticket + 1, P.scal);
     LQCD_CUDA(cudaGetLastError());
     LQCD_CUDA(cudaMemcpyAsync(c->h_pinned_d, P.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -294,32 +296,36 @@ double unit_scale_pub(double n2, double n)
 }
 
 // ------------------------------------------------------------------ iteration chunks
+// Kernel k (0: K1 .. 3: K4) of one iteration.
+template <int NJ>
+static void launch_kernel_k(const IterBatch<NJ> &B, int k, int ntot, int vp, int lf, cudaStream_t s)
+{
+    const dim3 g4((unsigned)ntot, (unsigned)(B.max_shift > 0 ? B.max_shift : 1));
+    if (vp == VP_DF) {
+        if (k == 0) k_it_deo1<NJ, VP_DF, LF_DF18><<<ntot, kIterThreads, 0, s>>>(B);
+        if (k == 1) k_it_deo2<NJ, VP_DF, LF_DF18><<<ntot, kIterThreads, 0, s>>>(B);
+        if (k == 2) k_it_upd_r<NJ, VP_DF><<<ntot, kIterThreads, 0, s>>>(B);
+        if (k == 3) k_it_upd_shifts<NJ, VP_DF><<<g4, kIterThreads, 0, s>>>(B);
+        return;
+    }
+    if (k == 0) {
+        if (lf == LF_F32_18) k_it_deo1<NJ, VP_F32, LF_F32_18><<<ntot, kIterThreads, 0, s>>>(B);
+        else if (lf == LF_F32_12) k_it_deo1<NJ, VP_F32, LF_F32_12><<<ntot, kIterThreads, 0, s>>>(B);
+        else k_it_deo1<NJ, VP_F32, LF_F16_12><<<ntot, kIterThreads, 0, s>>>(B);
+    }
+    if (k == 1) {
+        if (lf == LF_F32_18) k_it_deo2<NJ, VP_F32, LF_F32_18><<<ntot, kIterThreads, 0, s>>>(B);
+        else if (lf == LF_F32_12) k_it_deo2<NJ, VP_F32, LF_F32_12><<<ntot, kIterThreads, 0, s>>>(B);
+        else k_it_deo2<NJ, VP_F32, LF_F16_12><<<ntot, kIterThreads, 0, s>>>(B);
+    }
+    if (k == 2) k_it_upd_r<NJ, VP_F32><<<ntot, kIterThreads, 0, s>>>(B);
+    if (k == 3) k_it_upd_shifts<NJ, VP_F32><<<g4, kIterThreads, 0, s>>>(B);
+}
+
 template <int NJ>
 static void launch_iteration(const IterBatch<NJ> &B, int ntot, int vp, int lf, cudaStream_t s)
 {
-    if (vp == VP_DF) {
-        k_it_deo1<NJ, VP_DF, LF_DF18><<<ntot, kTile, 0, s>>>(B);
-        k_it_deo2<NJ, VP_DF, LF_DF18><<<ntot, kTile, 0, s>>>(B);
-        k_it_upd_r<NJ, VP_DF><<<ntot, kTile, 0, s>>>(B);
-        k_it_upd_shifts<NJ, VP_DF><<<ntot, kTile, 0, s>>>(B);
-    } else {
-        switch (lf) {
-        case LF_F32_18:
-            k_it_deo1<NJ, VP_F32, LF_F32_18><<<ntot, kTile, 0, s>>>(B);
-            k_it_deo2<NJ, VP_F32, LF_F32_18><<<ntot, kTile, 0, s>>>(B);
-            break;
-        case LF_F32_12:
-            k_it_deo1<NJ, VP_F32, LF_F32_12><<<ntot, kTile, 0, s>>>(B);
-            k_it_deo2<NJ, VP_F32, LF_F32_12><<<ntot, kTile, 0, s>>>(B);
-            break;
-        default:
-            k_it_deo1<NJ, VP_F32, LF_F16_12><<<ntot, kTile, 0, s>>>(B);
-            k_it_deo2<NJ, VP_F32, LF_F16_12><<<ntot, kTile, 0, s>>>(B);
-            break;
-        }
-        k_it_upd_r<NJ, VP_F32><<<ntot, kTile, 0, s>>>(B);
-        k_it_upd_shifts<NJ, VP_F32><<<ntot, kTile, 0, s>>>(B);
-    }
+    for (int k = 0; k < 4; ++k) launch_kernel_k<NJ>(B, k, ntot, vp, lf, s);
 }
 
 void GraphCache::reset()
@@ -503,6 +509,7 @@ static int engine_mscg(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void 
     IterBatch<1> B;
     memset(&B, 0, sizeof B);
     B.njobs = 1;
+    B.max_shift = n_shift;
     B.tile_start[0] = 0;
     B.tile_start[1] = P.ntiles;
     fill_job(c, P, links, B.job[0]);
@@ -556,6 +563,7 @@ static int refine_shift(lqcd_ctx *c, const WsPtrs &P, int vp, int lf, const void
         IterBatch<1> B;
         memset(&B, 0, sizeof B);
         B.njobs = 1;
+        B.max_shift = 1;
         B.tile_start[1] = P.ntiles;
         fill_job(c, P, links, B.job[0]);
         for (int inner = 0; inner < 100000; ++inner) {
@@ -649,8 +657,19 @@ int job_setup(JobRun &J, cudaStream_t s)
         k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(J.b, J.P.r, n3, J.scale);
     LQCD_CUDA(cudaGetLastError());
     // FP64: iterate to half the tolerance; mixed: FP32 reaches ~1e-6 at best
-    const double tol_iter = J.vp == VP_DF ? 0.5 * J.tol : std::max(J.tol, 1e-6);
+    // both engines iterate to tol/2; the FP32 engine refreshes its residual
+    // in FP64 (reliable update) whenever it has fallen by delta
+    // FP16 links differ from the operator by ~1e-3 relative; with the
+    // condition numbers of the small shifts that error times kappa exceeds
+    // one, so FP16 iterations stop at a moderate residual (no reliable
+    // updates) and the FP32 batched refinement finishes every shift.
+    const bool f16 = J.lf == LF_F16_12;
+    const double tol_iter = f16 ? std::max(0.5 * J.tol, 3e-4) : 0.5 * J.tol;
     init_state(S, J.mass, J.shifts, J.n_shift, tol_iter, J.b2 * J.scale * J.scale, c->opts.max_iter);
+    if (J.vp == VP_F32) {
+        if (!f16) S.rel_stop2 = c->opts.delta_reliable * c->opts.delta_reliable * S.rho;
+        LQCD_CUDA(cudaMemsetAsync(J.x, 0, (size_t)J.n_shift * n3 * sizeof(double2), s));
+    }
     LQCD_CUDA(cudaMemcpyAsync(J.P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
     if (J.vp == VP_DF)
         k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(J.P.r, J.P.r, J.P.x, J.P.ps, n3, J.n_shift);
@@ -662,6 +681,53 @@ int job_setup(JobRun &J, cudaStream_t s)
 }
 
 void job_fill(const JobRun &J, IterJob &out) { fill_job(J.c, J.P, J.links, out); }
+
+// Reliable update of the FP32 multi-shift iteration: every shift's FP32
+// solution is added to its FP64 solution and cleared, the base residual is
+// replaced by the FP64 true residual of the base system (rescaled to O(1)
+// entries), and the search directions are kept (rescaled with it).  The
+// shifted residuals stay zeta_i times the base residual.
+int job_reliable_update(JobRun &J, cudaStream_t s)
+{
+    lqcd_ctx *c = J.c;
+    const long n3 = 3 * (long)c->Vh;
+    SolverState O;
+    LQCD_CUDA(cudaMemcpyAsync(&O, J.P.st, sizeof O, cudaMemcpyDeviceToHost, s));
+    LQCD_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < J.n_shift; ++i) {
+        const size_t off = (size_t)i * n3;
+        k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>((const float2 *)J.P.x + off, J.x + off, n3, 1.0 / J.scale, 1);
+    }
+    k_zero_vec<VP_F32><<<nblk(n3 * J.n_shift), 256, 0, s>>>(J.P.x, n3 * J.n_shift);
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += J.n_shift + 1;
+    double rr;
+    const double a0 = J.mass * J.mass + J.shifts[O.base];
+    int st = true_residual(c, J.P, VP_F32, a0, J.x + (size_t)O.base * n3, J.b, J.P.r_hi, nullptr, 1.0, s, rr);
+    if (st) return st;
+    if (!std::isfinite(rr)) return fail(LQCD_ENAN, "NaN/Inf in a reliable update");
+    const double old = J.scale;
+    J.scale = unit_scale(rr, 6.0 * c->Vh);
+    k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(J.P.r_hi, J.P.r, n3, J.scale);
+    k_scale_vec<VP_F32><<<nblk(n3 * J.n_shift), 256, 0, s>>>(J.P.ps, n3 * J.n_shift, (float)(J.scale / old));
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += 2;
+    SolverState U = O;
+    U.rho = rr * J.scale * J.scale;
+    U.rel_stop2 = c->opts.delta_reliable * c->opts.delta_reliable * U.rho;
+    U.tol2_b2 = 0.25 * J.tol * J.tol * J.b2 * J.scale * J.scale;
+    U.halt = HALT_NONE;
+    U.do_k4 = 0;
+    LQCD_CUDA(cudaMemcpyAsync(J.P.st, &U, sizeof U, cudaMemcpyHostToDevice, s));
+    ++J.I.reliable_updates;
+    // the iterated residual may already meet the target after the refresh
+    if (rr <= 0.25 * J.tol * J.tol * J.b2) {
+        U.halt = HALT_CONVERGED;
+        U.n_act = 0;
+        LQCD_CUDA(cudaMemcpyAsync(J.P.st, &U, sizeof U, cudaMemcpyHostToDevice, s));
+    }
+    return LQCD_OK;
+}
 
 // After the iterations: IEEE solutions, FP64 true residuals, refinement.
 int job_finish(JobRun &J, cudaStream_t s)
@@ -691,7 +757,7 @@ int job_finish(JobRun &J, cudaStream_t s)
         if (J.vp == VP_DF)
             k_vec_to_ieee<VP_DF><<<nblk(n3), 256, 0, s>>>((const float4 *)J.P.x + off, J.x + off, n3, 1.0 / J.scale, 0);
         else
-            k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>((const float2 *)J.P.x + off, J.x + off, n3, 1.0 / J.scale, 0);
+            k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>((const float2 *)J.P.x + off, J.x + off, n3, 1.0 / J.scale, 1);
         LQCD_CUDA(cudaGetLastError());
         c->launches += 1;
     }
@@ -786,10 +852,15 @@ int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, 
         IterBatch<1> B;
         memset(&B, 0, sizeof B);
         B.njobs = 1;
+        B.max_shift = J.n_shift;
         B.tile_start[1] = J.P.ntiles;
         job_fill(J, B.job[0]);
-        std::vector<int> halts;
-        if ((st = run_until_halt<1>(c, B, J.vp, J.lf, c->opts.check_every, c->opts.max_iter, s, halts))) return st;
+        for (;;) {
+            std::vector<int> halts;
+            if ((st = run_until_halt<1>(c, B, J.vp, J.lf, c->opts.check_every, c->opts.max_iter, s, halts))) return st;
+            if (halts[0] != HALT_RELIABLE) break;
+            if ((st = job_reliable_update(J, s))) return st;
+        }
     }
     st = job_finish(J, s);
     J.I.secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -798,97 +869,67 @@ int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, 
     return st;
 }
 
-int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, const double2 *b, int iters,
-                      double ms[4], double *n_act_avg)
+int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double2 *b,
+                      int iters, double ms[4], double *n_act_avg)
 {
-    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
-    if (!shifts || !b || n_shift < 1 || n_shift > LQCD_MAX_SHIFTS || iters < 1 || iters > 100000)
-        return fail(LQCD_EINVAL, "bad profile arguments");
-    cudaStream_t s = c->stream;
-    const int vp = c->opts.prec == LQCD_PREC_FP64 || c->opts.prec == LQCD_PREC_FP64_NATIVE ? VP_DF : VP_F32;
-    const void *links = nullptr;
-    const int lf = link_fmt_for(c, vp == VP_DF ? LQCD_PREC_FP64 : c->opts.prec, &links);
-    WsPtrs P;
-    int st = ensure_workspace(c, vp, n_shift, P);
+    if (!b || iters < 1 || iters > 100000) return fail(LQCD_EINVAL, "bad profile arguments");
+    JobRun J;
+    int st = job_init(J, c, nullptr, mass, shifts, n_shift, tol, b, nullptr);
     if (st) return st;
-    const long n3 = 3 * (long)c->Vh;
-    double b2;
-    if ((st = norm2_ieee(c, P, b, 1, s, b2))) return st;
-    const double scale = unit_scale(b2, 6.0 * c->Vh);
-    if (vp == VP_DF)
-        k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
-    else
-        k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(b, P.r, n3, scale);
+    cudaStream_t s = c->stream;
+    if ((st = job_setup(J, s))) return st;
+    if (J.zero) return fail(LQCD_EINVAL, "zero source");
+    // iterate as the solve does (same stopping rule), past its end if asked
     SolverState S;
-    init_state(S, mass, shifts, n_shift, 1e-300, b2 * scale * scale, iters + 1);
-    LQCD_CUDA(cudaMemcpyAsync(P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
-    if (vp == VP_DF)
-        k_init_vectors<VP_DF><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
-    else
-        k_init_vectors<VP_F32><<<nblk(n3), 256, 0, s>>>(P.r, P.r, P.x, P.ps, n3, n_shift);
-    LQCD_CUDA(cudaGetLastError());
-    c->launches += 1;
+    LQCD_CUDA(cudaMemcpy(&S, J.P.st, sizeof S, cudaMemcpyDeviceToHost));
+    S.max_iter = iters + 1;
+    LQCD_CUDA(cudaMemcpy(J.P.st, &S, sizeof S, cudaMemcpyHostToDevice));
     IterBatch<1> B;
     memset(&B, 0, sizeof B);
     B.njobs = 1;
-    B.tile_start[1] = P.ntiles;
-    fill_job(c, P, links, B.job[0]);
+    B.max_shift = n_shift;
+    B.tile_start[1] = J.P.ntiles;
+    job_fill(J, B.job[0]);
     std::vector<cudaEvent_t> ev(5 * (size_t)iters);
     for (auto &e : ev) LQCD_CUDA(cudaEventCreate(&e));
-    std::vector<int> nact(iters, 0);
-    int *hn = c->h_pinned;
-    const int ntot = P.ntiles;
-    for (int k = 0; k < iters; ++k) {
+    int *hn = nullptr;
+    LQCD_CUDA(cudaHostAlloc((void **)&hn, (size_t)iters * sizeof(int), cudaHostAllocDefault));
+    const int ntot = J.P.ntiles;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < iters && e == cudaSuccess; ++k) {
         cudaEvent_t *E = &ev[5 * (size_t)k];
         cudaEventRecord(E[0], s);
-        if (vp == VP_DF) {
-            k_it_deo1<1, VP_DF, LF_DF18><<<ntot, kTile, 0, s>>>(B);
-            cudaEventRecord(E[1], s);
-            k_it_deo2<1, VP_DF, LF_DF18><<<ntot, kTile, 0, s>>>(B);
-            cudaEventRecord(E[2], s);
-            k_it_upd_r<1, VP_DF><<<ntot, kTile, 0, s>>>(B);
-            cudaEventRecord(E[3], s);
-            k_it_upd_shifts<1, VP_DF><<<ntot, kTile, 0, s>>>(B);
-        } else {
-            if (lf == LF_F32_18) {
-                k_it_deo1<1, VP_F32, LF_F32_18><<<ntot, kTile, 0, s>>>(B);
-                cudaEventRecord(E[1], s);
-                k_it_deo2<1, VP_F32, LF_F32_18><<<ntot, kTile, 0, s>>>(B);
-            } else if (lf == LF_F32_12) {
-                k_it_deo1<1, VP_F32, LF_F32_12><<<ntot, kTile, 0, s>>>(B);
-                cudaEventRecord(E[1], s);
-                k_it_deo2<1, VP_F32, LF_F32_12><<<ntot, kTile, 0, s>>>(B);
-            } else {
-                k_it_deo1<1, VP_F32, LF_F16_12><<<ntot, kTile, 0, s>>>(B);
-                cudaEventRecord(E[1], s);
-                k_it_deo2<1, VP_F32, LF_F16_12><<<ntot, kTile, 0, s>>>(B);
-            }
-            cudaEventRecord(E[2], s);
-            k_it_upd_r<1, VP_F32><<<ntot, kTile, 0, s>>>(B);
-            cudaEventRecord(E[3], s);
-            k_it_upd_shifts<1, VP_F32><<<ntot, kTile, 0, s>>>(B);
+        for (int q = 0; q < 4; ++q) {
+            launch_kernel_k<1>(B, q, ntot, J.vp, J.lf, s);
+            cudaEventRecord(E[q + 1], s);
         }
-        cudaEventRecord(E[4], s);
         c->launches += 4;
-        if (k < 2 * kMaxJobs) cudaMemcpyAsync(hn + k, &P.st->n_act, sizeof(int), cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(hn + k, &J.P.st->n_act, sizeof(int), cudaMemcpyDeviceToHost, s);
     }
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    double acc[4] = {0, 0, 0, 0};
-    if (e == cudaSuccess)
-        for (int k = 0; k < iters; ++k)
-            for (int j = 0; j < 4; ++j) {
+    double acc[4] = {0, 0, 0, 0}, na = 0;
+    int counted = 0;
+    if (e == cudaSuccess) {
+        SolverState O;
+        e = cudaMemcpy(&O, J.P.st, sizeof O, cudaMemcpyDeviceToHost);
+        // only iterations that ran (the solve may converge before `iters`)
+        counted = std::min(iters, O.iters);
+        for (int k = 0; k < counted; ++k) {
+            for (int q = 0; q < 4; ++q) {
                 float t = 0.f;
-                cudaEventElapsedTime(&t, ev[5 * (size_t)k + j], ev[5 * (size_t)k + j + 1]);
-                acc[j] += t;
+                cudaEventElapsedTime(&t, ev[5 * (size_t)k + q], ev[5 * (size_t)k + q + 1]);
+                acc[q] += t;
             }
-    double na = 0;
-    const int kn = std::min(iters, 2 * kMaxJobs);
-    for (int k = 0; k < kn; ++k) na += hn[k];
+            na += hn[k];
+        }
+    }
     for (auto &ee : ev) cudaEventDestroy(ee);
+    cudaFreeHost(hn);
     if (e != cudaSuccess) return cuda_fail(e, "profile iteration");
-    for (int j = 0; j < 4; ++j) ms[j] = acc[j] / iters;
-    *n_act_avg = na / kn;
+    if (counted == 0) return fail(LQCD_EINVAL, "no iteration ran");
+    for (int q = 0; q < 4; ++q) ms[q] = acc[q] / counted;
+    *n_act_avg = na / counted;
     return LQCD_OK;
 }
 
@@ -925,6 +966,7 @@ int mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, const do
     int nj = 0, tiles = 0;
     for (int i = 0; i < n; ++i) {
         if (J[i].zero) continue;
+        B.max_shift = std::max(B.max_shift, J[i].n_shift);
         B.tile_start[nj] = tiles;
         job_fill(J[i], B.job[nj]);
         tiles += J[i].P.ntiles;

@@ -37,8 +37,9 @@ __device__ __forceinline__ int find_job(const IterBatch<NJ> &B)
 template <class Fn>
 __device__ __forceinline__ void reduce_finish(double *part, unsigned *ticket, int ntiles, int tile, double v, Fn fn)
 {
+    // blockDim.x is a multiple of 32 and at most 1024
     __shared__ int s_last;
-    __shared__ double s_red[kTile / 32];
+    __shared__ double s_red[32];
     if (threadIdx.x == 0) {
         part[tile] = v;
         __threadfence();
@@ -49,15 +50,15 @@ __device__ __forceinline__ void reduce_finish(double *part, unsigned *ticket, in
     if (!s_last) return;
     __threadfence();
     double s = 0.0;
-    for (int k = threadIdx.x; k < ntiles; k += kTile) s += __ldcg(part + k);
+    for (int k = threadIdx.x; k < ntiles; k += blockDim.x) s += __ldcg(part + k);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
     __syncthreads();
     if (threadIdx.x == 0) {
         double tot = 0.0;
-#pragma unroll
-        for (int k = 0; k < kTile / 32; ++k) tot += s_red[k];
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < nw; ++k) tot += s_red[k];
         fn(tot);
         *ticket = 0u;
         __threadfence();
@@ -149,9 +150,40 @@ template <int VP> struct VecT;
 template <> struct VecT<VP_DF> { using T = float4; };
 template <> struct VecT<VP_F32> { using T = float2; };
 
+// ------------------------------------------------------------------ launch shape
+// One thread per even site; a tile is kSites consecutive half-lattice sites
+// and one block of kIterThreads = kSites threads.  Reductions produce one
+// partial per tile, which fixes their order for a given lattice.  (A thread
+// per (site, colour) was measured slower: the three colour threads re-load
+// the neighbour spinors, and 64-site tiles made the reductions' atomics and
+// tails expensive.)
+#ifndef LQCD_TILE_SITES
+#define LQCD_TILE_SITES 128
+#endif
+#ifndef LQCD_ITER_MINB
+#define LQCD_ITER_MINB 4
+#endif
+constexpr int kSites = LQCD_TILE_SITES;
+constexpr int kIterThreads = kSites;
+
+template <int NT>
+__device__ __forceinline__ double block_reduce_acc_n(Acc2 A, double *smem)
+{
+    warp_reduce_acc(A);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) smem[w] = (double)A.s + (double)A.c;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < NT / 32; ++k) r += smem[k];
+    }
+    return r;
+}
+
 // ------------------------------------------------------------------ K1
 template <int NJ, int VP, int LF>
-__global__ void __launch_bounds__(kTile, 2) k_it_deo1(const __grid_constant__ IterBatch<NJ> B)
+__global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo1(const __grid_constant__ IterBatch<NJ> B)
 {
     using T = typename VecT<VP>::T;
     const int j = find_job(B);
@@ -160,7 +192,7 @@ __global__ void __launch_bounds__(kTile, 2) k_it_deo1(const __grid_constant__ It
     if ((int)blockIdx.x == B.tile_start[j] && threadIdx.x == 0) st->do_k4 = 0;
     if (st->halt) return;
     const int Vh = J.g.Vh;
-    const int i = ((int)blockIdx.x - B.tile_start[j]) * kTile + threadIdx.x;
+    const int i = ((int)blockIdx.x - B.tile_start[j]) * kSites + threadIdx.x;
     if (i >= Vh) return;
     const T *p = (const T *)J.ps + (size_t)st->base * 3 * Vh;
     T *t = (T *)J.t;
@@ -171,7 +203,8 @@ __global__ void __launch_bounds__(kTile, 2) k_it_deo1(const __grid_constant__ It
         bool bad = false;
         deo_site_df<SF_DF>(J.g, (const float4 *)J.links, p, S, i, 1, Vh, res, bad);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) t[(size_t)c * Vh + i] = make_float4(res[2 * c].x, res[2 * c].y, res[2 * c + 1].x, res[2 * c + 1].y);
+        for (int c = 0; c < 3; ++c)
+            t[(size_t)c * Vh + i] = make_float4(res[2 * c].x, res[2 * c].y, res[2 * c + 1].x, res[2 * c + 1].y);
     } else {
         float2 o[3];
         deo_site_f32<LF>(J.g, J.links, p, S, i, 1, Vh, o);
@@ -182,17 +215,17 @@ __global__ void __launch_bounds__(kTile, 2) k_it_deo1(const __grid_constant__ It
 
 // ------------------------------------------------------------------ K2
 template <int NJ, int VP, int LF>
-__global__ void __launch_bounds__(kTile, 2) k_it_deo2(const __grid_constant__ IterBatch<NJ> B)
+__global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo2(const __grid_constant__ IterBatch<NJ> B)
 {
     using T = typename VecT<VP>::T;
-    __shared__ double s_red[kTile / 32];
+    __shared__ double s_red[kIterThreads / 32];
     const int j = find_job(B);
     const IterJob &J = B.job[j];
     SolverState *st = J.st;
     if (st->halt) return;
     const int Vh = J.g.Vh;
     const int tile = (int)blockIdx.x - B.tile_start[j];
-    const int i = tile * kTile + threadIdx.x;
+    const int i = tile * kSites + threadIdx.x;
     Acc2 dot;
     acc_zero(dot);
     if (i < Vh) {
@@ -229,23 +262,23 @@ __global__ void __launch_bounds__(kTile, 2) k_it_deo2(const __grid_constant__ It
             dot.s = d;
         }
     }
-    const double v = block_reduce_acc<kTile>(dot, s_red);
+    const double v = block_reduce_acc_n<kIterThreads>(dot, s_red);
     tile_finish(J, tile, v, [&](double tot) { finalize_pq(st, tot); });
 }
 
 // ------------------------------------------------------------------ K3
 template <int NJ, int VP>
-__global__ void __launch_bounds__(kTile) k_it_upd_r(const __grid_constant__ IterBatch<NJ> B)
+__global__ void __launch_bounds__(kIterThreads) k_it_upd_r(const __grid_constant__ IterBatch<NJ> B)
 {
     using T = typename VecT<VP>::T;
-    __shared__ double s_red[kTile / 32];
+    __shared__ double s_red[kIterThreads / 32];
     const int j = find_job(B);
     const IterJob &J = B.job[j];
     SolverState *st = J.st;
     if (st->halt) return;
     const int Vh = J.g.Vh;
     const int tile = (int)blockIdx.x - B.tile_start[j];
-    const int i = tile * kTile + threadIdx.x;
+    const int i = tile * kSites + threadIdx.x;
     Acc2 nrm;
     acc_zero(nrm);
     if (i < Vh) {
@@ -256,11 +289,11 @@ __global__ void __launch_bounds__(kTile) k_it_upd_r(const __grid_constant__ Iter
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float4 rv = r[(size_t)c * Vh + i], qv = q[(size_t)c * Vh + i];
-                const float2 a = df_fma(na, make_float2(qv.x, qv.y), make_float2(rv.x, rv.y));
-                const float2 b = df_fma(na, make_float2(qv.z, qv.w), make_float2(rv.z, rv.w));
-                r[(size_t)c * Vh + i] = make_float4(a.x, a.y, b.x, b.y);
-                acc_prod(nrm, a.x, a.y, a.x, a.y);
-                acc_prod(nrm, b.x, b.y, b.x, b.y);
+                const float2 x = df_fma(na, make_float2(qv.x, qv.y), make_float2(rv.x, rv.y));
+                const float2 y = df_fma(na, make_float2(qv.z, qv.w), make_float2(rv.z, rv.w));
+                r[(size_t)c * Vh + i] = make_float4(x.x, x.y, y.x, y.y);
+                acc_prod(nrm, x.x, x.y, x.x, x.y);
+                acc_prod(nrm, y.x, y.y, y.x, y.y);
             }
         } else {
             const float na = -st->alpha_df.x;
@@ -268,59 +301,59 @@ __global__ void __launch_bounds__(kTile) k_it_upd_r(const __grid_constant__ Iter
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 const float2 rv = r[(size_t)c * Vh + i], qv = q[(size_t)c * Vh + i];
-                const float2 o = make_float2(__fmaf_rn(na, qv.x, rv.x), __fmaf_rn(na, qv.y, rv.y));
-                r[(size_t)c * Vh + i] = o;
-                d = __fmaf_rn(o.x, o.x, __fmaf_rn(o.y, o.y, d));
+                const float2 w = make_float2(__fmaf_rn(na, qv.x, rv.x), __fmaf_rn(na, qv.y, rv.y));
+                r[(size_t)c * Vh + i] = w;
+                d = __fmaf_rn(w.x, w.x, __fmaf_rn(w.y, w.y, d));
             }
             nrm.s = d;
         }
     }
-    const double v = block_reduce_acc<kTile>(nrm, s_red);
+    const double v = block_reduce_acc_n<kIterThreads>(nrm, s_red);
     tile_finish(J, tile, v, [&](double tot) { finalize_rr(st, tot); });
 }
 
 // ------------------------------------------------------------------ K4
+// 2-D grid: blockIdx.x = tile, blockIdx.y = slot k of the active shift list;
+// one thread per (site, shift), so the streams of all active shifts are in
+// flight together.  Slots beyond the active count exit at once.
 template <int NJ, int VP>
-__global__ void __launch_bounds__(kTile) k_it_upd_shifts(const __grid_constant__ IterBatch<NJ> B)
+__global__ void __launch_bounds__(kIterThreads) k_it_upd_shifts(const __grid_constant__ IterBatch<NJ> B)
 {
     using T = typename VecT<VP>::T;
     const int j = find_job(B);
     const IterJob &J = B.job[j];
     const SolverState *st = J.st;
     if (!st->do_k4) return;
+    const int k = blockIdx.y;
+    if (k >= st->n_act) return;
     const int Vh = J.g.Vh;
-    const int i = ((int)blockIdx.x - B.tile_start[j]) * kTile + threadIdx.x;
+    const int i = ((int)blockIdx.x - B.tile_start[j]) * kSites + threadIdx.x;
     if (i >= Vh) return;
-    const T *r = (const T *)J.r;
+    const int s = st->act_list[k];
+    const size_t off = (size_t)s * 3 * Vh + i;
     T *x = (T *)J.x, *ps = (T *)J.ps;
-    T rv[3];
+    const T *r = (const T *)J.r;
+    if constexpr (VP == VP_DF) {
+        const float2 as = st->alpha_s_df[s], zn = st->zeta_new_df[s], bs = st->beta_s_df[s];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) rv[c] = r[(size_t)c * Vh + i];
-    const int n_act = st->n_act;
-#pragma unroll 1
-    for (int k = 0; k < n_act; ++k) {
-        const int s = st->act_list[k];
-        const size_t off = (size_t)s * 3 * Vh + i;
-        if constexpr (VP == VP_DF) {
-            const float2 as = st->alpha_s_df[s], zn = st->zeta_new_df[s], bs = st->beta_s_df[s];
+        for (int c = 0; c < 3; ++c) {
+            const float4 rv = r[(size_t)c * Vh + i];
+            const float4 pv = ps[off + (size_t)c * Vh], xv = x[off + (size_t)c * Vh];
+            const float2 xr = df_fma(as, make_float2(pv.x, pv.y), make_float2(xv.x, xv.y));
+            const float2 xi = df_fma(as, make_float2(pv.z, pv.w), make_float2(xv.z, xv.w));
+            const float2 pr = df_mul2(zn, make_float2(rv.x, rv.y), bs, make_float2(pv.x, pv.y));
+            const float2 pi = df_mul2(zn, make_float2(rv.z, rv.w), bs, make_float2(pv.z, pv.w));
+            x[off + (size_t)c * Vh] = make_float4(xr.x, xr.y, xi.x, xi.y);
+            ps[off + (size_t)c * Vh] = make_float4(pr.x, pr.y, pi.x, pi.y);
+        }
+    } else {
+        const float as = st->alpha_s_df[s].x, zn = st->zeta_new_df[s].x, bs = st->beta_s_df[s].x;
 #pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float4 pv = ps[off + (size_t)c * Vh], xv = x[off + (size_t)c * Vh];
-                const float2 xr = df_fma(as, make_float2(pv.x, pv.y), make_float2(xv.x, xv.y));
-                const float2 xi = df_fma(as, make_float2(pv.z, pv.w), make_float2(xv.z, xv.w));
-                const float2 pr = df_mul2(zn, make_float2(rv[c].x, rv[c].y), bs, make_float2(pv.x, pv.y));
-                const float2 pi = df_mul2(zn, make_float2(rv[c].z, rv[c].w), bs, make_float2(pv.z, pv.w));
-                x[off + (size_t)c * Vh] = make_float4(xr.x, xr.y, xi.x, xi.y);
-                ps[off + (size_t)c * Vh] = make_float4(pr.x, pr.y, pi.x, pi.y);
-            }
-        } else {
-            const float as = st->alpha_s_df[s].x, zn = st->zeta_new_df[s].x, bs = st->beta_s_df[s].x;
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float2 pv = ps[off + (size_t)c * Vh], xv = x[off + (size_t)c * Vh];
-                x[off + (size_t)c * Vh] = make_float2(__fmaf_rn(as, pv.x, xv.x), __fmaf_rn(as, pv.y, xv.y));
-                ps[off + (size_t)c * Vh] = make_float2(__fmaf_rn(zn, rv[c].x, bs * pv.x), __fmaf_rn(zn, rv[c].y, bs * pv.y));
-            }
+        for (int c = 0; c < 3; ++c) {
+            const float2 rv = r[(size_t)c * Vh + i];
+            const float2 pv = ps[off + (size_t)c * Vh], xv = x[off + (size_t)c * Vh];
+            x[off + (size_t)c * Vh] = make_float2(__fmaf_rn(as, pv.x, xv.x), __fmaf_rn(as, pv.y, xv.y));
+            ps[off + (size_t)c * Vh] = make_float2(__fmaf_rn(zn, rv.x, bs * pv.x), __fmaf_rn(zn, rv.y, bs * pv.y));
         }
     }
 }

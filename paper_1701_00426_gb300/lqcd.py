@@ -124,7 +124,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_mscg_solve_packed": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.POINTER(dp), ip,
                                                   dp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                                   ctypes.POINTER(lqcd_solve_info)]),
-        "lqcd_profile_iteration": (ctypes.c_int, [vp, ctypes.c_double, dp, ctypes.c_int, vp, ctypes.c_int, dp, dp]),
+        "lqcd_profile_iteration": (ctypes.c_int, [vp, ctypes.c_double, dp, ctypes.c_int, ctypes.c_double, vp,
+                                                  ctypes.c_int, dp, dp]),
         "lqcd_serve_create": (ctypes.c_int, [sz, ctypes.c_int, ctypes.c_int, ctypes.POINTER(vp)]),
         "lqcd_serve_register_field": (ctypes.c_int, [vp, ip, vp, sz, ip]),
         "lqcd_serve_submit": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, dp, ctypes.c_int,
@@ -295,13 +296,13 @@ class Context:
             check(st)
         return info.as_dict()
 
-    def profile_iteration(self, mass: float, shifts, b, iters: int = 20):
+    def profile_iteration(self, mass: float, shifts, b, tol: float = 1e-10, iters: int = 20):
         """Per-kernel average ms of one solver iteration (see lqcd_profile_iteration)."""
         sh = np.ascontiguousarray(shifts, dtype=np.float64)
         ms = (ctypes.c_double * 4)()
         nact = ctypes.c_double()
         check(self.lib.lqcd_profile_iteration(self.h, float(mass), sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                              sh.size, _dptr(b), int(iters), ms, ctypes.byref(nact)))
+                                              sh.size, float(tol), _dptr(b), int(iters), ms, ctypes.byref(nact)))
         return list(ms), nact.value
 
     def cg_solve_mrhs(self, mass: float, sigma: float, tol: float, b: np.ndarray):
