@@ -195,6 +195,71 @@ __global__ void __launch_bounds__(kTile, 2)
     for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
 }
 
+// Same operator with SPLIT threads per site (adjacent lanes): thread `part`
+// takes directions mu in [part*4/SPLIT, (part+1)*4/SPLIT), the partial
+// double-float sums are merged across the lanes by a fixed xor butterfly
+// (two_sum is exact and symmetric, so every lane ends with the same value)
+// and the first lane writes.  Shortens the per-thread chain of dependent
+// loads on small lattices, where one wave of threads cannot fill the GPU.
+template <int SPLIT>
+__global__ void __launch_bounds__(kTile)
+    k_deo_df_ieee_split(Geom g, const float4 *__restrict__ L, const double2 *__restrict__ in,
+                        double2 *__restrict__ out, int P)
+{
+    const long tid = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    const int i = (int)(tid / SPLIT);
+    const int part = (int)(tid - (long)i * SPLIT);
+    if (i >= g.Vh) return;  // all SPLIT lanes of a site leave together
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned gmask = ((1u << SPLIT) - 1u) << (lane & ~(unsigned)(SPLIT - 1));
+    Stencil S;
+    make_stencil(g, i, P, S);
+    Acc2 acc[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc_zero(acc[k]);
+    bool bad = false;
+    const int Vh = g.Vh;
+#pragma unroll 1
+    for (int mu = part * (4 / SPLIT); mu < (part + 1) * (4 / SPLIT); ++mu) {
+        int f, b;
+        uint32_t nf, nb;
+        hop(g, S, mu, f, b, nf, nb);
+        float4 U[9], v[3];
+        float ch[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        load_link_df(L, mu, P, i, Vh, U);
+        load_spinor_df<SF_IEEE>(in, f, Vh, nf, v, bad);
+        hop_fwd_df(acc, ch, U, v);
+        load_link_df(L, mu, 1 - P, b, Vh, U);
+        load_spinor_df<SF_IEEE>(in, b, Vh, nb, v, bad);
+        hop_bwd_df(acc, ch, U, v);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) acc_flush(acc[k], ch[k]);
+    }
+#pragma unroll
+    for (int o = 1; o < SPLIT; o <<= 1)
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            const float s2 = __shfl_xor_sync(gmask, acc[k].s, o);
+            const float c2 = __shfl_xor_sync(gmask, acc[k].c, o);
+            acc_merge(acc[k], s2, c2);
+        }
+    bad = __any_sync(gmask, bad);
+    if (part != 0) return;
+    double2 o[3];
+    if (bad) {
+        deo_site_native_from_df(g, L, in, S, i, P, Vh, o);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 re = acc_result(acc[2 * c]), im = acc_result(acc[2 * c + 1]);
+            o[c] = make_double2(df_to_f64(make_float2(0.5f * re.x, 0.5f * re.y)),
+                                df_to_f64(make_float2(0.5f * im.x, 0.5f * im.y)));
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[(size_t)c * Vh + i] = o[c];
+}
+
 __global__ void __launch_bounds__(kTile, 2)
     k_deo_nat(Geom g, const double2 *__restrict__ L, const double2 *__restrict__ in, double2 *__restrict__ out, int P)
 {
@@ -236,7 +301,7 @@ static bool g_tune_loaded = false;
 static std::string tune_key(const lqcd_ctx *c, int variant)
 {
     char buf[128];
-    snprintf(buf, sizeof buf, "deo v%d %dx%dx%dx%d", variant, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
+    snprintf(buf, sizeof buf, "deo2 v%d %dx%dx%dx%d", variant, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
     return buf;
 }
 
@@ -271,8 +336,11 @@ static void tune_save(const std::string &key, int bs)
     fclose(fp);
 }
 
+// Candidates are encoded as kind * 1024 + threads per block; kind selects a
+// kernel variant (0: one thread per site, 1/2: 2/4 threads per site).
 template <class Launch>
-static int tuned_launch(lqcd_ctx *c, int variant, cudaStream_t s, Launch launch)
+static int tuned_launch(lqcd_ctx *c, int variant, cudaStream_t s, Launch launch, int ncand = 3,
+                        const int *cands = nullptr)
 {
     const std::string key = tune_key(c, variant);
     int bs = 0;
@@ -286,12 +354,13 @@ static int tuned_launch(lqcd_ctx *c, int variant, cudaStream_t s, Launch launch)
     cudaStreamIsCapturing(s, &cap);
     if (bs == 0 && cap != cudaStreamCaptureStatusNone) bs = kTile;
     if (bs == 0) {
-        const int cand[3] = {64, 128, 256};
+        const int def[3] = {64, 128, 256};
+        const int *cand = cands ? cands : def;
         float best = 1e30f;
         cudaEvent_t e0, e1;
         LQCD_CUDA(cudaEventCreate(&e0));
         LQCD_CUDA(cudaEventCreate(&e1));
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < ncand; ++k) {
             launch(cand[k]);  // warm
             float t = 0.f;
             cudaEventRecord(e0, s);
@@ -334,12 +403,23 @@ int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *ou
     auto nb = [&](int bs) { return (unsigned)((c->Vh + bs - 1) / bs); };
     int st = LQCD_OK;
     switch (prec) {
-    case LQCD_PREC_FP64:
+    case LQCD_PREC_FP64: {
         if (recon != 18) return fail(LQCD_EINVAL, "FP64 D_eo uses 18-real links");
-        st = tuned_launch(c, 0, s, [&](int bs) {
-            k_deo_df_ieee<<<nb(bs), bs, 0, s>>>(g, c->lnk_df.as<float4>(), (const double2 *)in, (double2 *)out, P);
-        });
+        static const int cand[7] = {64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256};
+        const float4 *L = c->lnk_df.as<float4>();
+        st = tuned_launch(c, 0, s, [&](int code) {
+            const int kind = code >> 10, bs = code & 1023;
+            if (kind == 0)
+                k_deo_df_ieee<<<nb(bs), bs, 0, s>>>(g, L, (const double2 *)in, (double2 *)out, P);
+            else if (kind == 1)
+                k_deo_df_ieee_split<2><<<(unsigned)((2 * c->Vh + bs - 1) / bs), bs, 0, s>>>(
+                    g, L, (const double2 *)in, (double2 *)out, P);
+            else
+                k_deo_df_ieee_split<4><<<(unsigned)((4 * c->Vh + bs - 1) / bs), bs, 0, s>>>(
+                    g, L, (const double2 *)in, (double2 *)out, P);
+        }, 7, cand);
         break;
+    }
     case LQCD_PREC_FP64_NATIVE:
         if (recon != 18) return fail(LQCD_EINVAL, "native FP64 D_eo uses 18-real links");
         st = tuned_launch(c, 1, s, [&](int bs) {

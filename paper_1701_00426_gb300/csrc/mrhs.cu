@@ -97,10 +97,16 @@ __global__ void __launch_bounds__(kTile) k_deo_mrhs(const MrhsArgs A)
     const int grp = (int)(tid - (long)site * A.G);
     if (site >= A.g.Vh) return;
     if (A.st && blockIdx.x == 0 && threadIdx.x < A.n) A.st[threadIdx.x].do_k4 = 0;
+    const int j0 = grp * R;
+    if (A.st) {  // solver use: fields that have stopped are not recomputed
+        bool all = true;
+#pragma unroll
+        for (int r = 0; r < R; ++r) all &= A.st[j0 + r].halt != HALT_NONE;
+        if (all) return;
+    }
     Stencil S;
     make_stencil(A.g, site, A.P, S);
     float2 acc[R][3];
-    const int j0 = grp * R;
     mrhs_site<LF, R>(A, S, site, j0, acc);
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -158,7 +164,10 @@ __global__ void __launch_bounds__(kTile) k_mrhs_deo2(const MrhsArgs A)
     double dots[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) dots[r] = 0.0;
-    if (site < A.g.Vh) {
+    bool live = false;
+#pragma unroll
+    for (int r = 0; r < R; ++r) live |= A.st[j0 + r].halt == HALT_NONE;
+    if (site < A.g.Vh && live) {
         Stencil S;
         make_stencil(A.g, site, 0, S);
         float2 acc[R][3];

@@ -668,7 +668,7 @@ int job_setup(JobRun &J, cudaStream_t s)
     init_state(S, J.mass, J.shifts, J.n_shift, tol_iter, J.b2 * J.scale * J.scale, c->opts.max_iter);
     if (J.vp == VP_F32) {
         if (!f16) S.rel_stop2 = c->opts.delta_reliable * c->opts.delta_reliable * S.rho;
-        LQCD_CUDA(cudaMemsetAsync(J.x, 0, (size_t)J.n_shift * n3 * sizeof(double2), s));
+        if (J.x) LQCD_CUDA(cudaMemsetAsync(J.x, 0, (size_t)J.n_shift * n3 * sizeof(double2), s));
     }
     LQCD_CUDA(cudaMemcpyAsync(J.P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
     if (J.vp == VP_DF)

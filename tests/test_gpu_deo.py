@@ -173,3 +173,45 @@ def test_deo_fp64_full_size_matches_oracle(gpu, orc, dims):
         torch.cuda.synchronize()
         got = gpu.from_device_spinor(out)
     check_fp64(got, orc.deo(dims, 0, U, x))
+
+
+FORCE_SCRIPT = r'''
+import sys, json, numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_1701_00426_gb300 import inputs, lqcd
+from oracle import oracle
+orc = oracle()
+out = {}
+for dims in [(4, 6, 8, 10), (8, 8, 8, 8), (2, 2, 2, 2)]:
+    U = inputs.random_links(dims)
+    with lqcd.Context(dims) as c:
+        c.links_upload(U)
+        for parity in (0, 1):
+            x = inputs.gaussian_field(dims, k=3 + parity)
+            ref = orc.deo(dims, parity, U, x)
+            got = c.deo_apply(parity, x)
+            d = np.abs(got - ref)
+            out[f"{dims}{parity}"] = [float(np.linalg.norm(d) / np.linalg.norm(ref)), float(d.max() / np.abs(ref).max())]
+print(json.dumps(out))
+'''
+
+
+@pytest.mark.parametrize("code", [64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256])
+def test_every_tuned_fp64_variant_matches_oracle(gpu, tmp_path, code):
+    """Each candidate of the autotuner, forced through a tuning-cache file."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    lines = [f"deo2 v0 {d[0]}x{d[1]}x{d[2]}x{d[3]} {code}" for d in [(4, 6, 8, 10), (8, 8, 8, 8), (2, 2, 2, 2)]]
+    cache.write_text("\n".join(lines) + "\n")
+    script = tmp_path / "force.py"
+    script.write_text(FORCE_SCRIPT)
+    env = dict(os.environ, LQCD_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, str(script), root], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    for k, (n, m) in res.items():
+        assert n <= FP64_TOL and m <= FP64_TOL, f"variant {code} case {k}: {n:.2e} {m:.2e}"
