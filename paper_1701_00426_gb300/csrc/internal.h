@@ -80,6 +80,7 @@ template <int NJ>
 struct IterBatch {
     int njobs;
     int max_shift;              // largest n_shift of the jobs (grid height of the shift update)
+    int interleave;             // 1: jobs on one lattice, block b belongs to job b % njobs
     int tile_start[NJ + 1];
     IterJob job[NJ];
 };
@@ -172,6 +173,7 @@ struct JobRun {
     double2 *x = nullptr;         // IEEE device solutions [n][3][Vh]
     double b2 = 0, scale = 1, bytes = 0;
     bool zero = false;
+    bool warm = false;            // x holds an initial guess (single shift, FP32 engine)
     uint64_t launches0 = 0;
     lqcd_solve_info I;
 };

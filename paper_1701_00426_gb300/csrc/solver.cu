@@ -650,11 +650,29 @@ int job_setup(JobRun &J, cudaStream_t s)
         LQCD_CUDA(cudaMemsetAsync(J.x, 0, (size_t)J.n_shift * n3 * sizeof(double2), s));
         return LQCD_OK;
     }
-    J.scale = unit_scale(J.b2, 6.0 * c->Vh);
+    double rho0 = J.b2;
+    const double2 *src = J.b;
+    if (J.warm) {
+        // start from the guess in x: iterate on its FP64 true residual
+        const double a0 = J.mass * J.mass + J.shifts[0];
+        if ((st = true_residual(c, J.P, J.vp, a0, J.x, J.b, J.P.r_hi, nullptr, 1.0, s, rho0))) return st;
+        if (rho0 <= 0.25 * J.tol * J.tol * J.b2) {
+            memset(&S, 0, sizeof S);
+            S.halt = HALT_CONVERGED;
+            S.n_shift = 1;
+            LQCD_CUDA(cudaMemcpyAsync(J.P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
+            J.scale = 1.0;
+            if (J.vp == VP_F32)
+                k_zero_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(J.P.x, n3);
+            return LQCD_OK;
+        }
+        src = J.P.r_hi;
+    }
+    J.scale = unit_scale(rho0, 6.0 * c->Vh);
     if (J.vp == VP_DF)
-        k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(J.b, J.P.r, n3, J.scale);
+        k_ieee_to_vec<VP_DF><<<nblk(n3), 256, 0, s>>>(src, J.P.r, n3, J.scale);
     else
-        k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(J.b, J.P.r, n3, J.scale);
+        k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(src, J.P.r, n3, J.scale);
     LQCD_CUDA(cudaGetLastError());
     // FP64: iterate to half the tolerance; mixed: FP32 reaches ~1e-6 at best
     // both engines iterate to tol/2; the FP32 engine refreshes its residual
@@ -666,9 +684,10 @@ int job_setup(JobRun &J, cudaStream_t s)
     const bool f16 = J.lf == LF_F16_12;
     const double tol_iter = f16 ? std::max(0.5 * J.tol, 3e-4) : 0.5 * J.tol;
     init_state(S, J.mass, J.shifts, J.n_shift, tol_iter, J.b2 * J.scale * J.scale, c->opts.max_iter);
+    S.rho = rho0 * J.scale * J.scale;  // the iterated residual starts at b (or at the guess's residual)
     if (J.vp == VP_F32) {
         if (!f16) S.rel_stop2 = c->opts.delta_reliable * c->opts.delta_reliable * S.rho;
-        if (J.x) LQCD_CUDA(cudaMemsetAsync(J.x, 0, (size_t)J.n_shift * n3 * sizeof(double2), s));
+        if (J.x && !J.warm) LQCD_CUDA(cudaMemsetAsync(J.x, 0, (size_t)J.n_shift * n3 * sizeof(double2), s));
     }
     LQCD_CUDA(cudaMemcpyAsync(J.P.st, &S, sizeof S, cudaMemcpyHostToDevice, s));
     if (J.vp == VP_DF)
@@ -729,6 +748,104 @@ int job_reliable_update(JobRun &J, cudaStream_t s)
     return LQCD_OK;
 }
 
+// Finish every shift of a mixed-precision multi-shift job: warm-started
+// single-shift FP32 CG with FP64 reliable updates, one job per shift, all in
+// one interleaved packed launch.  Fills J.I.true_resid; returns the largest
+// iteration count and the number of reliable updates.
+static int refine_shifts_packed(JobRun &J, int lf, cudaStream_t s, int &iters, int &reliable)
+{
+    lqcd_ctx *c = J.c;
+    const long n3 = 3 * (long)c->Vh;
+    const void *links = lf == LF_F32_12 ? c->lnk_f12.ptr : c->lnk_f18.ptr;
+    std::vector<JobRun> R(J.n_shift);
+    std::vector<Workspace> W(J.n_shift);
+    std::vector<int> idx;
+    int st;
+    for (int i = 0; i < J.n_shift; ++i) {
+        JobRun &K = R[i];
+        K.c = c;
+        K.vp = VP_F32;
+        K.lf = lf;
+        K.links = links;
+        K.mass = J.mass;
+        K.n_shift = 1;
+        K.shifts[0] = J.shifts[i];
+        K.tol = J.tol;
+        K.b = J.b;
+        K.x = J.x + (size_t)i * n3;
+        K.warm = true;
+        if ((st = ensure_workspace_in(c, W[i], VP_F32, 1, K.P))) return st;
+        if ((st = job_setup(K, s))) return st;
+        SolverState O;
+        LQCD_CUDA(cudaMemcpyAsync(&O, K.P.st, sizeof O, cudaMemcpyDeviceToHost, s));
+        LQCD_CUDA(cudaStreamSynchronize(s));
+        if (O.halt == HALT_NONE) idx.push_back(i);
+    }
+    iters = 0;
+    reliable = 0;
+    if (!idx.empty()) {
+        IterBatch<kMaxJobs> B;
+        memset(&B, 0, sizeof B);
+        B.njobs = (int)idx.size();
+        B.max_shift = 1;
+        B.interleave = 1;
+        for (int k = 0; k < B.njobs; ++k) job_fill(R[idx[k]], B.job[k]);
+        const int ntot = R[idx[0]].P.ntiles * B.njobs;
+        const int chunk = c->opts.check_every;
+        cudaGraphExec_t exec = nullptr;
+        {
+            cudaGraph_t g;
+            LQCD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            for (int k = 0; k < chunk; ++k) launch_iteration<kMaxJobs>(B, ntot, VP_F32, lf, s);
+            cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (e != cudaSuccess) return cuda_fail(e, "refinement graph capture");
+            e = cudaGraphInstantiate(&exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(e, "refinement graph instantiate");
+        }
+        int *hs = c->h_pinned;
+        const int max_chunks = 4 * (c->opts.max_iter / chunk + 4);
+        int rc = LQCD_OK;
+        for (int k = 0; k < max_chunks && rc == LQCD_OK; ++k) {
+            cudaError_t e = cudaGraphLaunch(exec, s);
+            c->launches += 4 * (uint64_t)chunk;
+            for (int q = 0; q < B.njobs && e == cudaSuccess; ++q)
+                e = cudaMemcpyAsync(hs + q, &B.job[q].st->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { rc = cuda_fail(e, "refinement chunk"); break; }
+            bool all = true;
+            for (int q = 0; q < B.njobs && rc == LQCD_OK; ++q) {
+                if (hs[q] == HALT_RELIABLE) rc = job_reliable_update(R[idx[q]], s), all = false;
+                else if (hs[q] == HALT_NAN) rc = fail(LQCD_ENAN, "NaN/Inf or breakdown in refinement");
+                else if (hs[q] == HALT_NONE) all = false;
+            }
+            if (all) break;
+        }
+        cudaGraphExecDestroy(exec);
+        if (rc) return rc;
+    }
+    for (int i = 0; i < J.n_shift; ++i) {
+        JobRun &K = R[i];
+        k_vec_to_ieee<VP_F32><<<nblk(n3), 256, 0, s>>>(K.P.x, K.x, n3, 1.0 / K.scale, 1);
+        LQCD_CUDA(cudaGetLastError());
+        SolverState O;
+        LQCD_CUDA(cudaMemcpyAsync(&O, K.P.st, sizeof O, cudaMemcpyDeviceToHost, s));
+        double rr;
+        if ((st = true_residual(c, K.P, VP_F32, J.mass * J.mass + J.shifts[i], K.x, J.b, nullptr, nullptr, 1.0, s,
+                                rr)))
+            return st;
+        J.I.true_resid[i] = std::sqrt(rr / J.b2);
+        iters = std::max(iters, O.iters);
+        reliable += K.I.reliable_updates;
+        const double spin = 24.0;
+        J.bytes += (double)c->Vh * O.iters * (iter_bytes_base(VP_F32, lf) + 4 * spin);
+    }
+    for (auto &w : W) {
+        w.vec.release(); w.ieee.release(); w.part.release(); w.tickets.release(); w.state.release();
+    }
+    return LQCD_OK;
+}
+
 // After the iterations: IEEE solutions, FP64 true residuals, refinement.
 int job_finish(JobRun &J, cudaStream_t s)
 {
@@ -777,28 +894,20 @@ int job_finish(JobRun &J, cudaStream_t s)
             if (!(res <= J.tol)) status = LQCD_ENOCONV;
         }
     } else {
-        // mixed: every shift finished together by the batched CG (FP32
-        // iterations, links read once per application for all shifts, FP64
-        // reliable updates); the FP16 variant uses FP32 links here because
-        // FP16 rounding times the condition number of the smallest shifts
-        // exceeds one and would stall the reliable updates
+        // mixed: every shift above tol is finished by its own single-shift
+        // CG (FP32 iterations, FP64 reliable updates) started from its
+        // multi-shift solution; all of them run as one packed launch whose
+        // blocks interleave the shifts, so the blocks of different shifts
+        // that read the same links run together and share them in L2.  The
+        // FP16 variant uses FP32 links here (FP16 rounding times the
+        // condition number of the smallest shifts exceeds one).
         const int lf2 = c->opts.recon == 12 || J.lf == LF_F16_12 ? LF_F32_12 : LF_F32_18;
-        for (int g0 = 0; g0 < J.n_shift; g0 += 16) {
-            const int ng = std::min(16, J.n_shift - g0);
-            lqcd_solve_info K[16];
-            memset(K, 0, sizeof K);
-            const int rc = mrhs_cg_core(c, J.mass, J.shifts + g0, ng, J.tol, J.b, 0, J.x + (size_t)g0 * n3, lf2, K,
-                                        J.bytes);
-            if (rc != LQCD_OK && rc != LQCD_ENOCONV) return rc;
-            int mx = 0;
-            for (int k = 0; k < ng; ++k) {
-                J.I.true_resid[g0 + k] = K[k].true_resid[0];
-                J.I.reliable_updates += K[k].reliable_updates;
-                mx = std::max(mx, K[k].iters);
-                if (!(K[k].true_resid[0] <= J.tol)) status = LQCD_ENOCONV;
-            }
-            J.I.refine_iters += mx;
-        }
+        int it = 0, rel = 0;
+        if ((st = refine_shifts_packed(J, lf2, s, it, rel))) return st;
+        J.I.refine_iters += it;
+        J.I.reliable_updates += rel;
+        for (int i = 0; i < J.n_shift; ++i)
+            if (!(J.I.true_resid[i] <= J.tol)) status = LQCD_ENOCONV;
     }
     LQCD_CUDA(cudaStreamSynchronize(s));
     J.I.bytes_moved = J.bytes;

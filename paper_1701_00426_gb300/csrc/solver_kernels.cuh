@@ -21,15 +21,27 @@
 
 namespace lqcd {
 
+// Block -> job.  Contiguous batches give each job a range of blocks;
+// interleaved batches (jobs on one lattice) give block b to job b % njobs,
+// so that the jobs' blocks reading the same links run next to each other
+// and share them through L2.
 template <int NJ>
 __device__ __forceinline__ int find_job(const IterBatch<NJ> &B)
 {
     int j = 0;
     if (NJ > 1) {
+        if (B.interleave) return (int)(blockIdx.x % (unsigned)B.njobs);
 #pragma unroll 1
         while (j + 1 < B.njobs && (int)blockIdx.x >= B.tile_start[j + 1]) ++j;
     }
     return j;
+}
+
+template <int NJ>
+__device__ __forceinline__ int job_tile(const IterBatch<NJ> &B, int j)
+{
+    if (NJ > 1 && B.interleave) return (int)(blockIdx.x / (unsigned)B.njobs);
+    return (int)blockIdx.x - B.tile_start[j];
 }
 
 // Sum per-tile partials in tile order and hand the total to fn (thread 0 of
@@ -153,15 +165,15 @@ template <> struct VecT<VP_F32> { using T = float2; };
 // ------------------------------------------------------------------ launch shape
 // One thread per even site; a tile is kSites consecutive half-lattice sites
 // and one block of kIterThreads = kSites threads.  Reductions produce one
-// partial per tile, which fixes their order for a given lattice.  (A thread
-// per (site, colour) was measured slower: the three colour threads re-load
-// the neighbour spinors, and 64-site tiles made the reductions' atomics and
-// tails expensive.)
+// partial per tile, which fixes their order for a given lattice.  Measured
+// on the 32^4 15-shift solve: 256-site tiles with 2 blocks per SM beat 128
+// (4 or 5 blocks) and 64-site tiles; a thread per (site, colour) was slower
+// still (the colour threads re-load the neighbour spinors).
 #ifndef LQCD_TILE_SITES
-#define LQCD_TILE_SITES 128
+#define LQCD_TILE_SITES 256
 #endif
 #ifndef LQCD_ITER_MINB
-#define LQCD_ITER_MINB 4
+#define LQCD_ITER_MINB 2
 #endif
 constexpr int kSites = LQCD_TILE_SITES;
 constexpr int kIterThreads = kSites;
@@ -189,10 +201,11 @@ __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo1(const 
     const int j = find_job(B);
     const IterJob &J = B.job[j];
     SolverState *st = J.st;
-    if ((int)blockIdx.x == B.tile_start[j] && threadIdx.x == 0) st->do_k4 = 0;
+    const int tile = job_tile(B, j);
+    if (tile == 0 && threadIdx.x == 0) st->do_k4 = 0;
     if (st->halt) return;
     const int Vh = J.g.Vh;
-    const int i = ((int)blockIdx.x - B.tile_start[j]) * kSites + threadIdx.x;
+    const int i = tile * kSites + threadIdx.x;
     if (i >= Vh) return;
     const T *p = (const T *)J.ps + (size_t)st->base * 3 * Vh;
     T *t = (T *)J.t;
@@ -224,7 +237,7 @@ __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo2(const 
     SolverState *st = J.st;
     if (st->halt) return;
     const int Vh = J.g.Vh;
-    const int tile = (int)blockIdx.x - B.tile_start[j];
+    const int tile = job_tile(B, j);
     const int i = tile * kSites + threadIdx.x;
     Acc2 dot;
     acc_zero(dot);
@@ -277,7 +290,7 @@ __global__ void __launch_bounds__(kIterThreads) k_it_upd_r(const __grid_constant
     SolverState *st = J.st;
     if (st->halt) return;
     const int Vh = J.g.Vh;
-    const int tile = (int)blockIdx.x - B.tile_start[j];
+    const int tile = job_tile(B, j);
     const int i = tile * kSites + threadIdx.x;
     Acc2 nrm;
     acc_zero(nrm);
@@ -327,7 +340,7 @@ __global__ void __launch_bounds__(kIterThreads) k_it_upd_shifts(const __grid_con
     const int k = blockIdx.y;
     if (k >= st->n_act) return;
     const int Vh = J.g.Vh;
-    const int i = ((int)blockIdx.x - B.tile_start[j]) * kSites + threadIdx.x;
+    const int i = job_tile(B, j) * kSites + threadIdx.x;
     if (i >= Vh) return;
     const int s = st->act_list[k];
     const size_t off = (size_t)s * 3 * Vh + i;
