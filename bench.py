@@ -477,6 +477,9 @@ def run_ours(args, rank, world, local):
             mixed[name] = {"solves_per_s": round(1.0 / dt, 4), "speedup_vs_fp64": round((1.0 / dt) / value, 3),
                            "max_true_resid": max(mi["true_resid"]), "iters": mi["iters"],
                            "refine_iters": mi["refine_iters"], "reliable_updates": mi["reliable_updates"]}
+            # the low-precision iteration's kernels, first iterations (before any reliable update)
+            mms, _ = ctx.profile_iteration(MASS, shifts, bd, tol=TOL, iters=30)
+            mixed[name]["kernels_ms"] = [round(m, 4) for m in mms]
         except Exception as exc:  # reported, never hidden
             mixed[name] = {"error": repr(exc)}
     ctx.set_opts(prec=0, recon=18)

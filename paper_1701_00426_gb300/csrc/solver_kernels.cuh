@@ -83,6 +83,41 @@ __device__ __forceinline__ void tile_finish(const IterJob &J, int tile, double v
     reduce_finish(J.part, J.ticket, J.ntiles, tile, v, fn);
 }
 
+// As reduce_finish, but every thread of the last block calls fn(total), so
+// that the finaliser can spread per-shift work over the block.
+template <class Fn>
+__device__ __forceinline__ void tile_finish_block(const IterJob &J, int tile, double v, Fn fn)
+{
+    __shared__ int s_last;
+    __shared__ double s_red[32];
+    __shared__ double s_tot;
+    if (threadIdx.x == 0) {
+        J.part[tile] = v;
+        __threadfence();
+        const unsigned prev = atomicAdd(J.ticket, 1u);
+        s_last = (prev == (unsigned)(J.ntiles - 1));
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double s = 0.0;
+    for (int k = threadIdx.x; k < J.ntiles; k += blockDim.x) s += __ldcg(J.part + k);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        const int nw = blockDim.x >> 5;
+        for (int k = 0; k < nw; ++k) tot += s_red[k];
+        s_tot = tot;
+        *J.ticket = 0u;
+    }
+    __syncthreads();
+    fn(s_tot);
+    __threadfence();
+}
+
 __device__ __forceinline__ float2 split_scalar(double d)
 {
     const float h = __double2float_rn(d);
@@ -119,6 +154,93 @@ __device__ inline void finalize_pq(SolverState *st, double pq)
         st->zeta_new[s] = zn;
         st->zeta_new_df[s] = split_scalar(zn);
         st->alpha_s_df[s] = split_scalar(alpha * zn / z);
+    }
+}
+
+// finalize_pq spread over a block: thread 0 rotates the recurrences and
+// computes alpha, then one thread per active shift computes zeta_i, alpha_i.
+// Called by every thread of the block.
+__device__ inline void finalize_pq_block(SolverState *st, double pq)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        st->last_sum = pq;
+        st->alpha_prev = st->alpha;
+        st->beta_prev = st->beta;
+        int n_act = 0;
+        for (int s = 0; s < st->n_shift; ++s) {
+            if (!st->active_next[s]) continue;
+            st->zeta_prev[s] = st->zeta[s];
+            st->zeta[s] = st->zeta_new[s];
+            st->act_list[n_act++] = s;
+        }
+        st->n_act = n_act;
+        const double alpha = st->rho / pq;
+        s_ok = (pq > 0.0) && isfinite(alpha);
+        if (s_ok) {
+            st->alpha = alpha;
+            st->alpha_df = split_scalar(alpha);
+        } else {
+            st->halt = HALT_NAN;
+            st->nan_flag = 1;
+        }
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const double alpha = st->alpha;
+    for (int k = threadIdx.x; k < st->n_act; k += blockDim.x) {
+        const int s = st->act_list[k];
+        const double z = st->zeta[s], zp = st->zeta_prev[s];
+        const double den = alpha * st->beta_prev * (zp - z) + zp * st->alpha_prev * (1.0 + st->shift_rel[s] * alpha);
+        const double zn = z * zp * st->alpha_prev / den;
+        st->zeta_new[s] = zn;
+        st->zeta_new_df[s] = split_scalar(zn);
+        st->alpha_s_df[s] = split_scalar(alpha * zn / z);
+    }
+}
+
+// finalize_rr spread over a block (one thread per active shift for beta_i
+// and the convergence tests).  Called by every thread of the block.
+__device__ inline void finalize_rr_block(SolverState *st, double rr)
+{
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        st->last_sum = rr;
+        s_ok = isfinite(rr);
+        if (s_ok) {
+            st->beta = rr / st->rho;
+            st->rho = rr;
+            st->iters += 1;
+        } else {
+            st->halt = HALT_NAN;
+            st->nan_flag = 1;
+        }
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    const double beta = st->beta;
+    int open = 0;
+    for (int k = threadIdx.x; k < st->n_act; k += blockDim.x) {
+        const int s = st->act_list[k];
+        const double ratio = st->zeta_new[s] / st->zeta[s];
+        st->beta_s_df[s] = split_scalar(beta * ratio * ratio);
+        const double zn = st->zeta_new[s];
+        const bool conv = zn * zn * rr <= st->tol2_b2;
+        if (conv && st->shift_iters[s] == 0) st->shift_iters[s] = st->iters;
+        st->active_next[s] = conv ? 0 : 1;
+        open |= !conv;
+    }
+    const int any = __syncthreads_or(open);
+    if (threadIdx.x == 0) {
+        // the base direction must keep moving while any shift still iterates
+        if (any) st->active_next[st->base] = 1;
+        st->do_k4 = 1;
+        if (!any)
+            st->halt = HALT_CONVERGED;
+        else if (st->rel_stop2 > 0.0 && rr < st->rel_stop2)
+            st->halt = HALT_RELIABLE;
+        else if (st->iters >= st->max_iter)
+            st->halt = HALT_MAXITER;
     }
 }
 
@@ -276,7 +398,7 @@ __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo2(const 
         }
     }
     const double v = block_reduce_acc_n<kIterThreads>(dot, s_red);
-    tile_finish(J, tile, v, [&](double tot) { finalize_pq(st, tot); });
+    tile_finish_block(J, tile, v, [&](double tot) { finalize_pq_block(st, tot); });
 }
 
 // ------------------------------------------------------------------ K3
@@ -322,7 +444,7 @@ __global__ void __launch_bounds__(kIterThreads) k_it_upd_r(const __grid_constant
         }
     }
     const double v = block_reduce_acc_n<kIterThreads>(nrm, s_red);
-    tile_finish(J, tile, v, [&](double tot) { finalize_rr(st, tot); });
+    tile_finish_block(J, tile, v, [&](double tot) { finalize_rr_block(st, tot); });
 }
 
 // ------------------------------------------------------------------ K4
