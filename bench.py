@@ -341,6 +341,48 @@ def serving_bench(lqcd, inputs, n_req=40):
 
 
 # ---------------------------------------------------------------- ours
+def rel_diff_per_shift(x, xref):
+    """max over shifts of ||x_i - xref_i|| / ||xref_i|| (device complex128 [n][3][Vh])."""
+    d = (x - xref).reshape(x.shape[0], -1).abs().pow(2).sum(1).sqrt()
+    n = xref.reshape(x.shape[0], -1).abs().pow(2).sum(1).sqrt()
+    return float((d / n).max())
+
+
+def mixed_48_bench(lqcd, inputs, torch):
+    """Mixed precision on 48^4 (same mass and shifts): FP32 12-real links with an FP64
+    phase to 3e-4 and FP64 reliable updates, against the FP64 solver on the same lattice."""
+    dims = (48, 48, 48, 48)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=0)
+    shifts = inputs.log_shifts(N_SHIFT)
+    ctx = lqcd.Context(dims)
+    ctx.links_upload(U)
+    del U
+    bd = lqcd.to_device_spinor(b)
+    xd = torch.empty((N_SHIFT, 3, ctx.Vh), dtype=torch.complex128, device="cuda")
+    out = {"lattice": list(dims)}
+    x64 = None
+    for name, kw in [("fp64", dict(prec=0, recon=18)), ("fp32_12r", dict(prec=1, recon=12, fp64_until=3e-4))]:
+        ctx.set_opts(**kw)
+        ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)  # warm-up (graph capture, workspaces)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        info = ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"solves_per_s": round(1.0 / dt, 4), "s": round(dt, 3), "iters": info["iters"],
+                     "refine_iters": info["refine_iters"], "reliable_updates": info["reliable_updates"],
+                     "max_true_resid": max(info["true_resid"])}
+        if x64 is None:
+            x64 = xd.clone()
+        else:
+            out[name]["max_rel_diff_vs_fp64_solution"] = rel_diff_per_shift(xd, x64)
+    out["speedup_fp32_vs_fp64"] = round(out["fp64"]["s"] / out["fp32_12r"]["s"], 3)
+    out["note"] = "second of two solves of each kind (the first captures graphs and allocates workspaces)"
+    ctx.close()
+    return out
+
+
 def deo_sweep(lqcd, inputs, torch, flush, hbm_peak, sizes):
     """ns/site and algorithmic GB/s of one D_eo, median of reps with L2 flushed."""
     out = {}
@@ -465,9 +507,11 @@ def run_ours(args, rank, world, local):
 
     # mixed precision on the same workload
     mixed = {}
-    for name, prec, recon in [("fp32_12r", 1, 12), ("fp16_12r", 2, 12)]:
+    x64 = xd.clone()
+    for name, prec, recon, fu in [("fp32_12r", 1, 12, 3e-4), ("fp32_18r", 1, 18, 3e-4),
+                                  ("fp32_12r_no_fp64_phase", 1, 12, 0.0), ("fp16_12r", 2, 12, 0.0)]:
         try:
-            ctx.set_opts(prec=prec, recon=recon)
+            ctx.set_opts(prec=prec, recon=recon, fp64_until=fu)
             ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -476,13 +520,15 @@ def run_ours(args, rank, world, local):
             dt = time.perf_counter() - t0
             mixed[name] = {"solves_per_s": round(1.0 / dt, 4), "speedup_vs_fp64": round((1.0 / dt) / value, 3),
                            "max_true_resid": max(mi["true_resid"]), "iters": mi["iters"],
-                           "refine_iters": mi["refine_iters"], "reliable_updates": mi["reliable_updates"]}
+                           "refine_iters": mi["refine_iters"], "reliable_updates": mi["reliable_updates"],
+                           "fp64_until": fu,
+                           "max_rel_diff_vs_fp64_solution": rel_diff_per_shift(xd, x64)}
             # the low-precision iteration's kernels, first iterations (before any reliable update)
             mms, _ = ctx.profile_iteration(MASS, shifts, bd, tol=TOL, iters=30)
             mixed[name]["kernels_ms"] = [round(m, 4) for m in mms]
         except Exception as exc:  # reported, never hidden
             mixed[name] = {"error": repr(exc)}
-    ctx.set_opts(prec=0, recon=18)
+    ctx.set_opts(prec=0, recon=18, fp64_until=3e-4)
     ctx.close()
     del bd, xd
     torch.cuda.empty_cache()
@@ -492,7 +538,8 @@ def run_ours(args, rank, world, local):
     del flush
     torch.cuda.empty_cache()
     extras = {}
-    for name, fn in [("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
+    for name, fn in [("mixed_48", lambda: mixed_48_bench(lqcd, inputs, torch)),
+                     ("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
                      ("packed", lambda: packed_bench(lqcd, inputs)),
                      ("serving", lambda: serving_bench(lqcd, inputs))]:
         if name in args.skip:
@@ -536,7 +583,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sweep", type=int, nargs="*", default=[16, 24, 32, 48])
     ap.add_argument("--lattice", type=int, default=32, help="side of the solve lattice (default 32)")
-    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: batched packed serving")
+    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: mixed_48 batched packed serving")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
     args = ap.parse_args()

@@ -82,6 +82,15 @@ typedef struct lqcd_opts {
                               residual at the last update (default 0.1) */
     int max_iter;          /* iteration cap per solve (default 20000) */
     int check_every;       /* iterations between host convergence checks (default 32) */
+    double fp64_until;     /* mixed precision with FP32 links: the multi-shift
+                              iteration runs in FP64 (double-float) until
+                              ||r|| <= fp64_until * ||b||, then in FP32 with
+                              reliable updates (0 = FP32 from the start; must
+                              be in [0, 1); default 3e-4).  Rounding of the FP32
+                              phase enters the shifted systems in proportion to
+                              the residual at the switch, so a later switch
+                              leaves less for the per-shift refinement.
+                              Ignored by FP64 and FP16 solves. */
 } lqcd_opts;
 
 #define LQCD_MAX_SHIFTS 32

@@ -56,6 +56,8 @@ size_t ctx_device_bytes(const lqcd_ctx *c)
                          &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
     size_t s = 0;
     for (const DevBuf *p : b) s += p->bytes;
+    s += c->ws32.bytes();
+    for (const Workspace &w : c->ref_ws) s += w.bytes();
     return s;
 }
 
@@ -66,6 +68,7 @@ static int check_opts(const lqcd_opts *o)
     if (!(o->delta_reliable > 0.0 && o->delta_reliable < 1.0)) return fail(LQCD_EINVAL, "opts.delta_reliable must be in (0,1)");
     if (o->max_iter < 1) return fail(LQCD_EINVAL, "opts.max_iter must be >= 1");
     if (o->check_every < 1 || o->check_every > 4096) return fail(LQCD_EINVAL, "opts.check_every must be in 1..4096");
+    if (!(o->fp64_until >= 0.0 && o->fp64_until < 1.0)) return fail(LQCD_EINVAL, "opts.fp64_until must be in [0,1)");
     return LQCD_OK;
 }
 
@@ -83,6 +86,7 @@ void lqcd_default_opts(lqcd_opts *o)
     o->delta_reliable = 0.1;
     o->max_iter = 20000;
     o->check_every = 32;
+    o->fp64_until = 3e-4;
 }
 
 const char *lqcd_last_error(void) { return g_err.c_str(); }
@@ -132,6 +136,8 @@ void lqcd_destroy(lqcd_ctx *c)
     DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->io_a, &c->io_b,
                    &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
     for (DevBuf *p : b) p->release();
+    c->ws32.release();
+    for (Workspace &w : c->ref_ws) w.release();
     if (c->h_pinned) cudaFreeHost(c->h_pinned);
     if (c->h_pinned_d) cudaFreeHost(c->h_pinned_d);
     if (c->stream) cudaStreamDestroy(c->stream);

@@ -96,6 +96,11 @@ struct Workspace {
     DevBuf state;           // SolverState
     DevBuf stage;           // host-format staging
     uint64_t gen = 0;       // bumped on every reallocation (graph cache key)
+    void release()
+    {
+        vec.release(); ieee.release(); part.release(); tickets.release(); state.release(); stage.release();
+    }
+    size_t bytes() const { return vec.bytes + ieee.bytes + part.bytes + tickets.bytes + state.bytes + stage.bytes; }
 };
 
 struct WsPtrs {
@@ -110,9 +115,16 @@ struct WsPtrs {
     int ntiles256;      // tiles (blocks) of the 256-thread helper kernels
 };
 
+// Instantiated iteration-chunk graphs of a context, keyed by a hash of the
+// launch parameters (pointers included); least recently used is replaced.
 struct GraphCache {
-    uint64_t key = ~0ull;
-    cudaGraphExec_t exec = nullptr;
+    static constexpr int kEntries = 4;
+    uint64_t key[kEntries] = {~0ull, ~0ull, ~0ull, ~0ull};
+    cudaGraphExec_t exec[kEntries] = {};
+    uint64_t used[kEntries] = {};
+    uint64_t tick = 0;
+    cudaGraphExec_t find(uint64_t k);
+    void put(uint64_t k, cudaGraphExec_t e);
     void reset();
 };
 
@@ -134,6 +146,8 @@ struct lqcd_ctx {
     lqcd::DevBuf lnk_h12;   // FP16, 12 reals:       [8][Vh] uint4 + [8][Vh] uint2
     lqcd::DevBuf io_a, io_b;  // device staging of host spinors for where = 0
     lqcd::Workspace ws;
+    lqcd::Workspace ws32;                  // FP32 phase of a hybrid mixed-precision solve
+    std::vector<lqcd::Workspace> ref_ws;   // per-shift refinement jobs
     lqcd::GraphCache graph;
     int *h_pinned = nullptr;  // pinned host words for halt/iteration polling
     double *h_pinned_d = nullptr;
@@ -174,6 +188,8 @@ struct JobRun {
     double b2 = 0, scale = 1, bytes = 0;
     bool zero = false;
     bool warm = false;            // x holds an initial guess (single shift, FP32 engine)
+    double switch_rel = 0;        // double-float phase of a hybrid solve: halt at ||r|| <= this * ||b||
+    int iters0 = 0;               // iterations done by an earlier phase (byte accounting)
     uint64_t launches0 = 0;
     lqcd_solve_info I;
 };

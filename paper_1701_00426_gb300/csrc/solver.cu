@@ -104,6 +104,16 @@ __global__ void k_init_vectors(const void *src, void *r, void *x, void *ps, long
     }
 }
 
+// dst (FP32) = scale * src (double-float), rounded to nearest
+__global__ void k_df_to_f32(const float4 *__restrict__ src, float2 *__restrict__ dst, long n, double scale)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float4 v = src[t];
+    dst[t] = make_float2((float)(df_to_f64(make_float2(v.x, v.y)) * scale),
+                         (float)(df_to_f64(make_float2(v.z, v.w)) * scale));
+}
+
 template <int VP>
 __global__ void k_scale_vec(void *v, long n3, float f)
 {
@@ -387,9 +397,33 @@ static void launch_iteration(const IterBatch<NJ> &B, int ntot, int vp, int lf, c
 
 void GraphCache::reset()
 {
-    if (exec) cudaGraphExecDestroy(exec);
-    exec = nullptr;
-    key = ~0ull;
+    for (int k = 0; k < kEntries; ++k) {
+        if (exec[k]) cudaGraphExecDestroy(exec[k]);
+        exec[k] = nullptr;
+        key[k] = ~0ull;
+        used[k] = 0;
+    }
+}
+
+cudaGraphExec_t GraphCache::find(uint64_t k)
+{
+    for (int e = 0; e < kEntries; ++e)
+        if (exec[e] && key[e] == k) {
+            used[e] = ++tick;
+            return exec[e];
+        }
+    return nullptr;
+}
+
+void GraphCache::put(uint64_t k, cudaGraphExec_t g)
+{
+    int v = 0;
+    for (int e = 1; e < kEntries; ++e)
+        if (used[e] < used[v]) v = e;
+    if (exec[v]) cudaGraphExecDestroy(exec[v]);
+    exec[v] = g;
+    key[v] = k;
+    used[v] = ++tick;
 }
 
 static uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603ull)
@@ -404,28 +438,39 @@ static uint64_t fnv1a(const void *p, size_t n, uint64_t h = 1469598103934665603u
 
 // Run iteration chunks (graph of `chunk` iterations) until every job halts.
 // Pipelined: chunk k+1 is queued before chunk k's halt words are read.
+// The cached graph of `chunk` iterations of batch B (captured on first use).
 template <int NJ>
-static int run_until_halt(lqcd_ctx *c, const IterBatch<NJ> &B, int vp, int lf, int chunk, int max_iter,
-                          cudaStream_t s, std::vector<int> &halts)
+static int chunk_graph(lqcd_ctx *c, const IterBatch<NJ> &B, int vp, int lf, int chunk, cudaStream_t s,
+                       cudaGraphExec_t &out)
 {
-    int ntot = B.tile_start[B.njobs];
+    // blocks of the launch: interleaved jobs share one tile count
+    const int ntot = B.interleave ? B.job[0].ntiles * B.njobs : B.tile_start[B.njobs];
+    if (ntot <= 0) return fail(LQCD_EINVAL, "empty iteration batch");
     uint64_t key = fnv1a(&B, sizeof(B));
     key = fnv1a(&vp, sizeof vp, key);
     key = fnv1a(&lf, sizeof lf, key);
     key = fnv1a(&chunk, sizeof chunk, key);
     key ^= (uint64_t)NJ * 0x9E3779B97F4A7C15ull;
-    if (c->graph.key != key || !c->graph.exec) {
-        c->graph.reset();
-        cudaGraph_t g;
-        LQCD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        for (int k = 0; k < chunk; ++k) launch_iteration<NJ>(B, ntot, vp, lf, s);
-        cudaError_t e = cudaStreamEndCapture(s, &g);
-        if (e != cudaSuccess) return cuda_fail(e, "graph capture");
-        e = cudaGraphInstantiate(&c->graph.exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
-        c->graph.key = key;
-    }
+    out = c->graph.find(key);
+    if (out) return LQCD_OK;
+    cudaGraph_t g;
+    LQCD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+    for (int k = 0; k < chunk; ++k) launch_iteration<NJ>(B, ntot, vp, lf, s);
+    cudaError_t e = cudaStreamEndCapture(s, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&out, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+    c->graph.put(key, out);
+    return LQCD_OK;
+}
+
+template <int NJ>
+static int run_until_halt(lqcd_ctx *c, const IterBatch<NJ> &B, int vp, int lf, int chunk, int max_iter,
+                          cudaStream_t s, std::vector<int> &halts)
+{
+    cudaGraphExec_t exec = nullptr;
+    if (int st = chunk_graph<NJ>(c, B, vp, lf, chunk, s, exec)) return st;
     const int nj = B.njobs;
     // pinned status words: [2][nj] halts
     int *hs = c->h_pinned;
@@ -435,7 +480,7 @@ static int run_until_halt(lqcd_ctx *c, const IterBatch<NJ> &B, int vp, int lf, i
     LQCD_CUDA(cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
     LQCD_CUDA(cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     auto enqueue = [&](int sl) -> cudaError_t {
-        cudaError_t e = cudaGraphLaunch(c->graph.exec, s);
+        cudaError_t e = cudaGraphLaunch(exec, s);
         c->launches += 4 * (uint64_t)chunk;
         for (int j = 0; j < nj && e == cudaSuccess; ++j)
             e = cudaMemcpyAsync(hs + sl * kMaxJobs + j, &B.job[j].st->halt, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -742,6 +787,7 @@ int job_setup(JobRun &J, cudaStream_t s)
     const double tol_iter = f16 ? std::max(0.5 * J.tol, 3e-4) : 0.5 * J.tol;
     init_state(S, J.mass, J.shifts, J.n_shift, tol_iter, J.b2 * J.scale * J.scale, c->opts.max_iter);
     S.rho = rho0 * J.scale * J.scale;  // the iterated residual starts at b (or at the guess's residual)
+    if (J.vp == VP_DF && J.switch_rel > 0.0) S.rel_stop2 = J.switch_rel * J.switch_rel * J.b2 * J.scale * J.scale;
     if (J.vp == VP_F32) {
         if (!f16) S.rel_stop2 = c->opts.delta_reliable * c->opts.delta_reliable * S.rho;
         if (J.x && !J.warm) LQCD_CUDA(cudaMemsetAsync(J.x, 0, (size_t)J.n_shift * n3 * sizeof(double2), s));
@@ -815,7 +861,8 @@ static int refine_shifts_packed(JobRun &J, int lf, cudaStream_t s, int &iters, i
     const long n3 = 3 * (long)c->Vh;
     const void *links = lf == LF_F32_12 ? c->lnk_f12.ptr : c->lnk_f18.ptr;
     std::vector<JobRun> R(J.n_shift);
-    std::vector<Workspace> W(J.n_shift);
+    std::vector<Workspace> &W = c->ref_ws;
+    if ((int)W.size() < J.n_shift) W.resize(J.n_shift);
     std::vector<int> idx;
     int st;
     for (int i = 0; i < J.n_shift; ++i) {
@@ -847,19 +894,9 @@ static int refine_shifts_packed(JobRun &J, int lf, cudaStream_t s, int &iters, i
         B.max_shift = 1;
         B.interleave = 1;
         for (int k = 0; k < B.njobs; ++k) job_fill(R[idx[k]], B.job[k]);
-        const int ntot = R[idx[0]].P.ntiles * B.njobs;
         const int chunk = c->opts.check_every;
         cudaGraphExec_t exec = nullptr;
-        {
-            cudaGraph_t g;
-            LQCD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-            for (int k = 0; k < chunk; ++k) launch_iteration<kMaxJobs>(B, ntot, VP_F32, lf, s);
-            cudaError_t e = cudaStreamEndCapture(s, &g);
-            if (e != cudaSuccess) return cuda_fail(e, "refinement graph capture");
-            e = cudaGraphInstantiate(&exec, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return cuda_fail(e, "refinement graph instantiate");
-        }
+        if ((st = chunk_graph<kMaxJobs>(c, B, VP_F32, lf, chunk, s, exec))) return st;
         int *hs = c->h_pinned;
         const int max_chunks = 4 * (c->opts.max_iter / chunk + 4);
         int rc = LQCD_OK;
@@ -878,7 +915,6 @@ static int refine_shifts_packed(JobRun &J, int lf, cudaStream_t s, int &iters, i
             }
             if (all) break;
         }
-        cudaGraphExecDestroy(exec);
         if (rc) return rc;
     }
     for (int i = 0; i < J.n_shift; ++i) {
@@ -897,10 +933,17 @@ static int refine_shifts_packed(JobRun &J, int lf, cudaStream_t s, int &iters, i
         const double spin = 24.0;
         J.bytes += (double)c->Vh * O.iters * (iter_bytes_base(VP_F32, lf) + 4 * spin);
     }
-    for (auto &w : W) {
-        w.vec.release(); w.ieee.release(); w.part.release(); w.tickets.release(); w.state.release();
-    }
     return LQCD_OK;
+}
+
+// Algorithmic bytes of the iterations a job ran since iteration J.iters0.
+static double phase_bytes(const JobRun &J, const SolverState &O)
+{
+    double shift_it = 0;
+    for (int i = 0; i < J.n_shift; ++i)
+        shift_it += std::max(0, (O.shift_iters[i] ? O.shift_iters[i] : O.iters) - J.iters0);
+    const double spin = J.vp == VP_DF ? 48.0 : 24.0;
+    return (double)J.c->Vh * (std::max(0, O.iters - J.iters0) * iter_bytes_base(J.vp, J.lf) + shift_it * 4 * spin);
 }
 
 // After the iterations: IEEE solutions, FP64 true residuals, refinement.
@@ -918,13 +961,8 @@ int job_finish(JobRun &J, cudaStream_t s)
     LQCD_CUDA(cudaStreamSynchronize(s));
     if (O.halt == HALT_NAN) return fail(LQCD_ENAN, "NaN/Inf or breakdown in the multi-shift iteration");
     J.I.iters = O.iters;
-    double shift_it = 0;
-    for (int i = 0; i < J.n_shift; ++i) {
-        J.I.shift_iters[i] = O.shift_iters[i];
-        shift_it += O.shift_iters[i] ? O.shift_iters[i] : O.iters;
-    }
-    const double spin = J.vp == VP_DF ? 48.0 : 24.0;
-    J.bytes += (double)c->Vh * (O.iters * iter_bytes_base(J.vp, J.lf) + shift_it * 4 * spin);
+    for (int i = 0; i < J.n_shift; ++i) J.I.shift_iters[i] = O.shift_iters[i];
+    J.bytes += phase_bytes(J, O);
     const bool maxed = O.halt == HALT_MAXITER;
     for (int i = 0; i < J.n_shift; ++i) {
         const size_t off = (size_t)i * n3;
@@ -973,14 +1011,14 @@ int job_finish(JobRun &J, cudaStream_t s)
     return status;
 }
 
-int job_init(JobRun &J, lqcd_ctx *c, Workspace *W, double mass, const double *shifts, int n_shift, double tol,
-             const double2 *b, double2 *x)
+static int job_init_prec(JobRun &J, lqcd_ctx *c, Workspace *W, int prec, double mass, const double *shifts,
+                         int n_shift, double tol, const double2 *b, double2 *x)
 {
     int st = validate_solve(c, mass, shifts, n_shift, tol);
     if (st) return st;
     J.c = c;
-    J.vp = c->opts.prec == LQCD_PREC_FP64 || c->opts.prec == LQCD_PREC_FP64_NATIVE ? VP_DF : VP_F32;
-    J.lf = link_fmt_for(c, J.vp == VP_DF ? LQCD_PREC_FP64 : c->opts.prec, &J.links);
+    J.vp = prec == LQCD_PREC_FP64 || prec == LQCD_PREC_FP64_NATIVE ? VP_DF : VP_F32;
+    J.lf = link_fmt_for(c, J.vp == VP_DF ? LQCD_PREC_FP64 : prec, &J.links);
     J.mass = mass;
     J.n_shift = n_shift;
     for (int i = 0; i < n_shift; ++i) J.shifts[i] = shifts[i];
@@ -988,6 +1026,57 @@ int job_init(JobRun &J, lqcd_ctx *c, Workspace *W, double mass, const double *sh
     J.b = b;
     J.x = x;
     return ensure_workspace_in(c, W ? *W : c->ws, J.vp, n_shift, J.P);
+}
+
+int job_init(JobRun &J, lqcd_ctx *c, Workspace *W, double mass, const double *shifts, int n_shift, double tol,
+             const double2 *b, double2 *x)
+{
+    return job_init_prec(J, c, W, c->opts.prec, mass, shifts, n_shift, tol, b, x);
+}
+
+// Hybrid mixed precision, switch from the double-float phase D (halted at
+// ||r|| <= fp64_until ||b||) to the FP32 phase F: the double-float solutions
+// go to the IEEE accumulators, the base residual is recomputed against the
+// FP64 operator, the directions are rounded to FP32 at the new scale, and the
+// recurrence scalars carry over unchanged (the same Krylov iteration goes on).
+static int job_switch_to_f32(JobRun &D, JobRun &F, cudaStream_t s)
+{
+    lqcd_ctx *c = D.c;
+    const long n3 = 3 * (long)c->Vh;
+    SolverState O;
+    LQCD_CUDA(cudaMemcpyAsync(&O, D.P.st, sizeof O, cudaMemcpyDeviceToHost, s));
+    LQCD_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < D.n_shift; ++i) {
+        const size_t off = (size_t)i * n3;
+        k_vec_to_ieee<VP_DF><<<nblk(n3), 256, 0, s>>>((const float4 *)D.P.x + off, D.x + off, n3, 1.0 / D.scale, 0);
+    }
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += D.n_shift;
+    double rr;
+    const double a0 = D.mass * D.mass + D.shifts[O.base];
+    int st = refresh_residual(c, F.P, VP_F32, a0, D.x + (size_t)O.base * n3, D.b, F.P.r_hi, s, rr);
+    if (st) return st;
+    if (!std::isfinite(rr)) return fail(LQCD_ENAN, "NaN/Inf at the switch to FP32");
+    F.scale = unit_scale(rr, 6.0 * c->Vh);
+    k_ieee_to_vec<VP_F32><<<nblk(n3), 256, 0, s>>>(F.P.r_hi, F.P.r, n3, F.scale);
+    k_df_to_f32<<<nblk(n3 * D.n_shift), 256, 0, s>>>((const float4 *)D.P.ps, (float2 *)F.P.ps, n3 * D.n_shift,
+                                                     F.scale / D.scale);
+    k_zero_vec<VP_F32><<<nblk(n3 * D.n_shift), 256, 0, s>>>(F.P.x, n3 * D.n_shift);
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += 3;
+    SolverState U = O;
+    U.rho = rr * F.scale * F.scale;
+    U.rel_stop2 = c->opts.delta_reliable * c->opts.delta_reliable * U.rho;
+    U.tol2_b2 = 0.25 * F.tol * F.tol * F.b2 * F.scale * F.scale;
+    U.halt = rr <= 0.25 * F.tol * F.tol * F.b2 ? HALT_CONVERGED : HALT_NONE;
+    U.do_k4 = 0;
+    if (U.halt) U.n_act = 0;
+    LQCD_CUDA(cudaMemcpyAsync(F.P.st, &U, sizeof U, cudaMemcpyHostToDevice, s));
+    F.iters0 = O.iters;
+    F.bytes = D.bytes + phase_bytes(D, O);
+    F.I = D.I;
+    F.launches0 = D.launches0;
+    return LQCD_OK;
 }
 
 // One packed iteration launch over several jobs (serving ticks).
@@ -1008,27 +1097,47 @@ int mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, 
 {
     const auto t0 = std::chrono::steady_clock::now();
     if (!b || !x) return fail(LQCD_EINVAL, "NULL argument");
+    // FP32 links: double-float iterations down to fp64_until, then FP32
+    const bool hybrid = c->opts.prec == LQCD_PREC_FP32 && c->opts.fp64_until > 0.0;
     JobRun J;
-    int st = job_init(J, c, nullptr, mass, shifts, n_shift, tol, b, x);
+    int st = job_init_prec(J, c, nullptr, hybrid ? LQCD_PREC_FP64 : c->opts.prec, mass, shifts, n_shift, tol, b, x);
     if (st) return st;
+    if (hybrid) J.switch_rel = c->opts.fp64_until;
     cudaStream_t s = c->stream;
     if (s_user && s_user != s) LQCD_CUDA(cudaStreamSynchronize(s_user));
     if ((st = job_setup(J, s))) return st;
-    if (!J.zero) {
+    auto iterate = [&](JobRun &R, bool stop_on_reliable, int &halt) -> int {
         IterBatch<1> B;
         memset(&B, 0, sizeof B);
         B.njobs = 1;
-        B.max_shift = J.n_shift;
-        B.tile_start[1] = J.P.ntiles;
-        job_fill(J, B.job[0]);
+        B.max_shift = R.n_shift;
+        B.tile_start[1] = R.P.ntiles;
+        job_fill(R, B.job[0]);
         for (;;) {
             std::vector<int> halts;
-            if ((st = run_until_halt<1>(c, B, J.vp, J.lf, c->opts.check_every, c->opts.max_iter, s, halts))) return st;
-            if (halts[0] != HALT_RELIABLE) break;
-            if ((st = job_reliable_update(J, s))) return st;
+            int rc = run_until_halt<1>(c, B, R.vp, R.lf, c->opts.check_every, c->opts.max_iter, s, halts);
+            if (rc) return rc;
+            halt = halts[0];
+            if (halt != HALT_RELIABLE || stop_on_reliable) return LQCD_OK;
+            if ((rc = job_reliable_update(R, s))) return rc;
+        }
+    };
+    JobRun F;
+    JobRun *fin = &J;
+    if (!J.zero) {
+        int halt = HALT_NONE;
+        if ((st = iterate(J, hybrid, halt))) return st;
+        if (hybrid && halt == HALT_RELIABLE) {
+            if ((st = job_init_prec(F, c, &c->ws32, LQCD_PREC_FP32, mass, shifts, n_shift, tol, b, x))) return st;
+            F.b2 = J.b2;
+            if ((st = job_switch_to_f32(J, F, s))) return st;
+            if ((st = iterate(F, false, halt))) return st;
+            fin = &F;
         }
     }
-    st = job_finish(J, s);
+    JobRun &R = *fin;
+    st = job_finish(R, s);
+    J.I = R.I;
     J.I.secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     if (info) *info = J.I;
     if (st == LQCD_ENOCONV) set_error("solver did not reach tol within max_iter");

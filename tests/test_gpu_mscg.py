@@ -55,20 +55,40 @@ def test_15_shifts_fp64(gpu, orc, dims):
     check_solution(orc, dims, U, 0.01, shifts, b, x, 1e-10, xref)
 
 
-@pytest.mark.parametrize("prec,recon", [(1, 18), (1, 12), (2, 12)])
-def test_15_shifts_mixed_precision(gpu, orc, prec, recon):
-    """FP32 / FP16-link iterations with FP64 reliable updates reach 1e-10."""
+@pytest.mark.parametrize("prec,recon,fp64_until",
+                         [(1, 18, 1e-4), (1, 12, 1e-4), (1, 12, 1e-2), (1, 18, 0.0), (1, 12, 0.0), (2, 12, 0.0)])
+def test_15_shifts_mixed_precision(gpu, orc, prec, recon, fp64_until):
+    """FP32 / FP16-link iterations with FP64 reliable updates reach 1e-10,
+    with the FP32 phase from the start (fp64_until = 0) or after a
+    double-float phase down to fp64_until."""
     dims = (8, 8, 8, 8)
     shifts = inputs.log_shifts(15)
     U = inputs.random_links(dims)
     b = inputs.gaussian_field(dims, k=2)
-    xref, _ = orc.mscg(dims, U, 0.01, shifts, b, 1e-10)
-    with gpu.Context(dims, prec=prec, recon=recon) as c:
+    xref, iref = orc.mscg(dims, U, 0.01, shifts, b, 1e-10)
+    with gpu.Context(dims, prec=prec, recon=recon, fp64_until=fp64_until) as c:
         c.links_upload(U)
         x, info = c.mscg_solve(0.01, shifts, 1e-10, b)
     assert max(info["true_resid"]) <= 1e-10
     assert info["reliable_updates"] > 0
+    # the multi-shift iteration is one Krylov run across the switch
+    if prec == 1:
+        assert abs(info["iters"] - iref["iters"]) <= 0.1 * iref["iters"] + 10
     check_solution(orc, dims, U, 0.01, shifts, b, x, 1e-10, xref)
+
+
+def test_hybrid_switch_on_ragged_lattice(gpu, orc):
+    """Double-float phase, switch and FP32 phase on a lattice whose half
+    volume is not a multiple of the tile (ragged last tile)."""
+    dims = (6, 6, 10, 8)
+    shifts = [1e-4, 1e-2, 0.3, 5.0]
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=5)
+    with gpu.Context(dims, prec=1, recon=12, fp64_until=1e-3) as c:
+        c.links_upload(U)
+        x, info = c.mscg_solve(0.02, shifts, 1e-10, b)
+    assert max(info["true_resid"]) <= 1e-10
+    check_solution(orc, dims, U, 0.02, shifts, b, x, 1e-10)
 
 
 def test_shift_order_and_duplicates(gpu, orc):
