@@ -39,6 +39,25 @@ WORKLOAD = "mscg 32^4, m=0.01, 15 shifts log-spaced 1e-5..1e2, tol 1e-10, FP64 (
 COUNTS_KEY = "mscg_32x32x32x32_m0.01_15shifts_tol1e-10"
 
 
+# DRAM traffic of the dominant kernel (k_it_deo2, FP64 iteration) from one ncu
+# capture at 24^4 (profiles/mscg_iteration_kernels_24x24x24x24_ncu.md):
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch / (V/2).  It scales
+# with the even sites (links stream from HBM at both sizes, spinors hit L2), so
+# a launch at V/2 sites moves bytes_per_site * V/2.  Reported only while the
+# kernel sources still hash to the captured version.
+K2_TRAFFIC = {"bytes_per_site": 1273.1, "src_sha256_16": "0d056e60b2915c39",
+              "sources": ["solver_kernels.cuh", "deo_core.cuh", "common.cuh", "internal.h"]}
+
+
+def k2_traffic_per_site():
+    import hashlib
+    h = hashlib.sha256()
+    for f in K2_TRAFFIC["sources"]:
+        with open(os.path.join(ROOT, "paper_1701_00426_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return K2_TRAFFIC["bytes_per_site"] if h.hexdigest()[:16] == K2_TRAFFIC["src_sha256_16"] else None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -281,11 +300,12 @@ def packed_bench(lqcd, inputs):
             "bitwise_equal_to_separate": same, "max_true_resid": max(max(i["true_resid"]) for i in infos)}
 
 
-def serving_bench(lqcd, inputs, n_req=40):
+def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 30):
     """Poisson stream of multi-shift requests over resident 8^4/16^4/24^4/32^4
     fields (1..16 shifts log-spaced in [1e-5, 1e2], tol 1e-8 or 1e-10,
-    m = 0.01), 16 GB budget.  A burst run measures capacity; a Poisson run at
-    ~70% of it measures latency."""
+    m = 0.01) under an HBM budget.  A burst run (all requests at t = 0)
+    measures capacity; Poisson runs at the given fractions of it measure
+    latency.  Peak admitted bytes and slots are sampled during each run."""
     sizes = [(8,) * 4, (16,) * 4, (24,) * 4, (32,) * 4]
     rng = np.random.default_rng(inputs.ARRIVAL_SEED)
     reqs = []
@@ -294,49 +314,58 @@ def serving_bench(lqcd, inputs, n_req=40):
         ns = int(rng.integers(1, 17))
         tol = [1e-8, 1e-10][int(rng.integers(0, 2))]
         reqs.append((f, ns, tol, k))
-    res = {}
-    with lqcd.Server(16 << 30, max_slots=16, max_queue=4096) as srv:
+    res = {"requests": n_req, "hbm_budget": budget}
+    with lqcd.Server(budget, max_slots=16, max_queue=4096) as srv:
         fids = [srv.register_field(d, inputs.random_links(d)) for d in sizes]
         srcs = {f: inputs.gaussian_field(sizes[f], k=100 + f) for f in range(4)}
 
         def run(arrivals):
-            """Submit at the given offsets; returns (wall, per-request latencies)."""
+            """Submit at the given offsets; returns (wall, latencies, peak bytes, peak slots, worst residual)."""
             t0 = time.perf_counter()
             pend, lat = [], []
+            peak_b = peak_s = 0
+            worst = 0.0
             i = 0
             while i < len(reqs) or pend:
                 now = time.perf_counter() - t0
                 while i < len(reqs) and arrivals[i] <= now:
                     f, ns, tol, k = reqs[i]
-                    pend.append((srv.submit(fids[f], MASS, inputs.log_shifts(ns), tol, srcs[f]), f, ns,
+                    pend.append((srv.submit(fids[f], MASS, inputs.log_shifts(ns), tol, srcs[f]), f, ns, tol,
                                  time.perf_counter()))
                     i += 1
                 keep = []
-                for t, f, ns, ts in pend:
+                for t, f, ns, tol, ts in pend:
                     r = srv.poll(t, fids[f], ns)
                     if r is None:
-                        keep.append((t, f, ns, ts))
+                        keep.append((t, f, ns, tol, ts))
                     else:
                         lat.append(time.perf_counter() - ts)
-                        assert max(r[1]["true_resid"]) <= 1e-8
+                        worst = max(worst, max(r[1]["true_resid"]) / tol)
+                        assert worst <= 1.0
                 pend = keep
+                st = srv.stats()
+                peak_b = max(peak_b, st["hbm_in_use"])
+                peak_s = max(peak_s, st["active_slots"])
                 time.sleep(0.0005)
-            return time.perf_counter() - t0, np.array(lat)
+            return time.perf_counter() - t0, np.array(lat), peak_b, peak_s, worst
 
-        wall, lat = run(np.zeros(len(reqs)))
-        cap = len(reqs) / wall
-        res["burst"] = {"requests": len(reqs), "solves_per_s": round(cap, 3), "wall_s": round(wall, 2),
-                        "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
-                        "p99_latency_s": round(float(np.percentile(lat, 99)), 4)}
-        rate = 0.7 * cap
-        wall, lat = run(inputs.poisson_arrivals(rate, len(reqs)))
-        res["poisson"] = {"rate_hz": round(rate, 3), "requests": len(reqs),
-                          "solves_per_s": round(len(reqs) / wall, 3),
-                          "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
-                          "p99_latency_s": round(float(np.percentile(lat, 99)), 4)}
+        def summary(wall, lat, peak_b, peak_s, worst):
+            return {"solves_per_s": round(len(reqs) / wall, 3), "wall_s": round(wall, 2),
+                    "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
+                    "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
+                    "peak_admitted_bytes": int(peak_b), "peak_active_slots": int(peak_s),
+                    "max_true_resid_over_tol": round(worst, 3)}
+
+        out = run(np.zeros(len(reqs)))
+        cap = len(reqs) / out[0]
+        res["burst"] = summary(*out)
+        for load in loads:
+            rate = load * cap
+            out = run(inputs.poisson_arrivals(rate, len(reqs)))
+            res[f"poisson_{load:g}"] = {"rate_hz": round(rate, 3), **summary(*out)}
         st = srv.stats()
-        res["hbm_budget"] = st["hbm_budget"]
         res["ticks"] = st["ticks"]
+        res["rejected"] = st["rejected"]
     return res
 
 
@@ -440,6 +469,8 @@ def run_ours(args, rank, world, local):
     shifts = inputs.log_shifts(N_SHIFT)
     ctx = lqcd.Context(DIMS)
     ctx.links_upload(U)
+    if args.solve_prec == "fp32":
+        ctx.set_opts(prec=1, recon=12, fp64_until=3e-4)
     bd = lqcd.to_device_spinor(b)
     xd = torch.empty((N_SHIFT, 3, ctx.Vh), dtype=torch.complex128, device="cuda")
     info = None
@@ -470,7 +501,8 @@ def run_ours(args, rank, world, local):
             print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                               "iters": it["iters"], "max_true_resid": worst_res, "gpu_launches": launches,
-                              "config": {"workload": WORKLOAD, "only_solve": True}}), flush=True)
+                              "config": {"workload": WORKLOAD, "only_solve": True, "prec": args.solve_prec}}),
+                  flush=True)
         ctx.close()
         return
 
@@ -499,8 +531,12 @@ def run_ours(args, rank, world, local):
     shares = [m / sum(ms) for m in ms]
     kdom = int(np.argmax(ms))
     achieved = kbytes[kdom] / (ms[kdom] * 1e-3) / 1e9
+    tps = k2_traffic_per_site() if kdom == 1 else None
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 3), "traffic": None, "kernel": knames[kdom],
+                "frac": round(achieved / hbm_peak, 3),
+                "traffic": None if tps is None else round(tps * Vh / 1e9, 4),
+                "traffic_unit": "GB per launch", "algorithmic": round(kbytes[kdom] / 1e9, 4),
+                "kernel": knames[kdom],
                 "peak_source": peak_src, "note": "of measured"}
     kernels = {knames[k]: {"ms": round(ms[k], 4), "share": round(shares[k], 3),
                            "GB_s": round(kbytes[k] / (ms[k] * 1e-3) / 1e9, 1)} for k in range(4)}
@@ -541,7 +577,8 @@ def run_ours(args, rank, world, local):
     for name, fn in [("mixed_48", lambda: mixed_48_bench(lqcd, inputs, torch)),
                      ("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
                      ("packed", lambda: packed_bench(lqcd, inputs)),
-                     ("serving", lambda: serving_bench(lqcd, inputs))]:
+                     ("serving", lambda: serving_bench(lqcd, inputs, n_req=args.serving_requests,
+                                                       budget=int(args.serving_budget_gb * (1 << 30))))]:
         if name in args.skip:
             continue
         try:
@@ -586,7 +623,14 @@ def main():
     ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: mixed_48 batched packed serving")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
+    ap.add_argument("--serving-requests", type=int, default=40, help="requests per serving run (default 40)")
+    ap.add_argument("--serving-budget-gb", type=float, default=16.0, help="HBM budget of the serving runs")
+    ap.add_argument("--solve-prec", choices=["fp64", "fp32"], default="fp64",
+                    help="with --only-solve: precision of the timed solves (fp32: 12-real links, FP64 phase "
+                         "to 3e-4, FP64 reliable updates)")
     args = ap.parse_args()
+    if args.solve_prec != "fp64" and not args.only_solve:
+        ap.error("--solve-prec applies to --only-solve runs")
     if args.impl == "reference":
         # the oracle runs on the host; ranks other than 0 exit without work
         run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
