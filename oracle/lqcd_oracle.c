@@ -393,11 +393,12 @@ int oracle_mscg(const int N[4], const cplx *links, double mass,
 /* Timing support                                                            */
 /* ------------------------------------------------------------------------ */
 
-/* Number of threads the parallel loops use (1 when built without OpenMP). */
+/* Set the threads of the parallel loops (n <= 0: one per processor); returns
+ * the number in use (1 when built without OpenMP). */
 int oracle_set_threads(int n)
 {
 #ifdef _OPENMP
-    if (n > 0) omp_set_num_threads(n);
+    omp_set_num_threads(n > 0 ? n : omp_get_num_procs());
     return omp_get_max_threads();
 #else
     (void)n;
