@@ -327,12 +327,16 @@ def packed_bench(lqcd, inputs):
             "bitwise_equal_to_separate": same, "max_true_resid": max(max(i["true_resid"]) for i in infos)}
 
 
-def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 30):
+def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 30, mixed=False, sequential=True):
     """Poisson stream of multi-shift requests over resident 8^4/16^4/24^4/32^4
     fields (1..16 shifts log-spaced in [1e-5, 1e2], tol 1e-8 or 1e-10,
     m = 0.01) under an HBM budget.  A burst run (all requests at t = 0)
     measures capacity; Poisson runs at the given fractions of it measure
-    latency.  Peak admitted bytes and slots are sampled during each run."""
+    latency.  Peak admitted bytes and slots are sampled during each run.
+    mixed: requests run in mixed precision (FP32 12-real links, FP64 phase
+    to 3e-4, FP64 reliable updates).  sequential: also time the same requests
+    solved one after another by the plain FP64 solver (device-resident
+    sources, no host copies)."""
     sizes = [(8,) * 4, (16,) * 4, (24,) * 4, (32,) * 4]
     rng = np.random.default_rng(inputs.ARRIVAL_SEED)
     reqs = []
@@ -341,8 +345,10 @@ def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 3
         ns = int(rng.integers(1, 17))
         tol = [1e-8, 1e-10][int(rng.integers(0, 2))]
         reqs.append((f, ns, tol, k))
-    res = {"requests": n_req, "hbm_budget": budget}
+    res = {"requests": n_req, "hbm_budget": budget, "prec": "fp32_12r (FP64 phase to 3e-4)" if mixed else "fp64"}
     with lqcd.Server(budget, max_slots=16, max_queue=4096) as srv:
+        if mixed:
+            srv.set_opts(prec=1, recon=12, fp64_until=3e-4)
         fids = [srv.register_field(d, inputs.random_links(d)) for d in sizes]
         srcs = {f: inputs.gaussian_field(sizes[f], k=100 + f) for f in range(4)}
 
@@ -393,6 +399,30 @@ def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 3
         st = srv.stats()
         res["ticks"] = st["ticks"]
         res["rejected"] = st["rejected"]
+    if not sequential:
+        return res
+    # the same requests solved one after another by the plain FP64 solver
+    import torch
+    ctxs, bds = [], []
+    for f, d in enumerate(sizes):
+        c = lqcd.Context(d)
+        c.links_upload(inputs.random_links(d))
+        ctxs.append(c)
+        bds.append(lqcd.to_device_spinor(inputs.gaussian_field(d, k=100 + f)))
+    for f in range(4):  # graphs and workspaces
+        ctxs[f].mscg_solve_dev(MASS, inputs.log_shifts(16), 1e-10, bds[f],
+                               torch.empty((16, 3, ctxs[f].Vh), dtype=torch.complex128, device="cuda"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for f, ns, tol, k in reqs:
+        xd = torch.empty((ns, 3, ctxs[f].Vh), dtype=torch.complex128, device="cuda")
+        ctxs[f].mscg_solve_dev(MASS, inputs.log_shifts(ns), tol, bds[f], xd)
+    torch.cuda.synchronize()
+    seq = len(reqs) / (time.perf_counter() - t0)
+    for c in ctxs:
+        c.close()
+    res["sequential_fp64_solves_per_s"] = round(seq, 3)
+    res["speedup_burst_vs_sequential_fp64"] = round(res["burst"]["solves_per_s"] / seq, 3)
     return res
 
 
@@ -615,7 +645,10 @@ def run_ours(args, rank, world, local):
                      ("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
                      ("packed", lambda: packed_bench(lqcd, inputs)),
                      ("serving", lambda: serving_bench(lqcd, inputs, n_req=args.serving_requests,
-                                                       budget=int(args.serving_budget_gb * (1 << 30))))]:
+                                                       budget=int(args.serving_budget_gb * (1 << 30)))),
+                     ("serving_mixed", lambda: serving_bench(lqcd, inputs, n_req=args.serving_requests, loads=(0.8,),
+                                                             budget=int(args.serving_budget_gb * (1 << 30)),
+                                                             mixed=True, sequential=False))]:
         if name in args.skip:
             continue
         try:
@@ -623,6 +656,10 @@ def run_ours(args, rank, world, local):
         except Exception as exc:  # reported, never hidden
             extras[name] = {"error": repr(exc)}
         torch.cuda.empty_cache()
+
+    sm, sf = extras.get("serving_mixed", {}), extras.get("serving", {})
+    if "burst" in sm and "sequential_fp64_solves_per_s" in sf:
+        sm["speedup_burst_vs_sequential_fp64"] = round(sm["burst"]["solves_per_s"] / sf["sequential_fp64_solves_per_s"], 3)
 
     # CPU baseline: the oracle on a bounded sample of the same workload
     counts = oracle_counts()
@@ -658,7 +695,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sweep", type=int, nargs="*", default=[16, 24, 32, 48])
     ap.add_argument("--lattice", type=int, default=32, help="side of the solve lattice (default 32)")
-    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: mixed_48 batched packed serving")
+    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: mixed_48 batched packed serving serving_mixed")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
     ap.add_argument("--only-deo", action="store_true",

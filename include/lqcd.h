@@ -284,6 +284,16 @@ int lqcd_serve_register_field(lqcd_server *srv, const int dims[4], const double 
 int lqcd_serve_submit(lqcd_server *srv, int field_id, double mass, const double *shifts,
                       int n_shift, double tol, const double *b, uint64_t *ticket);
 
+/* Options of the requests submitted after this call, and of every field's
+ * context: prec LQCD_PREC_FP64 (default) or LQCD_PREC_FP32 (mixed precision:
+ * double-float iterations down to fp64_until, then FP32 iterations with FP64
+ * reliable updates and per-shift refinement; recon selects the FP32 link
+ * format).  A mixed request reserves its FP32 and refinement workspaces in
+ * the HBM budget as well.  LQCD_EINVAL for invalid options or another prec;
+ * LQCD_EBUSY while requests are queued or running.  No counterpart in the
+ * paper (serving is outside its scope). */
+int lqcd_serve_set_opts(lqcd_server *srv, const lqcd_opts *opts);
+
 /* LQCD_ENOTREADY until the request has finished; then copies x
  * ([n_shift][Vh][3] complex128) and info, and forgets the ticket. */
 int lqcd_serve_poll(lqcd_server *srv, uint64_t ticket, double *x, lqcd_solve_info *info);

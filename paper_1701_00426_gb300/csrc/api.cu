@@ -61,7 +61,7 @@ size_t ctx_device_bytes(const lqcd_ctx *c)
     return s;
 }
 
-static int check_opts(const lqcd_opts *o)
+int validate_opts(const lqcd_opts *o)
 {
     if (o->prec < LQCD_PREC_FP64 || o->prec > LQCD_PREC_FP64_NATIVE) return fail(LQCD_EINVAL, "opts.prec out of range");
     if (o->recon != 18 && o->recon != 12) return fail(LQCD_EINVAL, "opts.recon must be 18 or 12");
@@ -106,7 +106,7 @@ int lqcd_create(const int dims[4], const lqcd_opts *opts, lqcd_ctx **out)
     lqcd_opts o;
     lqcd_default_opts(&o);
     if (opts) o = *opts;
-    int st = check_opts(&o);
+    int st = validate_opts(&o);
     if (st) return st;
     lqcd_ctx *c = new (std::nothrow) lqcd_ctx();
     if (!c) return fail(LQCD_ENOMEM, "host allocation failed");
@@ -147,7 +147,7 @@ void lqcd_destroy(lqcd_ctx *c)
 int lqcd_set_opts(lqcd_ctx *c, const lqcd_opts *o)
 {
     if (!c || !o) return fail(LQCD_EINVAL, "NULL argument");
-    int st = check_opts(o);
+    int st = validate_opts(o);
     if (st) return st;
     c->opts = *o;
     return LQCD_OK;

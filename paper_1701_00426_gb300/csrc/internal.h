@@ -197,7 +197,12 @@ int validate_solve(const lqcd_ctx *c, double mass, const double *shifts, int n_s
 int ensure_workspace_in(lqcd_ctx *c, Workspace &W, int vp, int n_shift, WsPtrs &P);
 int job_init(JobRun &J, lqcd_ctx *c, Workspace *W, double mass, const double *shifts, int n_shift, double tol,
              const double2 *b, double2 *x);
+int job_init_prec(JobRun &J, lqcd_ctx *c, Workspace *W, int prec, double mass, const double *shifts, int n_shift,
+                  double tol, const double2 *b, double2 *x);
 int job_setup(JobRun &J, cudaStream_t s);
+int job_reliable_update(JobRun &J, cudaStream_t s);
+int job_switch_to_f32(JobRun &D, JobRun &F, cudaStream_t s);
+int validate_opts(const lqcd_opts *o);
 void job_fill(const JobRun &J, IterJob &out);
 int job_finish(JobRun &J, cudaStream_t s);
 void launch_iteration_packed(const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s);

@@ -14,6 +14,10 @@
 // their work overlaps on the device with the requests already in flight.
 // The packed iteration of the current batch is captured as a CUDA graph and
 // replayed until the batch changes.
+// Mixed precision (server options with prec = FP32): a request iterates in
+// double-float down to fp64_until, switches to FP32 with reliable updates,
+// and is refined per shift at retirement, exactly as a solo mixed solve.
+// The requests of each engine are packed into their own launch each tick.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -41,10 +45,15 @@ struct Request {
     int status = LQCD_OK;
     std::chrono::steady_clock::time_point t_submit, t_done;
     // device side while active
-    Workspace ws;
+    Workspace ws, ws32;
     DevBuf bd, xd;
-    JobRun job;
+    JobRun job;                   // first engine (double-float, or FP32 from the start)
+    JobRun jobF;                  // FP32 phase after the switch
+    bool mixed = false;           // FP32 links (server prec = FP32 at submit)
+    double fp64_until = 0;
+    int phase = 0;                // 1 after the switch to FP32
     size_t bytes = 0;
+    JobRun &cur() { return phase ? jobF : job; }
 };
 
 struct Field {
@@ -60,6 +69,20 @@ static size_t request_bytes(const lqcd_ctx *c, int n_shift)
            + 2 * n3 * sizeof(double2)                         // r_hi, t (true residual)
            + (1 + (size_t)n_shift) * n3 * sizeof(double2)     // IEEE b, x
            + (size_t)ntiles * sizeof(double) + 1024 + sizeof(SolverState);
+}
+
+// Extra device bytes of a mixed-precision request: the FP32 phase's Krylov
+// vectors and IEEE temporaries, and the per-shift refinement workspaces
+// (held by the field's context after first use; counted per request).
+static size_t request_bytes_mixed(const lqcd_ctx *c, int n_shift)
+{
+    const size_t n3 = 3 * c->Vh;
+    const int ntiles = (int)((c->Vh + kTile - 1) / kTile);
+    const size_t phase = (3 + 2 * (size_t)n_shift) * n3 * sizeof(float2) + 2 * n3 * sizeof(double2) +
+                         (size_t)ntiles * sizeof(double) + 1024 + sizeof(SolverState);
+    const size_t refine = (size_t)n_shift * (5 * n3 * sizeof(float2) + 2 * n3 * sizeof(double2) +
+                                             (size_t)ntiles * sizeof(double) + 1024 + sizeof(SolverState));
+    return phase + refine;
 }
 
 }  // namespace lqcd
@@ -86,9 +109,10 @@ struct lqcd_server {
     std::chrono::steady_clock::time_point t_first, t_last;
     bool have_first = false;
     int n_active = 0;  // mirror for stats
-    // graph of the current batch
-    uint64_t batch_key = ~0ull;
-    cudaGraphExec_t exec = nullptr;
+    lqcd_opts opts;               // applied to fields and to requests submitted after
+    // graphs of the current batches, one per engine (double-float, FP32)
+    uint64_t batch_key[2] = {~0ull, ~0ull};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
     int chunk = 8;
     int error = LQCD_OK;
     std::string error_msg;
@@ -104,7 +128,7 @@ void lqcd_server::retire(std::unique_ptr<Request> &r, int st)
     Field &f = fields[r->field];
     lqcd_ctx *c = f.ctx;
     if (st == LQCD_OK || st == LQCD_ENOCONV) {
-        st = job_finish(r->job, stream);
+        st = job_finish(r->cur(), stream);
         if (st == LQCD_OK || st == LQCD_ENOCONV) {
             r->x.resize((size_t)r->shifts.size() * c->Vh * 6);
             const int st2 = soa_to_host(c, r->xd.as<double2>(), r->x.data(), (int)r->shifts.size(), stream);
@@ -113,11 +137,13 @@ void lqcd_server::retire(std::unique_ptr<Request> &r, int st)
         }
     }
     r->status = st;
-    r->info = r->job.I;
+    r->info = r->cur().I;
     r->t_done = std::chrono::steady_clock::now();
     r->info.secs = std::chrono::duration<double>(r->t_done - r->t_submit).count();
-    r->ws.vec.release(); r->ws.ieee.release(); r->ws.part.release(); r->ws.tickets.release();
-    r->ws.state.release(); r->ws.stage.release(); r->bd.release(); r->xd.release();
+    r->ws.release();
+    r->ws32.release();
+    r->bd.release();
+    r->xd.release();
     std::lock_guard<std::mutex> lk(mu);
     in_use -= r->bytes;
     latencies.push_back(r->info.secs);
@@ -145,8 +171,11 @@ bool lqcd_server::admit()
         const size_t n3 = 3 * c->Vh;
         int st = r->bd.ensure(n3 * sizeof(double2));
         if (!st) st = r->xd.ensure(r->shifts.size() * n3 * sizeof(double2));
-        if (!st) st = job_init(r->job, c, &r->ws, r->mass, r->shifts.data(), (int)r->shifts.size(), r->tol,
-                               r->bd.as<double2>(), r->xd.as<double2>());
+        // a mixed request starts in double-float unless fp64_until is 0
+        const int prec0 = r->mixed && r->fp64_until == 0.0 ? LQCD_PREC_FP32 : LQCD_PREC_FP64;
+        if (!st) st = job_init_prec(r->job, c, &r->ws, prec0, r->mass, r->shifts.data(), (int)r->shifts.size(),
+                                    r->tol, r->bd.as<double2>(), r->xd.as<double2>());
+        if (r->mixed && prec0 == LQCD_PREC_FP64) r->job.switch_rel = r->fp64_until;
         if (!st) st = host_to_soa(c, r->b.data(), r->bd.as<double2>(), 1, stream);
         if (!st) st = job_setup(r->job, stream);
         if (st) {
@@ -174,50 +203,85 @@ int lqcd_server::tick()
         }
     }
     if (active.empty()) return LQCD_OK;
-    // group by engine: FP64 df64 requests are packed together
-    IterBatch<kMaxJobs> B;
-    memset(&B, 0, sizeof B);
-    int tiles = 0;
-    for (size_t i = 0; i < active.size() && (int)i < kMaxJobs; ++i) {
-        B.tile_start[i] = tiles;
-        job_fill(active[i]->job, B.job[i]);
-        tiles += active[i]->job.P.ntiles;
-        B.max_shift = std::max(B.max_shift, active[i]->job.n_shift);
+    // one packed batch per engine: double-float (links df64) and FP32
+    // (the server's link format); a batch holds at most kMaxJobs requests
+    IterBatch<kMaxJobs> B[2];
+    std::vector<int> idx[2];
+    int lf[2] = {0, 0};
+    for (int g = 0; g < 2; ++g) {
+        memset(&B[g], 0, sizeof B[g]);
+        int tiles = 0;
+        for (size_t i = 0; i < active.size(); ++i) {
+            JobRun &J = active[i]->cur();
+            if (J.vp != g || B[g].njobs == kMaxJobs) continue;
+            const int k = B[g].njobs++;
+            B[g].tile_start[k] = tiles;
+            job_fill(J, B[g].job[k]);
+            tiles += J.P.ntiles;
+            B[g].max_shift = std::max(B[g].max_shift, J.n_shift);
+            lf[g] = J.lf;
+            idx[g].push_back((int)i);
+        }
+        B[g].tile_start[B[g].njobs] = tiles;
     }
-    B.njobs = (int)std::min<size_t>(active.size(), kMaxJobs);
-    B.tile_start[B.njobs] = tiles;
-    uint64_t key = 1469598103934665603ull;
-    {
-        const unsigned char *p = (const unsigned char *)&B;
-        for (size_t k = 0; k < sizeof B; ++k) key = (key ^ p[k]) * 1099511628211ull;
+    cudaError_t e = cudaSuccess;
+    for (int g = 0; g < 2 && e == cudaSuccess; ++g) {
+        if (!B[g].njobs) continue;
+        uint64_t key = 1469598103934665603ull;
+        const unsigned char *p = (const unsigned char *)&B[g];
+        for (size_t k = 0; k < sizeof B[g]; ++k) key = (key ^ p[k]) * 1099511628211ull;
+        key = (key ^ (uint64_t)lf[g]) * 1099511628211ull;
+        if (key != batch_key[g] || !exec[g]) {
+            if (exec[g]) cudaGraphExecDestroy(exec[g]);
+            exec[g] = nullptr;
+            cudaGraph_t gr;
+            e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(e, "serve capture");
+            for (int k = 0; k < chunk; ++k) launch_iteration_packed(B[g], g, lf[g], stream);
+            e = cudaStreamEndCapture(stream, &gr);
+            if (e != cudaSuccess) return cuda_fail(e, "serve capture");
+            e = cudaGraphInstantiate(&exec[g], gr, 0);
+            cudaGraphDestroy(gr);
+            if (e != cudaSuccess) return cuda_fail(e, "serve instantiate");
+            batch_key[g] = key;
+        }
+        e = cudaGraphLaunch(exec[g], stream);
     }
-    if (key != batch_key || !exec) {
-        if (exec) cudaGraphExecDestroy(exec);
-        exec = nullptr;
-        cudaGraph_t g;
-        cudaError_t e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
-        if (e != cudaSuccess) return cuda_fail(e, "serve capture");
-        for (int k = 0; k < chunk; ++k) launch_iteration_packed(B, VP_DF, 0 /* df64 links */, stream);
-        e = cudaStreamEndCapture(stream, &g);
-        if (e != cudaSuccess) return cuda_fail(e, "serve capture");
-        e = cudaGraphInstantiate(&exec, g, 0);
-        cudaGraphDestroy(g);
-        if (e != cudaSuccess) return cuda_fail(e, "serve instantiate");
-        batch_key = key;
-    }
-    cudaError_t e = cudaGraphLaunch(exec, stream);
-    std::vector<int> halts(B.njobs, 0);
-    for (int j = 0; j < B.njobs && e == cudaSuccess; ++j)
-        e = cudaMemcpyAsync(&halts[j], &B.job[j].st->halt, sizeof(int), cudaMemcpyDeviceToHost, stream);
+    std::vector<int> halts(active.size(), HALT_NONE);
+    for (int g = 0; g < 2; ++g)
+        for (int k = 0; k < B[g].njobs && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(&halts[idx[g][k]], &B[g].job[k].st->halt, sizeof(int), cudaMemcpyDeviceToHost,
+                                stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
     if (e != cudaSuccess) return cuda_fail(e, "serve tick");
     {
         std::lock_guard<std::mutex> lk(mu);
         ++ticks;
     }
-    for (int j = B.njobs - 1; j >= 0; --j) {
-        if (halts[j] == HALT_NONE) continue;
-        retire(active[j], halts[j] == HALT_NAN ? LQCD_ENAN : LQCD_OK);
+    for (int j = (int)active.size() - 1; j >= 0; --j) {
+        Request &r = *active[j];
+        const int h = halts[j];
+        if (h == HALT_NONE) continue;
+        int st = LQCD_OK;
+        if (h == HALT_RELIABLE) {
+            lqcd_ctx *c = fields[r.field].ctx;
+            if (r.cur().vp == VP_DF) {
+                // double-float phase reached fp64_until: switch to FP32
+                st = job_init_prec(r.jobF, c, &r.ws32, LQCD_PREC_FP32, r.mass, r.shifts.data(),
+                                   (int)r.shifts.size(), r.tol, r.bd.as<double2>(), r.xd.as<double2>());
+                if (!st) {
+                    r.jobF.b2 = r.job.b2;
+                    st = job_switch_to_f32(r.job, r.jobF, stream);
+                }
+                if (!st) r.phase = 1;
+            } else {
+                st = job_reliable_update(r.cur(), stream);
+            }
+            if (!st) continue;
+        } else if (h == HALT_NAN) {
+            st = LQCD_ENAN;
+        }
+        retire(active[j], st);
         active.erase(active.begin() + j);
     }
     return LQCD_OK;
@@ -270,6 +334,7 @@ int lqcd_serve_create(size_t hbm_budget_bytes, int max_slots, int max_queue, lqc
     if (hbm_budget_bytes == 0) return fail(LQCD_EINVAL, "hbm budget must be > 0");
     lqcd_server *s = new (std::nothrow) lqcd_server();
     if (!s) return fail(LQCD_ENOMEM, "host allocation failed");
+    lqcd_default_opts(&s->opts);
     s->budget = hbm_budget_bytes;
     s->max_slots = max_slots;
     s->max_queue = max_queue;
@@ -289,7 +354,12 @@ int lqcd_serve_register_field(lqcd_server *s, const int dims[4], const double *l
 {
     if (!s || !dims || !links || !field_id) return fail(LQCD_EINVAL, "NULL argument");
     lqcd_ctx *c = nullptr;
-    int st = lqcd_create(dims, nullptr, &c);
+    lqcd_opts o;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        o = s->opts;
+    }
+    int st = lqcd_create(dims, &o, &c);
     if (st) return st;
     // the field's links count against the budget (all storage formats)
     const size_t need = (size_t)c->Vh * (72 * 16 + 72 * 16 + 72 * 8 + 24 * 16 + 8 * 24);
@@ -332,9 +402,11 @@ int lqcd_serve_submit(lqcd_server *s, int field_id, double mass, const double *s
     r->tol = tol;
     r->shifts.assign(shifts, shifts + n_shift);
     r->b.assign(b, b + c->Vh * 6);
-    r->bytes = request_bytes(c, n_shift);
     r->t_submit = std::chrono::steady_clock::now();
     std::lock_guard<std::mutex> lk(s->mu);
+    r->mixed = s->opts.prec == LQCD_PREC_FP32;
+    r->fp64_until = s->opts.fp64_until;
+    r->bytes = request_bytes(c, n_shift) + (r->mixed ? request_bytes_mixed(c, n_shift) : 0);
     if (r->bytes + s->fields[field_id].bytes > s->budget) {
         ++s->rejected;
         return fail(LQCD_ENOMEM, "request can never fit the HBM budget");
@@ -352,6 +424,20 @@ int lqcd_serve_submit(lqcd_server *s, int field_id, double mass, const double *s
     ++s->submitted;
     s->queue.push_back(std::move(r));
     s->cv.notify_all();
+    return LQCD_OK;
+}
+
+int lqcd_serve_set_opts(lqcd_server *s, const lqcd_opts *o)
+{
+    if (!s || !o) return fail(LQCD_EINVAL, "NULL argument");
+    int st = validate_opts(o);
+    if (st) return st;
+    if (o->prec != LQCD_PREC_FP64 && o->prec != LQCD_PREC_FP32)
+        return fail(LQCD_EINVAL, "the server runs FP64 or FP32 (mixed) requests");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->completed < s->submitted) return fail(LQCD_EBUSY, "requests in flight");
+    s->opts = *o;
+    for (Field &f : s->fields) f.ctx->opts = *o;
     return LQCD_OK;
 }
 
@@ -430,10 +516,13 @@ void lqcd_serve_destroy(lqcd_server *s)
     s->cv.notify_all();
     if (s->th.joinable()) s->th.join();
     for (auto &r : s->active) {
-        r->ws.vec.release(); r->ws.ieee.release(); r->ws.part.release(); r->ws.tickets.release();
-        r->ws.state.release(); r->bd.release(); r->xd.release();
+        r->ws.release();
+        r->ws32.release();
+        r->bd.release();
+        r->xd.release();
     }
-    if (s->exec) cudaGraphExecDestroy(s->exec);
+    for (cudaGraphExec_t g : s->exec)
+        if (g) cudaGraphExecDestroy(g);
     for (auto &f : s->fields) lqcd_destroy(f.ctx);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;

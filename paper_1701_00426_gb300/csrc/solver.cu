@@ -1011,8 +1011,8 @@ int job_finish(JobRun &J, cudaStream_t s)
     return status;
 }
 
-static int job_init_prec(JobRun &J, lqcd_ctx *c, Workspace *W, int prec, double mass, const double *shifts,
-                         int n_shift, double tol, const double2 *b, double2 *x)
+int job_init_prec(JobRun &J, lqcd_ctx *c, Workspace *W, int prec, double mass, const double *shifts, int n_shift,
+                  double tol, const double2 *b, double2 *x)
 {
     int st = validate_solve(c, mass, shifts, n_shift, tol);
     if (st) return st;
@@ -1039,7 +1039,7 @@ int job_init(JobRun &J, lqcd_ctx *c, Workspace *W, double mass, const double *sh
 // go to the IEEE accumulators, the base residual is recomputed against the
 // FP64 operator, the directions are rounded to FP32 at the new scale, and the
 // recurrence scalars carry over unchanged (the same Krylov iteration goes on).
-static int job_switch_to_f32(JobRun &D, JobRun &F, cudaStream_t s)
+int job_switch_to_f32(JobRun &D, JobRun &F, cudaStream_t s)
 {
     lqcd_ctx *c = D.c;
     const long n3 = 3 * (long)c->Vh;

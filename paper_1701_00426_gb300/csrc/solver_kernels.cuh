@@ -157,27 +157,35 @@ __device__ inline void finalize_pq(SolverState *st, double pq)
     }
 }
 
-// finalize_pq spread over a block: thread 0 rotates the recurrences and
-// computes alpha, then one thread per active shift computes zeta_i, alpha_i.
-// Called by every thread of the block.
-__device__ inline void finalize_pq_block(SolverState *st, double pq)
+// finalize_pq on one warp, lane s = shift s (kMaxShifts == 32): every lane
+// loads its shift's scalars at once, the active list is compacted with a
+// ballot, and the recurrences of all shifts are updated in parallel.  Called
+// by warp 0 of the last block.
+static_assert(kMaxShifts == 32, "one lane per shift");
+__device__ inline void finalize_pq_warp(SolverState *st, double pq)
 {
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        st->last_sum = pq;
-        st->alpha_prev = st->alpha;
-        st->beta_prev = st->beta;
-        int n_act = 0;
-        for (int s = 0; s < st->n_shift; ++s) {
-            if (!st->active_next[s]) continue;
-            st->zeta_prev[s] = st->zeta[s];
-            st->zeta[s] = st->zeta_new[s];
-            st->act_list[n_act++] = s;
+    const int lane = threadIdx.x & 31;
+    const int ns = st->n_shift;
+    const double rho = st->rho, alpha_old = st->alpha, beta_old = st->beta;
+    int act = 0;
+    double zo = 0.0, zc = 0.0, srel = 0.0;
+    if (lane < ns) {
+        act = st->active_next[lane];
+        if (act) {
+            zo = st->zeta[lane];
+            zc = st->zeta_new[lane];
+            srel = st->shift_rel[lane];
         }
-        st->n_act = n_act;
-        const double alpha = st->rho / pq;
-        s_ok = (pq > 0.0) && isfinite(alpha);
-        if (s_ok) {
+    }
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, act);
+    const double alpha = rho / pq;
+    const bool ok = (pq > 0.0) && isfinite(alpha);
+    if (lane == 0) {
+        st->last_sum = pq;
+        st->alpha_prev = alpha_old;
+        st->beta_prev = beta_old;
+        st->n_act = __popc(m);
+        if (ok) {
             st->alpha = alpha;
             st->alpha_df = split_scalar(alpha);
         } else {
@@ -185,63 +193,65 @@ __device__ inline void finalize_pq_block(SolverState *st, double pq)
             st->nan_flag = 1;
         }
     }
-    __syncthreads();
-    if (!s_ok) return;
-    const double alpha = st->alpha;
-    for (int k = threadIdx.x; k < st->n_act; k += blockDim.x) {
-        const int s = st->act_list[k];
-        const double z = st->zeta[s], zp = st->zeta_prev[s];
-        const double den = alpha * st->beta_prev * (zp - z) + zp * st->alpha_prev * (1.0 + st->shift_rel[s] * alpha);
-        const double zn = z * zp * st->alpha_prev / den;
-        st->zeta_new[s] = zn;
-        st->zeta_new_df[s] = split_scalar(zn);
-        st->alpha_s_df[s] = split_scalar(alpha * zn / z);
-    }
+    if (!act) return;
+    // rotate: zeta_prev <- zeta, zeta <- zeta_new
+    st->zeta_prev[lane] = zo;
+    st->zeta[lane] = zc;
+    st->act_list[__popc(m & ((1u << lane) - 1u))] = lane;
+    if (!ok) return;
+    const double den = alpha * beta_old * (zo - zc) + zo * alpha_old * (1.0 + srel * alpha);
+    const double zn = zc * zo * alpha_old / den;
+    st->zeta_new[lane] = zn;
+    st->zeta_new_df[lane] = split_scalar(zn);
+    st->alpha_s_df[lane] = split_scalar(alpha * zn / zc);
 }
 
-// finalize_rr spread over a block (one thread per active shift for beta_i
-// and the convergence tests).  Called by every thread of the block.
-__device__ inline void finalize_rr_block(SolverState *st, double rr)
+// finalize_rr on one warp: lane k handles the k-th active shift (beta_i and
+// the convergence test); lane 0 the base scalars and the halt decision.
+// Called by warp 0 of the last block.
+__device__ inline void finalize_rr_warp(SolverState *st, double rr)
 {
-    __shared__ int s_ok;
-    if (threadIdx.x == 0) {
-        st->last_sum = rr;
-        s_ok = isfinite(rr);
-        if (s_ok) {
-            st->beta = rr / st->rho;
-            st->rho = rr;
-            st->iters += 1;
-        } else {
-            st->halt = HALT_NAN;
-            st->nan_flag = 1;
-        }
-    }
-    __syncthreads();
-    if (!s_ok) return;
-    const double beta = st->beta;
+    const int lane = threadIdx.x & 31;
+    const bool ok = isfinite(rr);
+    const double beta = rr / st->rho;
+    const int iters = st->iters + 1;
+    const int n_act = st->n_act;
+    const double tol2_b2 = st->tol2_b2;
+    // loaded up front so that lane 0's decisions wait on no further round trip
+    const int base = st->base, max_iter = st->max_iter;
+    const double rel_stop2 = st->rel_stop2;
     int open = 0;
-    for (int k = threadIdx.x; k < st->n_act; k += blockDim.x) {
-        const int s = st->act_list[k];
-        const double ratio = st->zeta_new[s] / st->zeta[s];
+    if (ok && lane < n_act) {
+        const int s = st->act_list[lane];
+        const double zc = st->zeta[s], zn = st->zeta_new[s];
+        const double ratio = zn / zc;
         st->beta_s_df[s] = split_scalar(beta * ratio * ratio);
-        const double zn = st->zeta_new[s];
-        const bool conv = zn * zn * rr <= st->tol2_b2;
-        if (conv && st->shift_iters[s] == 0) st->shift_iters[s] = st->iters;
+        const bool conv = zn * zn * rr <= tol2_b2;
+        if (conv && st->shift_iters[s] == 0) st->shift_iters[s] = iters;
         st->active_next[s] = conv ? 0 : 1;
-        open |= !conv;
+        open = !conv;
     }
-    const int any = __syncthreads_or(open);
-    if (threadIdx.x == 0) {
-        // the base direction must keep moving while any shift still iterates
-        if (any) st->active_next[st->base] = 1;
-        st->do_k4 = 1;
-        if (!any)
-            st->halt = HALT_CONVERGED;
-        else if (st->rel_stop2 > 0.0 && rr < st->rel_stop2)
-            st->halt = HALT_RELIABLE;
-        else if (st->iters >= st->max_iter)
-            st->halt = HALT_MAXITER;
+    const int any = __any_sync(0xFFFFFFFFu, open);
+    __syncwarp();
+    if (lane != 0) return;
+    st->last_sum = rr;
+    if (!ok) {
+        st->halt = HALT_NAN;
+        st->nan_flag = 1;
+        return;
     }
+    st->beta = beta;
+    st->rho = rr;
+    st->iters = iters;
+    // the base direction must keep moving while any shift still iterates
+    if (any) st->active_next[base] = 1;
+    st->do_k4 = 1;
+    if (!any)
+        st->halt = HALT_CONVERGED;
+    else if (rel_stop2 > 0.0 && rr < rel_stop2)
+        st->halt = HALT_RELIABLE;
+    else if (iters >= max_iter)
+        st->halt = HALT_MAXITER;
 }
 
 // beta, beta_i and the stopping decisions (FP64, one thread).
@@ -398,7 +408,9 @@ __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo2(const 
         }
     }
     const double v = block_reduce_acc_n<kIterThreads>(dot, s_red);
-    tile_finish_block(J, tile, v, [&](double tot) { finalize_pq_block(st, tot); });
+    tile_finish_block(J, tile, v, [&](double tot) {
+        if (threadIdx.x < 32) finalize_pq_warp(st, tot);
+    });
 }
 
 // ------------------------------------------------------------------ K3
@@ -444,7 +456,9 @@ __global__ void __launch_bounds__(kIterThreads) k_it_upd_r(const __grid_constant
         }
     }
     const double v = block_reduce_acc_n<kIterThreads>(nrm, s_red);
-    tile_finish_block(J, tile, v, [&](double tot) { finalize_rr_block(st, tot); });
+    tile_finish_block(J, tile, v, [&](double tot) {
+        if (threadIdx.x < 32) finalize_rr_warp(st, tot);
+    });
 }
 
 // ------------------------------------------------------------------ K4

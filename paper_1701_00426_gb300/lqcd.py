@@ -46,7 +46,7 @@ EXPORTED = [
     "lqcd_deo_apply", "lqcd_deo_apply_host_noalloc", "lqcd_deo_apply_ex", "lqcd_deo_apply_mrhs", "lqcd_mscg_solve",
     "lqcd_mscg_solve_dev", "lqcd_cg_solve_mrhs", "lqcd_mscg_solve_packed", "lqcd_profile_iteration",
     "lqcd_serve_create", "lqcd_serve_register_field", "lqcd_serve_submit", "lqcd_serve_poll",
-    "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy",
+    "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy", "lqcd_serve_set_opts",
 ]
 
 
@@ -134,6 +134,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_serve_drain": (ctypes.c_int, [vp, ctypes.c_double]),
         "lqcd_serve_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(lqcd_serve_stats)]),
         "lqcd_serve_destroy": (None, [vp]),
+        "lqcd_serve_set_opts": (ctypes.c_int, [vp, ctypes.POINTER(lqcd_opts)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -361,6 +362,11 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+    def set_opts(self, **kw):
+        """Options of later requests (prec 0 = FP64, 1 = FP32 mixed; recon, fp64_until, ...)."""
+        o = default_opts(**kw)
+        check(self.lib.lqcd_serve_set_opts(self.h, ctypes.byref(o)))
 
     def register_field(self, dims, links: np.ndarray) -> int:
         dims = tuple(int(d) for d in dims)

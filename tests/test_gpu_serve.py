@@ -81,6 +81,58 @@ def test_served_request_alone_equals_in_mix(gpu, orc):
     assert st["hbm_in_use"] <= st["hbm_budget"]
 
 
+@pytest.mark.parametrize("fp64_until", [3e-4, 0.0])
+def test_served_mixed_request_alone_equals_in_mix_and_solo(gpu, orc, fp64_until):
+    """Mixed-precision serving (FP32 12-real links, FP64 phase down to
+    fp64_until, reliable updates, refinement): a request gives the same
+    solution alone, in a mix of FP32 requests, and as a solo mixed solve."""
+    with gpu.Server(8 << 30, max_slots=8, max_queue=64) as srv:
+        srv.set_opts(prec=gpu.PREC_FP32, recon=12, fp64_until=fp64_until)
+        fids = [srv.register_field(d, inputs.random_links(d, seed=300 + k)) for k, d in enumerate(SIZES)]
+        target = (fids[0], 0.01, inputs.log_shifts(8), 1e-10, inputs.gaussian_field(SIZES[0], k=9))
+        x_alone, info_alone = _wait(srv, srv.submit(*target), fids[0], 8)
+        others = []
+        rng = np.random.default_rng(5)
+        for k in range(6):
+            f = int(rng.integers(0, len(fids)))
+            n = int(rng.integers(1, 9))
+            others.append((srv.submit(fids[f], 0.02, inputs.log_shifts(n, 1e-4, 1.0), 1e-9,
+                                      inputs.gaussian_field(SIZES[f], k=40 + k)), f, n))
+            if k == 2:
+                t2 = srv.submit(*target)
+        x_mix, info_mix = _wait(srv, t2, fids[0], 8)
+        for tk, f, n in others:
+            x, info = _wait(srv, tk, fids[f], n)
+            assert max(info["true_resid"]) <= 1e-9
+        srv.drain(60)
+        with pytest.raises(gpu.LqcdError) as e:  # FP16 requests are not served
+            srv.set_opts(prec=gpu.PREC_FP16)
+        assert e.value.status == gpu.LQCD_EINVAL
+    assert np.array_equal(x_alone, x_mix)
+    assert info_alone["reliable_updates"] == info_mix["reliable_updates"] > 0
+    U = inputs.random_links(SIZES[0], seed=300)
+    with gpu.Context(SIZES[0], prec=gpu.PREC_FP32, recon=12, fp64_until=fp64_until) as c:
+        c.links_upload(U)
+        x_solo, _ = c.mscg_solve(0.01, inputs.log_shifts(8), 1e-10, target[4])
+    assert np.array_equal(x_alone, x_solo)
+    for i, s in enumerate(inputs.log_shifts(8)):
+        assert orc.true_residual(SIZES[0], U, 0.01, s, target[4], x_mix[i]) <= 1e-10
+
+
+def test_set_opts_busy_while_requests_run(gpu):
+    d = (8, 8, 8, 8)
+    with gpu.Server(1 << 30, max_slots=2, max_queue=16) as srv:
+        fid = srv.register_field(d, inputs.random_links(d))
+        ts = [srv.submit(fid, 0.01, inputs.log_shifts(8), 1e-10, inputs.gaussian_field(d, k=k)) for k in range(4)]
+        with pytest.raises(gpu.LqcdError) as e:
+            srv.set_opts(prec=gpu.PREC_FP32)
+        assert e.value.status == gpu.LQCD_EBUSY
+        for t in ts:
+            _wait(srv, t, fid, 8)
+        srv.drain(60)
+        srv.set_opts(prec=gpu.PREC_FP32)
+
+
 def test_admission_respects_budget(gpu):
     d = (8, 8, 8, 8)
     with gpu.Server(64 << 20, max_slots=8, max_queue=64) as srv:
