@@ -91,6 +91,16 @@ typedef struct lqcd_opts {
                               the residual at the switch, so a later switch
                               leaves less for the per-shift refinement.
                               Ignored by FP64 and FP16 solves. */
+    int staged;            /* FP64 (double-float) D_eo kernels of the solver
+                              and of lqcd_deo_apply: 1 = links streamed into
+                              shared memory by bulk asynchronous copies
+                              (default; needs a second, tile-ordered copy of
+                              the FP64 links, 2 x 1152 B per even site),
+                              0 = per-thread loads from the structure-of-
+                              arrays links only.  Both give bitwise
+                              identical results.  Takes effect at the next
+                              lqcd_links_upload (the staged copy is built
+                              there) and at the next solve. */
 } lqcd_opts;
 
 #define LQCD_MAX_SHIFTS 32

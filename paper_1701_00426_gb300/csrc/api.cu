@@ -52,8 +52,8 @@ void DevBuf::release()
 
 size_t ctx_device_bytes(const lqcd_ctx *c)
 {
-    const DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->io_a, &c->io_b,
-                         &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
+    const DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->lnk_dfs,
+                         &c->err_word, &c->io_a, &c->io_b, &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
     size_t s = 0;
     for (const DevBuf *p : b) s += p->bytes;
     s += c->ws32.bytes();
@@ -69,6 +69,7 @@ int validate_opts(const lqcd_opts *o)
     if (o->max_iter < 1) return fail(LQCD_EINVAL, "opts.max_iter must be >= 1");
     if (o->check_every < 1 || o->check_every > 4096) return fail(LQCD_EINVAL, "opts.check_every must be in 1..4096");
     if (!(o->fp64_until >= 0.0 && o->fp64_until < 1.0)) return fail(LQCD_EINVAL, "opts.fp64_until must be in [0,1)");
+    if (o->staged != 0 && o->staged != 1) return fail(LQCD_EINVAL, "opts.staged must be 0 or 1");
     return LQCD_OK;
 }
 
@@ -87,6 +88,7 @@ void lqcd_default_opts(lqcd_opts *o)
     o->max_iter = 20000;
     o->check_every = 32;
     o->fp64_until = 3e-4;
+    o->staged = 1;
 }
 
 const char *lqcd_last_error(void) { return g_err.c_str(); }
@@ -133,8 +135,8 @@ void lqcd_destroy(lqcd_ctx *c)
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     c->graph.reset();
-    DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->io_a, &c->io_b,
-                   &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
+    DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->lnk_dfs, &c->err_word,
+                   &c->io_a, &c->io_b, &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
     for (DevBuf *p : b) p->release();
     c->ws32.release();
     for (Workspace &w : c->ref_ws) w.release();
@@ -188,7 +190,7 @@ int lqcd_deo_apply(lqcd_ctx *c, int out_parity, const void *in, void *out, int w
     dout.release();
     if (st) return st;
     if (e != cudaSuccess) return cuda_fail(e, "lqcd_deo_apply");
-    return LQCD_OK;
+    return deo_check_stall(c);
 }
 
 int lqcd_deo_apply_ex(lqcd_ctx *c, int out_parity, int prec, int recon, const void *in, void *out, void *stream)

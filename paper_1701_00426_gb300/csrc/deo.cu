@@ -1,5 +1,6 @@
 // deo.cu -- link upload / storage conversion, host <-> device spinor
 // layouts, and the stand-alone D_eo / D_oe launches of the C ABI.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -10,6 +11,7 @@
 
 #include "deo_core.cuh"
 #include "internal.h"
+#include "stencil_staged.cuh"
 
 namespace lqcd {
 
@@ -72,6 +74,40 @@ __global__ void k_links_to_canonical(Geom g, const double2 *__restrict__ nat, do
     for (int c = 0; c < 9; ++c) dst[t * 9 + c] = nat[link_base(mu, par, 9, g.Vh) + (size_t)c * g.Vh + idx];
 }
 
+// Tile-ordered FP64 link stream of the staged kernels (stencil_staged.cuh),
+// gathered from the SoA df64 links: element (P, tile, h, c, s) is component
+// c of the forward (h even) or backward (h odd) link of direction h/2 seen
+// from output site tile*256 + s of parity P; zero beyond V/2.
+__global__ void k_build_staged_df(Geom g, const float4 *__restrict__ L, float4 *__restrict__ st, int ntiles)
+{
+    const size_t n = staged_df_elems(ntiles);
+    const size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int s = (int)(t % kTile);
+    size_t r = t / kTile;
+    const int c = (int)(r % kDFComps);
+    r /= kDFComps;
+    const int h = (int)(r % 8);
+    r /= 8;
+    const int tile = (int)(r % (size_t)ntiles);
+    const int P = (int)(r / (size_t)ntiles);
+    const int i = tile * kTile + s;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < g.Vh) {
+        Stencil S;
+        make_stencil(g, i, P, S);
+        int f, b;
+        uint32_t nf, nb;
+        const int mu = h >> 1;
+        hop(g, S, mu, f, b, nf, nb);
+        if ((h & 1) == 0)
+            v = L[link_base(mu, P, 9, g.Vh) + (size_t)c * g.Vh + i];
+        else
+            v = L[link_base(mu, 1 - P, 9, g.Vh) + (size_t)c * g.Vh + b];
+    }
+    st[t] = v;
+}
+
 int upload_links(lqcd_ctx *c, const double *host, size_t n)
 {
     const size_t want = 4 * c->V * 18;
@@ -84,6 +120,14 @@ int upload_links(lqcd_ctx *c, const double *host, size_t n)
     if ((st = c->lnk_f18.ensure(72 * Vh * sizeof(float2)))) return st;
     if ((st = c->lnk_f12.ensure(24 * Vh * sizeof(float4)))) return st;
     if ((st = c->lnk_h12.ensure(8 * Vh * (sizeof(uint4) + sizeof(uint2))))) return st;
+    const int ntiles = (int)((Vh + kTile - 1) / kTile);
+    const bool staged = c->opts.staged && staged_deo_ready() && staged_solver_ready();
+    if (staged) {
+        if ((st = c->lnk_dfs.ensure(staged_df_elems(ntiles) * sizeof(float4)))) return st;
+        if ((st = c->err_word.ensure(4 * sizeof(int)))) return st;
+    } else {
+        c->lnk_dfs.release();
+    }
     DevBuf stage;
     if ((st = stage.ensure(want * sizeof(double) + 16))) return st;
     int *bad = (int *)((char *)stage.ptr + want * sizeof(double));
@@ -97,6 +141,13 @@ int upload_links(lqcd_ctx *c, const double *host, size_t n)
                                                             c->lnk_df.as<float4>(), c->lnk_f18.as<float2>(),
                                                             c->lnk_f12.as<float2>(), c->lnk_h12.as<uint32_t>(), bad, V);
         e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && staged) {
+        const size_t ne = staged_df_elems(ntiles);
+        k_build_staged_df<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(c->g, c->lnk_df.as<float4>(),
+                                                                          c->lnk_dfs.as<float4>(), ntiles);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemsetAsync(c->err_word.ptr, 0, 4 * sizeof(int), c->stream);
     }
     int hbad = 0;
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
@@ -287,6 +338,109 @@ __global__ void __launch_bounds__(kTile)
     for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
 }
 
+// Stand-alone D_eo, consumers.
+__device__ __forceinline__ void deo_staged_consume(const Geom &g, RingDF &R, const float4 *__restrict__ L,
+                                                   const double2 *__restrict__ in, double2 *__restrict__ out, int P,
+                                                   int ntiles, int *err)
+{
+    const int Vh = g.Vh;
+    uint32_t q = 0;
+    bool dead = false;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int i = tile * kTile + threadIdx.x;
+        const bool live = i < Vh;
+        Stencil S;
+        make_stencil(g, live ? i : 0, P, S);
+        float2 res[6];
+        bool bad = false;
+        deo_site_df_staged<SF_IEEE>(R, q, dead, g, in, S, Vh, res, bad);
+        if (!live) continue;
+        double2 o[3];
+        if (bad) {
+            deo_site_native_from_df(g, L, in, S, i, P, Vh, o);
+        } else {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) o[cc] = make_double2(df_to_f64(res[2 * cc]), df_to_f64(res[2 * cc + 1]));
+        }
+#pragma unroll
+        for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * Vh + i] = o[cc];
+    }
+    if (dead) atomicOr(err, 1);
+}
+
+// Stand-alone FP64 D_eo with the link stream staged through shared memory
+// (stencil_staged.cuh): IEEE complex128 spinors in and out, double-float
+// arithmetic, the native FP64 fallback for inputs outside the df64 window.
+// Persistent: gridDim.x <= resident blocks; err bit 0/1 records a stall.
+__global__ void __launch_bounds__(kStagedThreads, kStagedMinBlocks)
+    k_deo_df_ieee_staged(Geom g, const float4 *__restrict__ Lst, const float4 *__restrict__ L,
+                         const double2 *__restrict__ in, double2 *__restrict__ out, int P, int ntiles, int *err)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    RingDF &R = *reinterpret_cast<RingDF *>(smem_raw);
+    ring_init(R);
+    if (threadIdx.x >= kStagedConsumers) {
+        if (threadIdx.x == kStagedConsumers) {
+            int tile = blockIdx.x;
+            const bool ok = ring_produce(R, [&](const float4 *&base) -> bool {
+                if (tile >= ntiles) return false;
+                base = staged_tile_base(Lst, P, ntiles, tile);
+                tile += gridDim.x;
+                return true;
+            });
+            if (!ok) atomicOr(err, 2);
+        }
+    } else {
+        deo_staged_consume(g, R, L, in, out, P, ntiles, err);
+    }
+    ring_finish(R);
+}
+
+
+// Residency of the staged stand-alone kernel per device (0: cannot run).
+static std::mutex g_staged_mu;
+static int g_staged_blocks[64];
+static bool g_staged_done[64];
+
+bool staged_deo_ready()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(g_staged_mu);
+    if (!g_staged_done[dev]) {
+        g_staged_done[dev] = true;
+        int occ = 0, nsm = 0;
+        if (cudaFuncSetAttribute(k_deo_df_ieee_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRingDFBytes) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deo_df_ieee_staged, kStagedThreads,
+                                                          kRingDFBytes) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
+            g_staged_blocks[dev] = occ * nsm;
+        cudaGetLastError();  // a refusal above only disables the staged path
+    }
+    return g_staged_blocks[dev] > 0;
+}
+
+static int staged_deo_blocks(int dev)
+{
+    std::lock_guard<std::mutex> lk(g_staged_mu);
+    return dev >= 0 && dev < 64 ? g_staged_blocks[dev] : 0;
+}
+
+bool staged_active(const lqcd_ctx *c) { return c->opts.staged && c->lnk_dfs.ptr != nullptr; }
+
+int deo_check_stall(lqcd_ctx *c)
+{
+    if (!c->err_word.ptr) return LQCD_OK;
+    int w = 0;
+    LQCD_CUDA(cudaMemcpyAsync(&w, c->err_word.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LQCD_CUDA(cudaStreamSynchronize(c->stream));
+    if (!w) return LQCD_OK;
+    LQCD_CUDA(cudaMemsetAsync(c->err_word.ptr, 0, sizeof(int), c->stream));
+    LQCD_CUDA(cudaStreamSynchronize(c->stream));
+    return fail(LQCD_ETIMEOUT, "a staged D_eo wait for shared-memory link data ran out");
+}
+
 // ------------------------------------------------------------------ autotuner
 // Threads per block of the stand-alone D_eo kernels, chosen per (variant,
 // lattice) by timing 64, 128 and 256 on the first call (CUDA events on the
@@ -405,11 +559,20 @@ int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *ou
     switch (prec) {
     case LQCD_PREC_FP64: {
         if (recon != 18) return fail(LQCD_EINVAL, "FP64 D_eo uses 18-real links");
-        static const int cand[7] = {64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256};
+        static const int cand[8] = {64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256,
+                                    3072 + kStagedThreads};
         const float4 *L = c->lnk_df.as<float4>();
+        const bool staged = staged_active(c);
+        const int ntiles = (int)((c->Vh + kTile - 1) / kTile);
+        const int sgrid = std::min(ntiles, staged_deo_blocks(c->device));
         st = tuned_launch(c, 0, s, [&](int code) {
-            const int kind = code >> 10, bs = code & 1023;
-            if (kind == 0)
+            int kind = code >> 10, bs = code & 1023;
+            if (kind == 3 && (!staged || sgrid < 1)) kind = 0, bs = kTile;  // staged stream not built
+            if (kind == 3)
+                k_deo_df_ieee_staged<<<(unsigned)sgrid, kStagedThreads, kRingDFBytes, s>>>(
+                    g, c->lnk_dfs.as<float4>(), L, (const double2 *)in, (double2 *)out, P, ntiles,
+                    c->err_word.as<int>());
+            else if (kind == 0)
                 k_deo_df_ieee<<<nb(bs), bs, 0, s>>>(g, L, (const double2 *)in, (double2 *)out, P);
             else if (kind == 1)
                 k_deo_df_ieee_split<2><<<(unsigned)((2 * c->Vh + bs - 1) / bs), bs, 0, s>>>(
@@ -417,7 +580,7 @@ int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *ou
             else
                 k_deo_df_ieee_split<4><<<(unsigned)((4 * c->Vh + bs - 1) / bs), bs, 0, s>>>(
                     g, L, (const double2 *)in, (double2 *)out, P);
-        }, 7, cand);
+        }, staged ? 8 : 7, cand);
         break;
     }
     case LQCD_PREC_FP64_NATIVE:

@@ -54,12 +54,13 @@ struct SolverState {
     int act_list[kMaxShifts];
     int shift_iters[kMaxShifts];
     double last_sum;                  // last reduction result (diagnostics)
+    int stall;                        // a staged stencil wait ran out (turned into HALT_STALL)
     // split copies for the vector kernels: df64 (hi, lo) and FP32 (hi only)
     float2 a0_df, alpha_df;
     float2 alpha_s_df[kMaxShifts], zeta_new_df[kMaxShifts], beta_s_df[kMaxShifts];
 };
 
-enum Halt { HALT_NONE = 0, HALT_CONVERGED = 1, HALT_RELIABLE = 2, HALT_MAXITER = 3, HALT_NAN = 4 };
+enum Halt { HALT_NONE = 0, HALT_CONVERGED = 1, HALT_RELIABLE = 2, HALT_MAXITER = 3, HALT_NAN = 4, HALT_STALL = 5 };
 
 // Krylov vector precision of an engine
 enum VecPrec { VP_DF = 0, VP_F32 = 1 };
@@ -68,6 +69,7 @@ enum VecPrec { VP_DF = 0, VP_F32 = 1 };
 struct IterJob {
     Geom g;
     const void *links;   // link storage for the engine's deo variant
+    const float4 *links_st;  // tile-ordered FP64 link stream of the staged kernels (NULL: per-thread loads)
     void *r, *q, *t;     // residual, A p, odd temporary
     void *x, *ps;        // n_shift solutions / directions, shift-major [n][3][Vh]
     SolverState *st;
@@ -144,6 +146,9 @@ struct lqcd_ctx {
     lqcd::DevBuf lnk_f18;   // FP32, 18 reals:       [4][2][9][Vh] float2
     lqcd::DevBuf lnk_f12;   // FP32, 12 reals:       [4][2][3][Vh] float4
     lqcd::DevBuf lnk_h12;   // FP16, 12 reals:       [8][Vh] uint4 + [8][Vh] uint2
+    lqcd::DevBuf lnk_dfs;   // df64 pairs, tile-ordered stream of the staged kernels:
+                            //   [2 parities][ntiles][8 hops][9][256] float4 (stencil_staged.cuh)
+    lqcd::DevBuf err_word;  // device status word of the stand-alone staged D_eo (bit set = stall)
     lqcd::DevBuf io_a, io_b;  // device staging of host spinors for where = 0
     lqcd::Workspace ws;
     lqcd::Workspace ws32;                  // FP32 phase of a hybrid mixed-precision solve
@@ -165,6 +170,14 @@ __global__ void k_deo_df_ieee(Geom g, const float4 *__restrict__ L, const double
                               double2 *__restrict__ out, int P);
 int deo_launch(lqcd_ctx *c, int out_parity, int prec, int recon, const void *in, void *out, cudaStream_t s);
 int upload_links(lqcd_ctx *c, const double *host, size_t n);
+// Staged kernels: shared-memory attribute and residency, once per device.
+// Returns true when they can run on the current device.
+bool staged_deo_ready();
+bool staged_solver_ready();
+bool staged_active(const lqcd_ctx *c);   // staged option on and the staged link stream built
+// LQCD_ETIMEOUT (and clears the word) if a stand-alone staged D_eo of this
+// context recorded a stall; synchronises the context's stream.
+int deo_check_stall(lqcd_ctx *c);
 int download_links(lqcd_ctx *c, double *host, size_t n);
 int host_to_soa(lqcd_ctx *c, const double *host, double2 *dev_soa, int nfields, cudaStream_t s);
 int soa_to_host(lqcd_ctx *c, const double2 *dev_soa, double *host, int nfields, cudaStream_t s);

@@ -280,6 +280,8 @@ int lqcd_server::tick()
             if (!st) continue;
         } else if (h == HALT_NAN) {
             st = LQCD_ENAN;
+        } else if (h == HALT_STALL) {
+            st = LQCD_ETIMEOUT;
         }
         retire(active[j], st);
         active.erase(active.begin() + j);

@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "solver_kernels.cuh"
 
@@ -362,6 +363,61 @@ double unit_scale_pub(double n2, double n)
     return std::ldexp(1.0, -(int)std::lround(std::log2(rms)));
 }
 
+// ------------------------------------------------------------------ staged kernels
+// Shared-memory attribute and resident blocks of the staged K1 / K2, once per
+// device (called outside stream capture: at link upload).  0 blocks = the
+// staged path is unavailable and the per-thread kernels run.
+static std::mutex g_st_mu;
+static int g_st_blocks[64];
+static bool g_st_done[64];
+
+template <class K>
+static int staged_kernel_blocks(K kern, int nsm)
+{
+    int occ = 0;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kStagedIterSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kStagedThreads, kStagedIterSmem) != cudaSuccess)
+        occ = 0;
+    cudaGetLastError();
+    return occ * nsm;
+}
+
+bool staged_solver_ready()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    std::lock_guard<std::mutex> lk(g_st_mu);
+    if (!g_st_done[dev]) {
+        g_st_done[dev] = true;
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm = 0;
+        int b = staged_kernel_blocks(k_it_deo1_st<1>, nsm);
+        b = std::min(b, staged_kernel_blocks(k_it_deo2_st<1>, nsm));
+        b = std::min(b, staged_kernel_blocks(k_it_deo1_st<kMaxJobs>, nsm));
+        b = std::min(b, staged_kernel_blocks(k_it_deo2_st<kMaxJobs>, nsm));
+        g_st_blocks[dev] = b;
+    }
+    return g_st_blocks[dev] > 0;
+}
+
+static int staged_solver_blocks()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lk(g_st_mu);
+    return g_st_blocks[dev];
+}
+
+// All jobs of the batch carry the staged link stream.
+template <int NJ>
+static bool batch_staged(const IterBatch<NJ> &B)
+{
+    if (kSites != kTile) return false;  // the staged stream is laid out in 256-site tiles
+    for (int j = 0; j < B.njobs; ++j)
+        if (!B.job[j].links_st) return false;
+    return B.njobs > 0;
+}
+
 // ------------------------------------------------------------------ iteration chunks
 // Kernel k (0: K1 .. 3: K4) of one iteration.
 template <int NJ>
@@ -369,8 +425,11 @@ static void launch_kernel_k(const IterBatch<NJ> &B, int k, int ntot, int vp, int
 {
     const dim3 g4((unsigned)ntot, (unsigned)(B.max_shift > 0 ? B.max_shift : 1));
     if (vp == VP_DF) {
-        if (k == 0) k_it_deo1<NJ, VP_DF, LF_DF18><<<ntot, kIterThreads, 0, s>>>(B);
-        if (k == 1) k_it_deo2<NJ, VP_DF, LF_DF18><<<ntot, kIterThreads, 0, s>>>(B);
+        const int sb = (k < 2 && batch_staged(B)) ? std::min(ntot, staged_solver_blocks()) : 0;
+        if (k == 0 && sb > 0) k_it_deo1_st<NJ><<<sb, kStagedThreads, kStagedIterSmem, s>>>(B, ntot);
+        if (k == 1 && sb > 0) k_it_deo2_st<NJ><<<sb, kStagedThreads, kStagedIterSmem, s>>>(B, ntot);
+        if (k == 0 && sb == 0) k_it_deo1<NJ, VP_DF, LF_DF18><<<ntot, kIterThreads, 0, s>>>(B);
+        if (k == 1 && sb == 0) k_it_deo2<NJ, VP_DF, LF_DF18><<<ntot, kIterThreads, 0, s>>>(B);
         if (k == 2) k_it_upd_r<NJ, VP_DF><<<ntot, kIterThreads, 0, s>>>(B);
         if (k == 3) k_it_upd_shifts<NJ, VP_DF><<<g4, kIterThreads, 0, s>>>(B);
         return;
@@ -533,6 +592,8 @@ static void fill_job(lqcd_ctx *c, const WsPtrs &P, const void *links, IterJob &J
 {
     J.g = c->g;
     J.links = links;
+    // the staged stream holds the df64 links: only the FP64 engine uses it
+    J.links_st = (links == c->lnk_df.ptr && staged_active(c)) ? c->lnk_dfs.as<float4>() : nullptr;
     J.r = P.r;
     J.q = P.q;
     J.t = P.t;
@@ -960,6 +1021,7 @@ int job_finish(JobRun &J, cudaStream_t s)
     LQCD_CUDA(cudaMemcpyAsync(&O, J.P.st, sizeof O, cudaMemcpyDeviceToHost, s));
     LQCD_CUDA(cudaStreamSynchronize(s));
     if (O.halt == HALT_NAN) return fail(LQCD_ENAN, "NaN/Inf or breakdown in the multi-shift iteration");
+    if (O.halt == HALT_STALL) return fail(LQCD_ETIMEOUT, "a staged stencil wait for shared-memory link data ran out");
     J.I.iters = O.iters;
     for (int i = 0; i < J.n_shift; ++i) J.I.shift_iters[i] = O.shift_iters[i];
     J.bytes += phase_bytes(J, O);

@@ -18,6 +18,7 @@
 
 #include "deo_core.cuh"
 #include "internal.h"
+#include "stencil_staged.cuh"
 
 namespace lqcd {
 
@@ -235,6 +236,10 @@ __device__ inline void finalize_rr_warp(SolverState *st, double rr)
     __syncwarp();
     if (lane != 0) return;
     st->last_sum = rr;
+    if (st->stall) {  // a staged stencil of this iteration gave up waiting
+        st->halt = HALT_STALL;
+        return;
+    }
     if (!ok) {
         st->halt = HALT_NAN;
         st->nan_flag = 1;
@@ -258,6 +263,10 @@ __device__ inline void finalize_rr_warp(SolverState *st, double rr)
 __device__ inline void finalize_rr(SolverState *st, double rr)
 {
     st->last_sum = rr;
+    if (st->stall) {
+        st->halt = HALT_STALL;
+        return;
+    }
     if (!isfinite(rr)) {
         st->halt = HALT_NAN;
         st->nan_flag = 1;
@@ -412,6 +421,201 @@ __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo2(const 
         if (threadIdx.x < 32) finalize_pq_warp(st, tot);
     });
 }
+
+// ------------------------------------------------------------------ staged K1 / K2 (double-float)
+// The two stencil kernels of the FP64 iteration with the link stream staged
+// through shared memory (stencil_staged.cuh).  Persistent: block b walks the
+// batch's tiles b, b + gridDim.x, ...; the producer lane and the consumers
+// walk the same sequence and skip the same halted jobs (a job's halt word
+// does not change while its tiles are in flight).  Per-tile results, the
+// per-tile partials of <p, q> and the last-tile finaliser are those of
+// k_it_deo1 / k_it_deo2, so the iteration is bitwise the same.  No thread
+// leaves early: every kernel ends in ring_finish.
+template <int NJ>
+__device__ __forceinline__ void tile_of(const IterBatch<NJ> &B, int gt, int &j, int &tile)
+{
+    if (NJ == 1) {
+        j = 0;
+        tile = gt;
+        return;
+    }
+    if (B.interleave) {
+        j = gt % B.njobs;
+        tile = gt / B.njobs;
+        return;
+    }
+    int k = 0;
+#pragma unroll 1
+    while (k + 1 < B.njobs && gt >= B.tile_start[k + 1]) ++k;
+    j = k;
+    tile = gt - B.tile_start[k];
+}
+
+// Producer lane of a staged iteration kernel: tiles of live jobs, in order.
+template <int NJ>
+__device__ __forceinline__ void staged_iter_produce(RingDF &R, const IterBatch<NJ> &B, int ntot, int P)
+{
+    int gt = (int)blockIdx.x;
+    ring_produce(R, [&](const float4 *&base) -> bool {
+        for (; gt < ntot; gt += gridDim.x) {
+            int j, tile;
+            tile_of(B, gt, j, tile);
+            const IterJob &J = B.job[j];
+            if (J.st->halt) continue;
+            base = staged_tile_base(J.links_st, P, J.ntiles, tile);
+            gt += gridDim.x;
+            return true;
+        }
+        return false;
+    });
+}
+
+// Consumers of K1: t = D_oe p on the tiles of this block.
+template <int NJ>
+__device__ __forceinline__ void k1_staged_consume(RingDF &R, const IterBatch<NJ> &B, int ntot)
+{
+    uint32_t q = 0;
+    bool dead = false;
+    for (int gt = (int)blockIdx.x; gt < ntot; gt += gridDim.x) {
+        int j, tile;
+        tile_of(B, gt, j, tile);
+        const IterJob &J = B.job[j];
+        SolverState *st = J.st;
+        if (tile == 0 && threadIdx.x == 0) st->do_k4 = 0;
+        if (st->halt) continue;
+        const int Vh = J.g.Vh;
+        const int i = tile * kSites + threadIdx.x;
+        const bool live = i < Vh;
+        const float4 *p = (const float4 *)J.ps + (size_t)st->base * 3 * Vh;
+        Stencil S;
+        make_stencil(J.g, live ? i : 0, 1, S);
+        float2 res[6];
+        bool bad = false;
+        deo_site_df_staged<SF_DF>(R, q, dead, J.g, p, S, Vh, res, bad);
+        if (dead) st->stall = 1;
+        if (!live) continue;
+        float4 *t = (float4 *)J.t;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            t[(size_t)c * Vh + i] = make_float4(res[2 * c].x, res[2 * c].y, res[2 * c + 1].x, res[2 * c + 1].y);
+    }
+}
+
+// Consumers of K2: q = a p - D_eo t, the tile partial of <p, q>, and on the
+// job's last tile the tile-ordered total and the alpha / zeta finaliser.
+struct K2Shared {
+    double red[kStagedConsumers / 32];
+    double tot;
+    int last;
+};
+
+template <int NJ>
+__device__ __forceinline__ void k2_staged_consume(RingDF &R, K2Shared &sh, const IterBatch<NJ> &B, int ntot)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    uint32_t q = 0;
+    bool dead = false;
+    for (int gt = (int)blockIdx.x; gt < ntot; gt += gridDim.x) {
+        int j, tile;
+        tile_of(B, gt, j, tile);
+        const IterJob &J = B.job[j];
+        SolverState *st = J.st;
+        if (st->halt) continue;
+        const int Vh = J.g.Vh;
+        const int i = tile * kSites + threadIdx.x;
+        const bool live = i < Vh;
+        Stencil S;
+        make_stencil(J.g, live ? i : 0, 0, S);
+        float2 res[6];
+        bool bad = false;
+        deo_site_df_staged<SF_DF>(R, q, dead, J.g, J.t, S, Vh, res, bad);
+        if (dead) st->stall = 1;
+        Acc2 dot;
+        acc_zero(dot);
+        if (live) {
+            const float4 *p = (const float4 *)J.ps + (size_t)st->base * 3 * Vh;
+            float4 *qv = (float4 *)J.q;
+            const float2 a = st->a0_df;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float4 pv = p[(size_t)c * Vh + i];
+                const float2 qr = df_fma(a, make_float2(pv.x, pv.y), df_neg(res[2 * c]));
+                const float2 qi = df_fma(a, make_float2(pv.z, pv.w), df_neg(res[2 * c + 1]));
+                qv[(size_t)c * Vh + i] = make_float4(qr.x, qr.y, qi.x, qi.y);
+                acc_prod(dot, pv.x, pv.y, qr.x, qr.y);
+                acc_prod(dot, pv.z, pv.w, qi.x, qi.y);
+            }
+        }
+        // tile partial: the order of block_reduce_acc_n<256>
+        warp_reduce_acc(dot);
+        if (lane == 0) sh.red[w] = (double)dot.s + (double)dot.c;
+        consumer_sync();
+        if (threadIdx.x == 0) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < kStagedConsumers / 32; ++k) v += sh.red[k];
+            J.part[tile] = v;
+            __threadfence();
+            const unsigned prev = atomicAdd(J.ticket, 1u);
+            sh.last = (prev == (unsigned)(J.ntiles - 1));
+        }
+        consumer_sync();
+        if (!sh.last) continue;
+        // last tile of the job: partials in tile order (the order of tile_finish_block)
+        __threadfence();
+        double sum = 0.0;
+        for (int k = threadIdx.x; k < J.ntiles; k += kStagedConsumers) sum += __ldcg(J.part + k);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+        if (lane == 0) sh.red[w] = sum;
+        consumer_sync();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int k = 0; k < kStagedConsumers / 32; ++k) tot += sh.red[k];
+            sh.tot = tot;
+            *J.ticket = 0u;
+        }
+        consumer_sync();
+        if (threadIdx.x < 32) finalize_pq_warp(st, sh.tot);
+        __threadfence();
+    }
+}
+
+template <int NJ>
+__global__ void __launch_bounds__(kStagedThreads, kStagedMinBlocks)
+    k_it_deo1_st(const __grid_constant__ IterBatch<NJ> B, int ntot)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    RingDF &R = *reinterpret_cast<RingDF *>(smem_raw);
+    ring_init(R);
+    if (threadIdx.x >= kStagedConsumers) {
+        if (threadIdx.x == kStagedConsumers) staged_iter_produce(R, B, ntot, 1);
+    } else {
+        k1_staged_consume(R, B, ntot);
+    }
+    ring_finish(R);
+}
+
+// The reduction scratch lives in the dynamic allocation after the ring, so
+// both staged kernels place their barriers at the same offsets.
+template <int NJ>
+__global__ void __launch_bounds__(kStagedThreads, kStagedMinBlocks)
+    k_it_deo2_st(const __grid_constant__ IterBatch<NJ> B, int ntot)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    RingDF &R = *reinterpret_cast<RingDF *>(smem_raw);
+    K2Shared &sh = *reinterpret_cast<K2Shared *>(smem_raw + kRingDFBytes);
+    ring_init(R);
+    if (threadIdx.x >= kStagedConsumers) {
+        if (threadIdx.x == kStagedConsumers) staged_iter_produce(R, B, ntot, 0);
+    } else {
+        k2_staged_consume(R, sh, B, ntot);
+    }
+    ring_finish(R);
+}
+
+// Dynamic shared memory of the staged iteration kernels.
+constexpr size_t kStagedIterSmem = kRingDFBytes + sizeof(K2Shared);
 
 // ------------------------------------------------------------------ K3
 template <int NJ, int VP>
