@@ -469,9 +469,61 @@ def mixed_48_bench(lqcd, inputs, torch):
     return out
 
 
+class L2Flush:
+    """Flush between timed launches: write a 256 MB buffer (twice L2), then read
+    another 256 MB, so that L2 holds clean lines of the read buffer.  A write
+    alone leaves ~129 MB of dirty lines whose write-back the next kernel would
+    pay for (measured: +9 % on a 32^4 D_eo)."""
+
+    def __init__(self, torch):
+        self.w = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        self.r = torch.zeros(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def fill_(self, v):
+        self.w.fill_(v)
+        self.r.sum()
+
+
+def rational_bench(lqcd, inputs, torch):
+    """RHMC rational function on the 32^4 workload: y = r(A) b with the 15
+    quadrature poles of x^(-1/2) on [m^2, m^2 + 16] and the action Re <b, y>,
+    through the device call (inputs resident) and the host call; the host call
+    returns one spinor (25 MB) where the multi-shift host call returns 15."""
+    from paper_1701_00426_gb300 import rational
+    a0, a, sg = rational.inverse_sqrt_poles(N_SHIFT, MASS * MASS, MASS * MASS + 16.0)
+    U = inputs.random_links(DIMS)
+    b = inputs.gaussian_field(DIMS, k=0)
+    ctx = lqcd.Context(DIMS)
+    ctx.links_upload(U)
+    del U
+    bd = lqcd.to_device_spinor(b)
+    yd = torch.empty_like(bd)
+    ctx.rational_apply_dev(MASS, a0, a, sg, TOL, bd, yd)  # warm-up (graph capture, workspaces)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    act, info = ctx.rational_apply_dev(MASS, a0, a, sg, TOL, bd, yd)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    y, act_h, _ = ctx.rational_apply(MASS, a0, a, sg, TOL, b)
+    dth = time.perf_counter() - t1
+    t2 = time.perf_counter()
+    ctx.mscg_solve(MASS, sg, TOL, b)
+    dtm = time.perf_counter() - t2
+    ctx.close()
+    n3 = 3 * (int(np.prod(DIMS)) // 2)
+    return {"poles": N_SHIFT, "function": "x^(-1/2), Gauss-Legendre quadrature poles on [m^2, m^2+16]",
+            "rational_error_on_interval": rational.max_rel_error(a0, a, sg, MASS * MASS, MASS * MASS + 16.0),
+            "device_applies_per_s": round(1.0 / dt, 4), "host_applies_per_s": round(1.0 / dth, 4),
+            "host_mscg_solves_per_s_same_poles": round(1.0 / dtm, 4),
+            "d2h_bytes_host_apply": n3 * 16, "d2h_bytes_host_mscg": N_SHIFT * n3 * 16,
+            "action": act, "action_host_call": act_h, "iters": info["iters"],
+            "max_true_resid": max(info["true_resid"][:N_SHIFT])}
+
+
 def deo_sweep(lqcd, inputs, torch, flush, hbm_peak, sizes):
     """ns/site and algorithmic GB/s of one D_eo (odd -> even, library-tuned launch
-    shape), median and best of reps with L2 flushed (256 MB write) before each;
+    shape), median and best of reps with L2 flushed before each (L2Flush);
     fractions of the measured copy bandwidth and of the 7.9 TB/s nominal."""
     out = {}
     variants = [("fp64", 0, 18, torch.complex128, 1248.0), ("fp64_native_dfma", 3, 18, torch.complex128, 1248.0),
@@ -527,7 +579,7 @@ def run_ours(args, rank, world, local):
     hbm_peak, peak_src = peaks()
     if args.only_deo:
         if rank == 0:
-            flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+            flush = L2Flush(torch)
             print(json.dumps({"metric": METRIC, "unit": "ns/site", "config": {"only_deo": True},
                               "deo": deo_sweep(lqcd, inputs, torch, flush, hbm_peak, args.sweep)}), flush=True)
         return
@@ -636,12 +688,13 @@ def run_ours(args, rank, world, local):
     del bd, xd
     torch.cuda.empty_cache()
 
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush = L2Flush(torch)
     sweep = deo_sweep(lqcd, inputs, torch, flush, hbm_peak, args.sweep)
     del flush
     torch.cuda.empty_cache()
     extras = {}
-    for name, fn in [("mixed_48", lambda: mixed_48_bench(lqcd, inputs, torch)),
+    for name, fn in [("rational", lambda: rational_bench(lqcd, inputs, torch)),
+                     ("mixed_48", lambda: mixed_48_bench(lqcd, inputs, torch)),
                      ("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
                      ("packed", lambda: packed_bench(lqcd, inputs)),
                      ("serving", lambda: serving_bench(lqcd, inputs, n_req=args.serving_requests,
@@ -695,7 +748,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sweep", type=int, nargs="*", default=[16, 24, 32, 48])
     ap.add_argument("--lattice", type=int, default=32, help="side of the solve lattice (default 32)")
-    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: mixed_48 batched packed serving serving_mixed")
+    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: rational mixed_48 batched packed serving serving_mixed")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
     ap.add_argument("--only-deo", action="store_true",

@@ -225,6 +225,34 @@ int lqcd_mscg_solve_dev(lqcd_ctx *ctx, double mass, const double *shifts, int n_
                         double tol, const void *b, void *x, lqcd_solve_info *info,
                         void *stream);
 
+/* Rational function of A applied to a source, the step of the RHMC that
+ * replaces the root of the fermion matrix (Sec. 2.2, Eq. rooting, with the
+ * poles of Eq. shlineq; heatbath and actions of Algorithm 1, steps 3, 4, 6):
+ *   y = a0 b + sum_i a[i] (A + shifts[i])^{-1} b,   A = m^2 - D_eo D_oe,
+ * and, if action != NULL, *action = Re <b, y> (the pseudofermion action
+ * b^dag r(A) b).  a[i]: real coefficient of the pole shifts[i] (n_shift of
+ * each, 1..LQCD_MAX_SHIFTS; shifts >= 0; a0 and a[i] finite, any sign).
+ * One multi-shift solve to the FP64 true residual tol for every pole (as
+ * lqcd_mscg_solve; the per-pole residuals are in info), then a device
+ * epilogue forms y and the action in FP64 without moving the shifted
+ * solutions off the GPU; the error of y is at most
+ * tol ||b|| sum_i |a[i]| / (lambda_min + shifts[i]).  The shifted solutions
+ * live in a device scratch array of the context (n_shift x 48 B per even
+ * site), kept for later calls.  b, y: host canonical spinors ([Vh][3]
+ * complex128).  Synchronous.  LQCD_ENOCONV at max_iter (y, action and info
+ * still written); LQCD_EINVAL for a non-finite coefficient. */
+int lqcd_rational_apply(lqcd_ctx *ctx, double mass, double a0, const double *a,
+                        const double *shifts, int n_shift, double tol, const double *b,
+                        double *y, double *action, lqcd_solve_info *info);
+
+/* Same on device spinors (complex128 structure of arrays, as
+ * lqcd_mscg_solve_dev).  b is read and y written on the context's stream
+ * after `stream` (NULL = context stream) has been synchronised; returns when
+ * y and the action are complete. */
+int lqcd_rational_apply_dev(lqcd_ctx *ctx, double mass, double a0, const double *a,
+                            const double *shifts, int n_shift, double tol, const void *b,
+                            void *y, double *action, lqcd_solve_info *info, void *stream);
+
 /* Batched single-shift CG for n_rhs sources sharing the gauge field:
  * (A + sigma) x_k = b_k, k < n_rhs (1..16).  Inner iterations use the FP32
  * multi-right-hand-side D_eo (each link loaded once per application for all

@@ -390,6 +390,52 @@ int oracle_mscg(const int N[4], const cplx *links, double mass,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Rational function of A applied to a source (Sec. 2.2, RHMC)              */
+/* ------------------------------------------------------------------------ */
+
+/* The RHMC replaces the root of the fermion matrix in Eq. (rooting) by a
+ * rational function with real poles sigma_i (Sec. 2.2, Eq. shlineq):
+ *
+ *   r(A) b = a0 b + sum_i a_i (A + sigma_i)^{-1} b ,   A = m^2 - D_eo D_oe,
+ *
+ * and the pseudofermion action is phi^dag r(A) phi (Eq. rooting); the
+ * heatbath, the initial and the final action (Algorithm 1, steps 3, 4, 6) are
+ * each one such application.  Written out: the shifted solutions x_i come
+ * from oracle_mscg with tolerance tol, then y = a0 b + sum_i a_i x_i site by
+ * site, and *action = Re <b, y>.  Returns the status of oracle_mscg. */
+int oracle_rational_apply(const int N[4], const cplx *links, double mass, double a0,
+                          const double *a, const double *shifts, int n_shift,
+                          const cplx *b, cplx *y, double tol, int max_iter,
+                          double *action)
+{
+    const long n = volume(N) / 2 * 3;
+    if (n_shift < 1 || n_shift > 64) return -2;
+    cplx *x = malloc(sizeof(cplx) * n * n_shift);
+    int iters[2], shift_iters[64];
+    double resid[64];
+    const int status = oracle_mscg(N, links, mass, shifts, n_shift, b, x, tol, max_iter,
+                                   iters, shift_iters, resid);
+    for (long i = 0; i < n; ++i) {
+        cplx v = a0 * b[i];
+#if ORACLE_MUTANT == 11
+        /* planted: each coefficient applied to the next pole's solution */
+        for (int s = 0; s < n_shift; ++s) v += a[(s + 1) % n_shift] * x[s * n + i];
+#else
+        for (int s = 0; s < n_shift; ++s) v += a[s] * x[s * n + i];
+#endif
+        y[i] = v;
+    }
+#if ORACLE_MUTANT == 12
+    /* planted: the action takes the imaginary part */
+    *action = cimag(oracle_dot(n, b, y));
+#else
+    *action = creal(oracle_dot(n, b, y));
+#endif
+    free(x);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Timing support                                                            */
 /* ------------------------------------------------------------------------ */
 

@@ -72,6 +72,9 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.oracle_mscg.argtypes = [ip, vp, ctypes.c_double, dp, ctypes.c_int, vp, vp,
                                 ctypes.c_double, ctypes.c_int, ip, ip, dp]
     lib.oracle_mscg.restype = ctypes.c_int
+    lib.oracle_rational_apply.argtypes = [ip, vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int,
+                                          vp, vp, ctypes.c_double, ctypes.c_int, dp]
+    lib.oracle_rational_apply.restype = ctypes.c_int
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
     lib.oracle_set_threads.restype = ctypes.c_int
     lib.oracle_mutant.restype = ctypes.c_int
@@ -182,6 +185,24 @@ class Oracle:
         info = {"status": st, "iters": iters[0], "refine_iters": iters[1],
                 "shift_iters": list(shift_iters)[:n], "true_resid": resid[:n].copy()}
         return x, info
+
+    def rational_apply(self, dims, links, mass, a0, a, shifts, b, tol, max_iter=20000):
+        """y = a0 b + sum_i a_i (A + shifts_i)^{-1} b and Re <b, y>; returns (y, action, status)."""
+        V = int(np.prod(dims))
+        links = self._c128(links, (4, V, 3, 3))
+        b = self._c128(b, (V // 2, 3))
+        aa = np.ascontiguousarray(a, dtype=np.float64)
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        if aa.size != sh.size:
+            raise ValueError("one coefficient per shift")
+        y = np.empty_like(b)
+        act = ctypes.c_double()
+        dp = ctypes.POINTER(ctypes.c_double)
+        st = self.lib.oracle_rational_apply(self._dims(dims), self._ptr(links), float(mass), float(a0),
+                                            aa.ctypes.data_as(dp), sh.ctypes.data_as(dp), sh.size,
+                                            self._ptr(b), self._ptr(y), float(tol), int(max_iter),
+                                            ctypes.byref(act))
+        return y, act.value, st
 
     def set_threads(self, n: int = 0) -> int:
         return self.lib.oracle_set_threads(int(n))

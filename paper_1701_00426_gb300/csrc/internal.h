@@ -150,6 +150,8 @@ struct lqcd_ctx {
                             //   [2 parities][ntiles][8 hops][9][256] float4 (stencil_staged.cuh)
     lqcd::DevBuf err_word;  // device status word of the stand-alone staged D_eo (bit set = stall)
     lqcd::DevBuf io_a, io_b;  // device staging of host spinors for where = 0
+    lqcd::DevBuf rat_x;       // shifted solutions of a rational application [n][3][Vh] double2
+    lqcd::DevBuf rat_part;    // per-block partials of its action (+ the total)
     lqcd::Workspace ws;
     lqcd::Workspace ws32;                  // FP32 phase of a hybrid mixed-precision solve
     std::vector<lqcd::Workspace> ref_ws;   // per-shift refinement jobs

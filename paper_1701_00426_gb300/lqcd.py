@@ -44,7 +44,8 @@ EXPORTED = [
     "lqcd_default_opts", "lqcd_last_error", "lqcd_version", "lqcd_create", "lqcd_destroy",
     "lqcd_set_opts", "lqcd_device_bytes", "lqcd_links_upload", "lqcd_links_download",
     "lqcd_deo_apply", "lqcd_deo_apply_host_noalloc", "lqcd_deo_apply_ex", "lqcd_deo_apply_mrhs", "lqcd_mscg_solve",
-    "lqcd_mscg_solve_dev", "lqcd_cg_solve_mrhs", "lqcd_mscg_solve_packed", "lqcd_profile_iteration",
+    "lqcd_mscg_solve_dev", "lqcd_rational_apply", "lqcd_rational_apply_dev", "lqcd_cg_solve_mrhs",
+    "lqcd_mscg_solve_packed", "lqcd_profile_iteration",
     "lqcd_serve_create", "lqcd_serve_register_field", "lqcd_serve_submit", "lqcd_serve_poll",
     "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy", "lqcd_serve_set_opts",
 ]
@@ -120,6 +121,11 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                            ctypes.POINTER(lqcd_solve_info)]),
         "lqcd_mscg_solve_dev": (ctypes.c_int, [vp, ctypes.c_double, dp, ctypes.c_int, ctypes.c_double, vp, vp,
                                                ctypes.POINTER(lqcd_solve_info), vp]),
+        "lqcd_rational_apply": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int,
+                                               ctypes.c_double, vp, vp, dp, ctypes.POINTER(lqcd_solve_info)]),
+        "lqcd_rational_apply_dev": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int,
+                                                   ctypes.c_double, vp, vp, dp, ctypes.POINTER(lqcd_solve_info),
+                                                   vp]),
         "lqcd_cg_solve_mrhs": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                               ctypes.c_double, vp, vp, ctypes.POINTER(lqcd_solve_info)]),
         "lqcd_mscg_solve_packed": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, dp, ctypes.POINTER(dp), ip,
@@ -286,6 +292,39 @@ class Context:
         if not (allow_noconv and st == LQCD_ENOCONV):
             check(st)
         return x, info.as_dict()
+
+    def rational_apply(self, mass: float, a0: float, a, shifts, tol: float, b: np.ndarray,
+                       allow_noconv: bool = False):
+        """Host call: y = a0 b + sum_i a_i (A + shifts_i)^{-1} b; returns (y [Vh, 3], Re <b, y>, info)."""
+        aa = np.ascontiguousarray(a, dtype=np.float64)
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        if aa.size != sh.size:
+            raise ValueError("one coefficient per pole")
+        bb = _c128(b, (self.Vh, 3))
+        y = np.empty_like(bb)
+        act = ctypes.c_double()
+        info = lqcd_solve_info()
+        dp = ctypes.POINTER(ctypes.c_double)
+        st = self.lib.lqcd_rational_apply(self.h, float(mass), float(a0), aa.ctypes.data_as(dp),
+                                          sh.ctypes.data_as(dp), sh.size, float(tol), _ptr(bb), _ptr(y),
+                                          ctypes.byref(act), ctypes.byref(info))
+        if not (allow_noconv and st == LQCD_ENOCONV):
+            check(st)
+        return y, act.value, info.as_dict()
+
+    def rational_apply_dev(self, mass: float, a0: float, a, shifts, tol: float, b, y, stream=None):
+        """Device call: b, y complex128 [3, Vh]; returns (Re <b, y>, info)."""
+        aa = np.ascontiguousarray(a, dtype=np.float64)
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        if aa.size != sh.size:
+            raise ValueError("one coefficient per pole")
+        act = ctypes.c_double()
+        info = lqcd_solve_info()
+        dp = ctypes.POINTER(ctypes.c_double)
+        check(self.lib.lqcd_rational_apply_dev(self.h, float(mass), float(a0), aa.ctypes.data_as(dp),
+                                               sh.ctypes.data_as(dp), sh.size, float(tol), _dptr(b), _dptr(y),
+                                               ctypes.byref(act), ctypes.byref(info), _stream_ptr(stream)))
+        return act.value, info.as_dict()
 
     def mscg_solve_dev(self, mass: float, shifts, tol: float, b, x, stream=None, allow_noconv=False):
         """Device call: b complex128 [3, Vh], x complex128 [n_shift, 3, Vh]."""

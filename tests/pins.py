@@ -251,6 +251,71 @@ def pin_free_solve(orc, dims, shifts, k, mass=MASS, tol=1e-12) -> tuple[bool, st
     return worst <= 1e-10, f"free solve defect {worst:.2e}"
 
 
+# ------------------------------------------------- rational function (RHMC)
+RAT_A0 = 0.25
+RAT_A = [0.5, 1.2, 0.05, 3.0]
+RAT_SIGMA = [1e-3, 0.1, 2.0, 30.0]
+
+
+def rational_bound(tol, bnorm, a, sigma, lam_min) -> float:
+    """||y - r(A) b|| when every shifted solve meets the true residual tol:
+    ||x_i - x_i*|| <= ||(A + sigma_i)^{-1}|| tol ||b||."""
+    return tol * bnorm * sum(abs(ai) / (lam_min + si) for ai, si in zip(a, sigma))
+
+
+def pin_rational_vs_dense(orc, dims, mass=MASS, tol=1e-10) -> tuple[bool, str]:
+    """r(A) b = V diag(a0 + sum_i a_i / (lam + sigma_i)) V^dag b from the
+    eigendecomposition of the dense A (LAPACK), and the action b^dag r(A) b."""
+    U = inputs.random_links(dims, seed=55)
+    b = inputs.gaussian_field(dims, k=6)
+    y, act, st = orc.rational_apply(dims, U, mass, RAT_A0, RAT_A, RAT_SIGMA, b, tol)
+    if st != 0:
+        return False, f"status {st}"
+    lam, V = np.linalg.eigh(dense_A(orc, dims, U, mass))
+    r = RAT_A0 + sum(ai / (lam + si) for ai, si in zip(RAT_A, RAT_SIGMA))
+    ystar = V @ (r * (V.conj().T @ b.ravel()))
+    bound = rational_bound(tol, np.linalg.norm(b), RAT_A, RAT_SIGMA, lam[0])
+    err = float(np.linalg.norm(y.ravel() - ystar))
+    act_star = float(np.vdot(b.ravel(), ystar).real)
+    aerr = abs(act - act_star)
+    ok = err <= bound and aerr <= np.linalg.norm(b) * bound
+    return ok, f"|y - y*| = {err:.2e} (bound {bound:.2e}), |S - S*| = {aerr:.2e}"
+
+
+def pin_rational_inverse_sqrt(orc, dims, mass=MASS, tol=1e-10, n_poles=20) -> tuple[bool, str]:
+    """With the quadrature coefficients of x^(-1/2), r(A) b is A^(-1/2) b (dense
+    eigendecomposition) up to max_k |r(lam_k) - lam_k^(-1/2)| ||b|| plus the
+    solver bound; the action is b^dag A^(-1/2) b to the same order."""
+    from paper_1701_00426_gb300 import rational
+    U = inputs.random_links(dims, seed=56)
+    b = inputs.gaussian_field(dims, k=7)
+    lam, V = np.linalg.eigh(dense_A(orc, dims, U, mass))
+    a0, a, sig = rational.inverse_sqrt_poles(n_poles, lam[0], lam[-1])
+    y, act, st = orc.rational_apply(dims, U, mass, a0, a, sig, b, tol)
+    if st != 0:
+        return False, f"status {st}"
+    ystar = V @ (lam ** -0.5 * (V.conj().T @ b.ravel()))
+    approx = float(np.max(np.abs(rational.evaluate(a0, a, sig, lam) - lam ** -0.5)))
+    bnorm = np.linalg.norm(b)
+    bound = approx * bnorm + rational_bound(tol, bnorm, a, sig, lam[0])
+    err = float(np.linalg.norm(y.ravel() - ystar))
+    aerr = abs(act - float(np.vdot(b.ravel(), ystar).real))
+    ok = err <= 1.01 * bound and aerr <= 1.01 * bnorm * bound and approx < 1e-6
+    return ok, f"|y - A^-1/2 b| = {err:.2e} (bound {bound:.2e}, rational error {approx:.1e})"
+
+
+def pin_rational_free(orc, dims=(4, 4, 6, 8), k=(1, 3, 2, 5), mass=MASS, tol=1e-12) -> tuple[bool, str]:
+    """Free field: a plane wave b is an eigenvector, so r(A) b = r(lam_p) b."""
+    U = inputs.unit_links(dims)
+    b = plane_wave_even(dims, k, np.array([1.0, 0.5j, -0.25]))
+    lam = free_eigenvalue(dims, k, mass)
+    y, act, st = orc.rational_apply(dims, U, mass, RAT_A0, RAT_A, RAT_SIGMA, b, tol)
+    r = RAT_A0 + sum(ai / (lam + si) for ai, si in zip(RAT_A, RAT_SIGMA))
+    e = rel(y, r * b)
+    ae = abs(act - r * np.linalg.norm(b) ** 2) / (r * np.linalg.norm(b) ** 2)
+    return st == 0 and e <= 1e-10 and ae <= 1e-10, f"free rational defect {e:.2e}, action {ae:.2e}"
+
+
 BATTERY = [
     ("geometry 4x6x8x10", lambda o: pin_geometry(o, (4, 6, 8, 10))),
     ("phase anticommutation 4x6x8x10", lambda o: pin_phase_anticommutation(o, (4, 6, 8, 10))),
@@ -261,4 +326,6 @@ BATTERY = [
     ("free 2^4", pin_two_site),
     ("mscg vs LAPACK 4^4", lambda o: pin_mscg_vs_lapack(o, (4, 4, 4, 4), [1e-3, 0.05, 1.0, 30.0])),
     ("free solve 4x4x6x8", lambda o: pin_free_solve(o, (4, 4, 6, 8), [0.0, 0.3, 7.0], (1, 3, 2, 5))),
+    ("rational vs dense 4^4", lambda o: pin_rational_vs_dense(o, (4, 4, 4, 4))),
+    ("rational free 4x4x6x8", pin_rational_free),
 ]

@@ -16,6 +16,8 @@ MUTANTS = {
     8: "beta term dropped from zeta recurrence",
     9: "inverted zeta ratio in shifted step",
     10: "neighbours swapped in direction 1",
+    11: "rational coefficients applied to the next pole",
+    12: "rational action takes the imaginary part",
 }
 
 

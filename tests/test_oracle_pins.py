@@ -135,3 +135,33 @@ def test_inputs_are_su3_and_seeded():
     assert np.max(np.abs(np.linalg.det(m) - 1)) < 1e-14
     b = inputs.gaussian_field(dims, k=0)
     assert b.shape == (128, 3) and abs(np.mean(np.abs(b) ** 2) - 2.0) < 0.3
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4)])
+def test_rational_apply_matches_dense_eigendecomposition(orc, dims):
+    """RHMC rational function (Sec. 2.2): r(A) b and b^dag r(A) b vs LAPACK."""
+    ok, msg = pins.pin_rational_vs_dense(orc, dims)
+    assert ok, msg
+
+
+def test_rational_inverse_sqrt_matches_matrix_function(orc):
+    """Quadrature poles of x^(-1/2): r(A) b vs A^(-1/2) b from eigh."""
+    ok, msg = pins.pin_rational_inverse_sqrt(orc, (4, 4, 4, 4))
+    assert ok, msg
+
+
+def test_rational_free_field_closed_form(orc):
+    ok, msg = pins.pin_rational_free(orc)
+    assert ok, msg
+
+
+def test_inverse_sqrt_poles_converge():
+    """The quadrature rule is exact at x = s^2 and its error falls with the
+    number of poles on a fixed interval."""
+    from paper_1701_00426_gb300 import rational
+    errs = [rational.max_rel_error(*rational.inverse_sqrt_poles(n, 0.01, 4.01), 0.01, 4.01) for n in (8, 16, 24)]
+    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-10
+    a0, a, s = rational.inverse_sqrt_poles(5, 0.01, 4.01)
+    x = (0.01 * 4.01) ** 0.5
+    assert abs(rational.evaluate(a0, a, s, [x])[0] * x ** 0.5 - 1.0) < 1e-14
+    assert np.all(np.asarray(a) > 0) and np.all(np.diff(s) > 0)
