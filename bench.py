@@ -39,14 +39,15 @@ WORKLOAD = "mscg 32^4, m=0.01, 15 shifts log-spaced 1e-5..1e2, tol 1e-10, FP64 (
 COUNTS_KEY = "mscg_32x32x32x32_m0.01_15shifts_tol1e-10"
 
 
-# DRAM traffic of the dominant kernel (k_it_deo2, FP64 iteration) from one ncu
-# capture at 24^4 (profiles/mscg_iteration_kernels_24x24x24x24_ncu.md):
+# DRAM traffic of the dominant kernel (k_it_deo2_st, the staged FP64 D_eo with
+# the normal-operator epilogue) from one ncu capture at 24^4
+# (profiles/mscg_iteration_kernels_staged_24x24x24x24_ncu.md):
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch / (V/2).  It scales
 # with the even sites (links stream from HBM at both sizes, spinors hit L2), so
 # a launch at V/2 sites moves bytes_per_site * V/2.  Reported only while the
 # kernel sources still hash to the captured version.
-K2_TRAFFIC = {"bytes_per_site": 1273.1, "src_sha256_16": "0d056e60b2915c39",
-              "sources": ["solver_kernels.cuh", "deo_core.cuh", "common.cuh", "internal.h"]}
+K2_TRAFFIC = {"bytes_per_site": 1269.3, "src_sha256_16": "16c7b8e38c582c83",
+              "sources": ['solver_kernels.cuh', 'stencil_staged.cuh', 'bulk.cuh', 'deo_core.cuh', 'common.cuh', 'internal.h']}
 
 
 def k2_traffic_per_site():
