@@ -436,6 +436,259 @@ int oracle_rational_apply(const int N[4], const cplx *links, double mass, double
 }
 
 /* ------------------------------------------------------------------------ */
+/* Gauge part of the molecular dynamics step (Sec. 2.1, Sec. 4.2)           */
+/* ------------------------------------------------------------------------ */
+
+/* The gauge action is the tree-level Symanzik improved action (Sec. 2.1).
+ * Reading (the paper cites it and prints no formula):
+ *
+ *   S_g = -(beta/3) sum_x [ c0 sum_{mu<nu} Re Tr P_{mu nu}(x)
+ *                         + c1 sum_{mu!=nu} Re Tr R_{mu nu}(x) ],
+ *   c0 = 5/3, c1 = -1/12  (c0 + 8 c1 = 1),
+ *
+ * P_{mu nu}(x) the 1x1 plaquette and R_{mu nu}(x) the rectangle with two
+ * links along mu and one along nu, both starting at x, every loop counted
+ * once.  The momenta H_mu(x) are Hermitian and traceless (Sec. 2.2); the
+ * links move as U -> exp(i eps H) U, the kinetic term is (1/2) sum Tr H^2,
+ * so energy conservation fixes the force: F_mu(x) is the Hermitian traceless
+ * matrix with d/de S(exp(i e X) U)|_{e=0} = sum Tr(X_mu(x) F_mu(x)) for every
+ * Hermitian traceless X, and the momenta move as H -> H - eps F.  The gauge
+ * cycle of Algorithm 2 is built from these two updates; its most expensive
+ * part is the sum of the C-shaped 3- and 5-link paths around each link
+ * (Listing lst:rect_staples). */
+
+static const double SYM_C0 = 5.0 / 3.0;
+static const double SYM_C1 = -1.0 / 12.0;
+
+static void m_mul(const cplx *a, const cplx *b, cplx *c)
+{
+    cplx t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            cplx s = 0;
+            for (int k = 0; k < 3; ++k) s += a[i * 3 + k] * b[k * 3 + j];
+            t[i * 3 + j] = s;
+        }
+    memcpy(c, t, sizeof t);
+}
+
+static void m_dag(const cplx *a, cplx *c)
+{
+    cplx t[9];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) t[i * 3 + j] = conj(a[j * 3 + i]);
+    memcpy(c, t, sizeof t);
+}
+
+static void m_unit(cplx *a)
+{
+    for (int i = 0; i < 9; ++i) a[i] = (i % 4 == 0) ? 1.0 : 0.0;
+}
+
+/* coordinates x + d (periodic) */
+static void shifted(const int N[4], const int x[4], const int d[4], int y[4])
+{
+    for (int m = 0; m < 4; ++m) y[m] = ((x[m] + d[m]) % N[m] + N[m]) % N[m];
+}
+
+/* the link leaving site x + d in direction mu: U_mu(x + d) */
+static const cplx *link(const int N[4], const cplx *links, const int x[4], const int d[4], int mu)
+{
+    int y[4];
+    shifted(N, x, d, y);
+    return links + ((long)mu * volume(N) + lex_index(N, y)) * 9;
+}
+
+/* product of a path: start at x, take steps (dir, sign), multiply the link
+ * of each step: U_dir(y) for a step forward, U_dir(y - dir)^dag backward. */
+static void path_product(const int N[4], const cplx *links, const int x[4], int nsteps, const int *dir,
+                         const int *sgn, cplx *out)
+{
+    int d[4] = {0, 0, 0, 0};
+    cplx acc[9], t[9];
+    m_unit(acc);
+    for (int k = 0; k < nsteps; ++k) {
+        if (sgn[k] > 0) {
+            memcpy(t, link(N, links, x, d, dir[k]), sizeof t);
+            d[dir[k]] += 1;
+        } else {
+            d[dir[k]] -= 1;
+            m_dag(link(N, links, x, d, dir[k]), t);
+        }
+        m_mul(acc, t, acc);
+    }
+    memcpy(out, acc, sizeof acc);
+}
+
+static double re_trace(const cplx *a) { return creal(a[0] + a[4] + a[8]); }
+
+/* S_g by enumeration of every plaquette and rectangle (closed paths). */
+double oracle_gauge_action(const int N[4], const cplx *links, double beta)
+{
+    const long V = volume(N);
+    double sp = 0.0, sr = 0.0;
+    for (long n = 0; n < V; ++n) {
+        int x[4];
+        long r = n;
+        for (int m = 0; m < 4; ++m) { x[m] = (int)(r % N[m]); r /= N[m]; }
+        cplx W[9];
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = 0; nu < 4; ++nu) {
+                if (nu == mu) continue;
+                if (mu < nu) {
+                    const int dir[4] = {mu, nu, mu, nu}, sg[4] = {1, 1, -1, -1};
+                    path_product(N, links, x, 4, dir, sg, W);
+                    sp += re_trace(W);
+                }
+                const int dir[6] = {mu, mu, nu, mu, mu, nu}, sg[6] = {1, 1, 1, -1, -1, -1};
+                path_product(N, links, x, 6, dir, sg, W);
+                sr += re_trace(W);
+            }
+    }
+    return -(beta / 3.0) * (SYM_C0 * sp + SYM_C1 * sr);
+}
+
+/* Sum of the staples of U_mu(x): A with S_g = -(beta/3) Re Tr(U_mu(x) A) +
+ * (terms without U_mu(x)), written as the open paths from x + mu back to x
+ * that close each loop through U_mu(x), for nu != mu and both signs of nu:
+ *   plaquette:      nu, -mu, -nu
+ *   rectangle (a):  mu, nu, -mu, -mu, -nu        (U_mu(x) first of two)
+ *   rectangle (b):  nu, -mu, -mu, -nu, mu        (U_mu(x) second of two)
+ *   rectangle (c):  nu, nu, -mu, -nu, -nu        (two steps along nu)
+ * (with nu replaced by -nu for the other sign). */
+static void staple_sum(const int N[4], const cplx *links, const int x[4], int mu, cplx *A)
+{
+    int xp[4];
+    const int dmu[4] = {mu == 0, mu == 1, mu == 2, mu == 3};
+    shifted(N, x, dmu, xp);
+    for (int i = 0; i < 9; ++i) A[i] = 0;
+    cplx P[9];
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        for (int s = -1; s <= 1; s += 2) {
+            {
+                const int dir[3] = {nu, mu, nu}, sg[3] = {s, -1, -s};
+                path_product(N, links, xp, 3, dir, sg, P);
+                for (int i = 0; i < 9; ++i) A[i] += SYM_C0 * P[i];
+            }
+            {
+                const int dir[5] = {mu, nu, mu, mu, nu}, sg[5] = {1, s, -1, -1, -s};
+                path_product(N, links, xp, 5, dir, sg, P);
+                for (int i = 0; i < 9; ++i) A[i] += SYM_C1 * P[i];
+            }
+#if ORACLE_MUTANT != 13 /* mutant 13 planted: rectangle staple (b) left out */
+            {
+                const int dir[5] = {nu, mu, mu, nu, mu}, sg[5] = {s, -1, -1, -s, 1};
+                path_product(N, links, xp, 5, dir, sg, P);
+                for (int i = 0; i < 9; ++i) A[i] += SYM_C1 * P[i];
+            }
+#endif
+            {
+                const int dir[5] = {nu, nu, mu, nu, nu}, sg[5] = {s, s, -1, -s, -s};
+                path_product(N, links, xp, 5, dir, sg, P);
+                for (int i = 0; i < 9; ++i) A[i] += SYM_C1 * P[i];
+            }
+        }
+    }
+}
+
+/* F_mu(x) = traceless part of -(i beta / 6) (M - M^dag), M = U_mu(x) A_mu(x):
+ * from d/de Re Tr(exp(i e X) M) = (i/2) Tr(X (M - M^dag)).  F: [4][V][3][3]. */
+void oracle_gauge_force(const int N[4], const cplx *links, double beta, cplx *F)
+{
+    const long V = volume(N);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < V; ++n) {
+        int x[4];
+        long r = n;
+        for (int m = 0; m < 4; ++m) { x[m] = (int)(r % N[m]); r /= N[m]; }
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx A[9], M[9];
+            staple_sum(N, links, x, mu, A);
+            m_mul(links + ((long)mu * V + n) * 9, A, M);
+            cplx *f = F + ((long)mu * V + n) * 9;
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    f[i * 3 + j] = -I * (beta / 6.0) * (M[i * 3 + j] - conj(M[j * 3 + i]));
+#if ORACLE_MUTANT != 15 /* mutant 15 planted: the trace of the force is kept */
+            const cplx tr = (f[0] + f[4] + f[8]) / 3.0;
+            f[0] -= tr; f[4] -= tr; f[8] -= tr;
+#endif
+        }
+    }
+}
+
+/* E = exp(i t H) from the power series of the exponential: scale Z = i t H
+ * by 2^-k until its 1-norm is below 1/4, sum the series until the terms
+ * vanish against the partial sum, square k times. */
+void oracle_exp_iH(const cplx *H, double t, cplx *E)
+{
+    cplx Z[9], term[9], sum[9];
+    double nrm = 0.0;
+    for (int j = 0; j < 3; ++j) {
+        double c = 0.0;
+        for (int i = 0; i < 3; ++i) c += cabs(H[i * 3 + j]);
+        if (c > nrm) nrm = c;
+    }
+    nrm *= fabs(t);
+    int k = 0;
+    while (nrm > 0.25 && k < 60) { nrm *= 0.5; ++k; }
+    const double scale = ldexp(t, -k);
+    for (int i = 0; i < 9; ++i) Z[i] = I * scale * H[i];
+    m_unit(sum);
+    m_unit(term);
+    for (int n = 1; n < 40; ++n) {
+        m_mul(term, Z, term);
+        for (int i = 0; i < 9; ++i) term[i] /= n;
+        double tn = 0.0;
+        for (int i = 0; i < 9; ++i) { sum[i] += term[i]; tn += cabs(term[i]); }
+        if (tn < 1e-18) break;
+    }
+    for (int q = 0; q < k; ++q) m_mul(sum, sum, sum);
+    memcpy(E, sum, sizeof sum);
+}
+
+/* H_mu(x) -= eps F_mu(x) for every link (momenta [4][V][3][3]). */
+void oracle_mom_update(const int N[4], const cplx *links, cplx *mom, double beta, double eps)
+{
+    const long n9 = 4 * volume(N) * 9;
+    cplx *F = malloc(sizeof(cplx) * n9);
+    oracle_gauge_force(N, links, beta, F);
+    for (long i = 0; i < n9; ++i) mom[i] -= eps * F[i];
+    free(F);
+}
+
+/* U_mu(x) <- exp(i eps H_mu(x)) U_mu(x) for every link. */
+void oracle_link_update(const int N[4], cplx *links, const cplx *mom, double eps)
+{
+    const long nl = 4 * volume(N);
+#pragma omp parallel for schedule(static)
+    for (long l = 0; l < nl; ++l) {
+        cplx E[9];
+#if ORACLE_MUTANT == 14
+        /* planted: links move with exp(-i eps H) */
+        oracle_exp_iH(mom + l * 9, -eps, E);
+#else
+        oracle_exp_iH(mom + l * 9, eps, E);
+#endif
+        m_mul(E, links + l * 9, links + l * 9);
+    }
+}
+
+/* (1/2) sum Tr H^2 over all links. */
+double oracle_mom_energy(const int N[4], const cplx *mom)
+{
+    const long nl = 4 * volume(N);
+    double k = 0.0;
+    for (long l = 0; l < nl; ++l) {
+        const cplx *h = mom + l * 9;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) k += creal(h[i * 3 + j] * h[j * 3 + i]);
+    }
+    return 0.5 * k;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Timing support                                                            */
 /* ------------------------------------------------------------------------ */
 

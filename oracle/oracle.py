@@ -75,6 +75,18 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.oracle_rational_apply.argtypes = [ip, vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int,
                                           vp, vp, ctypes.c_double, ctypes.c_int, dp]
     lib.oracle_rational_apply.restype = ctypes.c_int
+    lib.oracle_gauge_action.argtypes = [ip, vp, ctypes.c_double]
+    lib.oracle_gauge_action.restype = ctypes.c_double
+    lib.oracle_gauge_force.argtypes = [ip, vp, ctypes.c_double, vp]
+    lib.oracle_gauge_force.restype = None
+    lib.oracle_exp_iH.argtypes = [vp, ctypes.c_double, vp]
+    lib.oracle_exp_iH.restype = None
+    lib.oracle_mom_update.argtypes = [ip, vp, vp, ctypes.c_double, ctypes.c_double]
+    lib.oracle_mom_update.restype = None
+    lib.oracle_link_update.argtypes = [ip, vp, vp, ctypes.c_double]
+    lib.oracle_link_update.restype = None
+    lib.oracle_mom_energy.argtypes = [ip, vp]
+    lib.oracle_mom_energy.restype = ctypes.c_double
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
     lib.oracle_set_threads.restype = ctypes.c_int
     lib.oracle_mutant.restype = ctypes.c_int
@@ -203,6 +215,46 @@ class Oracle:
                                             self._ptr(b), self._ptr(y), float(tol), int(max_iter),
                                             ctypes.byref(act))
         return y, act.value, st
+
+    # ------------------------------------------------- gauge MD (Symanzik)
+    def gauge_action(self, dims, links, beta: float) -> float:
+        V = int(np.prod(dims))
+        links = self._c128(links, (4, V, 3, 3))
+        return self.lib.oracle_gauge_action(self._dims(dims), self._ptr(links), float(beta))
+
+    def gauge_force(self, dims, links, beta: float) -> np.ndarray:
+        V = int(np.prod(dims))
+        links = self._c128(links, (4, V, 3, 3))
+        F = np.empty_like(links)
+        self.lib.oracle_gauge_force(self._dims(dims), self._ptr(links), float(beta), self._ptr(F))
+        return F
+
+    def exp_iH(self, H, t: float) -> np.ndarray:
+        H = self._c128(H, (3, 3))
+        E = np.empty_like(H)
+        self.lib.oracle_exp_iH(self._ptr(H), float(t), self._ptr(E))
+        return E
+
+    def mom_update(self, dims, links, mom, beta: float, eps: float) -> np.ndarray:
+        """H - eps F(U) (a new array)."""
+        V = int(np.prod(dims))
+        links = self._c128(links, (4, V, 3, 3))
+        H = np.array(self._c128(mom, (4, V, 3, 3)), copy=True)
+        self.lib.oracle_mom_update(self._dims(dims), self._ptr(links), self._ptr(H), float(beta), float(eps))
+        return H
+
+    def link_update(self, dims, links, mom, eps: float) -> np.ndarray:
+        """exp(i eps H) U for every link (a new array)."""
+        V = int(np.prod(dims))
+        U = np.array(self._c128(links, (4, V, 3, 3)), copy=True)
+        H = self._c128(mom, (4, V, 3, 3))
+        self.lib.oracle_link_update(self._dims(dims), self._ptr(U), self._ptr(H), float(eps))
+        return U
+
+    def mom_energy(self, dims, mom) -> float:
+        V = int(np.prod(dims))
+        H = self._c128(mom, (4, V, 3, 3))
+        return self.lib.oracle_mom_energy(self._dims(dims), self._ptr(H))
 
     def set_threads(self, n: int = 0) -> int:
         return self.lib.oracle_set_threads(int(n))

@@ -107,6 +107,22 @@ def random_gauge_transform(dims, seed: int) -> np.ndarray:
     return random_su3(V, np.random.default_rng(seed))
 
 
+MOM_SEED = 2017
+
+
+def random_momenta(dims, seed: int = MOM_SEED) -> np.ndarray:
+    """Hermitian traceless 3x3 matrices, one per link, [4][V][3][3] complex128,
+    with density proportional to exp(-(1/2) Tr H^2): real Gaussian diagonal
+    pairs and complex off-diagonal entries of variance 1/2 per part, the
+    diagonal made traceless."""
+    V = volume(check_dims(dims))
+    rng = np.random.default_rng(seed)
+    a = (rng.standard_normal((4, V, 3, 3)) + 1j * rng.standard_normal((4, V, 3, 3))) / np.sqrt(2.0)
+    h = 0.5 * (a + np.conj(np.swapaxes(a, -1, -2)))
+    tr = np.trace(h, axis1=-2, axis2=-1) / 3.0
+    return h - tr[..., None, None] * np.eye(3)
+
+
 def log_shifts(n: int = 15, lo: float = 1e-5, hi: float = 1e2) -> np.ndarray:
     """n shifts log-spaced from lo to hi, ascending."""
     if n == 1:

@@ -316,6 +316,109 @@ def pin_rational_free(orc, dims=(4, 4, 6, 8), k=(1, 3, 2, 5), mass=MASS, tol=1e-
     return st == 0 and e <= 1e-10 and ae <= 1e-10, f"free rational defect {e:.2e}, action {ae:.2e}"
 
 
+# ------------------------------------------------------- gauge MD (f2)
+BETA = 5.5
+
+
+def pin_gauge_action_unit(orc, dims=(4, 4, 4, 6), beta=BETA) -> tuple[bool, str]:
+    """U = 1: every plaquette and rectangle has trace 3, 6 plaquettes and 12
+    rectangles per site: S = -(beta/3) V (6 c0 + 12 c1) 3 = -9 beta V."""
+    V = int(np.prod(dims))
+    S = orc.gauge_action(dims, inputs.unit_links(dims), beta)
+    return abs(S + 9.0 * beta * V) <= 1e-12 * 9.0 * beta * V, f"S(1) = {S}, expected {-9.0 * beta * V}"
+
+
+def gauge_transform_links(dims, U, Om):
+    coords = list(sites(dims))
+    lex_of = {x: n for n, x in enumerate(coords)}
+    Up = np.empty_like(U)
+    for mu in range(4):
+        for n, x in enumerate(coords):
+            xp = list(x); xp[mu] = (xp[mu] + 1) % dims[mu]
+            Up[mu, n] = Om[n] @ U[mu, n] @ Om[lex_of[tuple(xp)]].conj().T
+    return Up
+
+
+def pin_gauge_invariance(orc, dims=(4, 4, 4, 6), beta=BETA, seed=71) -> tuple[bool, str]:
+    """S[U^Omega] = S[U] and F[U^Omega]_mu(x) = Omega(x) F[U]_mu(x) Omega(x)^dag."""
+    U = inputs.random_links(dims, seed=seed)
+    Om = inputs.random_gauge_transform(dims, seed=seed + 1)
+    Up = gauge_transform_links(dims, U, Om)
+    S, Sp = orc.gauge_action(dims, U, beta), orc.gauge_action(dims, Up, beta)
+    F, Fp = orc.gauge_force(dims, U, beta), orc.gauge_force(dims, Up, beta)
+    Frot = np.einsum("vij,mvjk,vlk->mvil", Om, F, Om.conj())
+    eS = abs(S - Sp) / abs(S)
+    eF = rel(Fp, Frot)
+    return eS <= 1e-13 and eF <= 1e-13, f"action {eS:.2e}, force covariance {eF:.2e}"
+
+
+def pin_force_is_derivative(orc, dims=(4, 4, 4, 4), beta=BETA, h=1e-4, seed=72) -> tuple[bool, str]:
+    """d/de S(exp(i e X) U) at e = 0 equals sum Tr(X F) for a random Hermitian
+    traceless X on every link (central difference, S enumerated loop by loop),
+    and F is Hermitian and traceless."""
+    U = inputs.random_links(dims, seed=seed)
+    X = inputs.random_momenta(dims, seed=seed + 1)
+    F = orc.gauge_force(dims, U, beta)
+    num = (orc.gauge_action(dims, orc.link_update(dims, U, X, h), beta)
+           - orc.gauge_action(dims, orc.link_update(dims, U, X, -h), beta)) / (2.0 * h)
+    ana = float(np.einsum("mvij,mvji->", X, F).real)
+    herm = float(np.abs(F - np.conj(np.swapaxes(F, -1, -2))).max())
+    trace = float(np.abs(np.trace(F, axis1=-2, axis2=-1)).max())
+    e = abs(num - ana) / abs(ana)
+    ok = e <= 1e-6 and herm <= 1e-13 * np.abs(F).max() and trace <= 1e-13 * np.abs(F).max()
+    return ok, f"derivative defect {e:.2e}, hermiticity {herm:.1e}, trace {trace:.1e}"
+
+
+def pin_exp(orc, seed=73) -> tuple[bool, str]:
+    """exp(i t H) against scipy.linalg.expm; unitary with determinant 1."""
+    import scipy.linalg
+    H = inputs.random_momenta((2, 2, 2, 2), seed=seed)[0, :6]
+    worst = 0.0
+    for t in (1e-3, 0.3, 5.0):
+        for h in H:
+            E = orc.exp_iH(h, t)
+            ref = scipy.linalg.expm(1j * t * h)
+            worst = max(worst, float(np.abs(E - ref).max()),
+                        float(np.abs(E @ E.conj().T - np.eye(3)).max()), abs(np.linalg.det(E) - 1.0))
+    return worst <= 1e-13, f"exp defect {worst:.2e}"
+
+
+def leapfrog(orc, dims, U, H, beta, tau, n):
+    """tau split in n leapfrog steps from the two updates (H half, U, H half)."""
+    e = tau / n
+    H = orc.mom_update(dims, U, H, beta, 0.5 * e)
+    for k in range(n):
+        U = orc.link_update(dims, U, H, e)
+        H = orc.mom_update(dims, U, H, beta, e if k < n - 1 else 0.5 * e)
+    return U, H
+
+
+def pin_md_reversible(orc, dims=(4, 4, 4, 4), beta=BETA, seed=74) -> tuple[bool, str]:
+    """Leapfrog forward, momenta flipped, leapfrog again: back to the start."""
+    U0 = inputs.random_links(dims, seed=seed)
+    H0 = inputs.random_momenta(dims, seed=seed + 1)
+    U1, H1 = leapfrog(orc, dims, U0, H0, beta, 0.1, 4)
+    U2, H2 = leapfrog(orc, dims, U1, -H1, beta, 0.1, 4)
+    eU, eH = rel(U2, U0), rel(-H2, H0)
+    moved = rel(U1, U0)
+    return eU <= 1e-12 and eH <= 1e-12 and moved > 1e-3, f"return defect U {eU:.1e}, H {eH:.1e} (moved {moved:.1e})"
+
+
+def pin_md_energy(orc, dims=(4, 4, 4, 4), beta=BETA, seed=75) -> tuple[bool, str]:
+    """dH = dK + dS of a leapfrog trajectory shrinks as the squared step: four
+    times less per halving of the step (second-order integrator)."""
+    U0 = inputs.random_links(dims, seed=seed)
+    H0 = inputs.random_momenta(dims, seed=seed + 1)
+    E0 = orc.mom_energy(dims, H0) + orc.gauge_action(dims, U0, beta)
+    dH = []
+    for n in (4, 8, 16):
+        U, H = leapfrog(orc, dims, U0, H0, beta, 0.2, n)
+        dH.append(abs(orc.mom_energy(dims, H) + orc.gauge_action(dims, U, beta) - E0))
+    r1, r2 = dH[0] / dH[1], dH[1] / dH[2]
+    ok = 3.5 <= r1 <= 4.5 and 3.5 <= r2 <= 4.5
+    return ok, f"|dH| {dH[0]:.2e} {dH[1]:.2e} {dH[2]:.2e}, ratios {r1:.2f} {r2:.2f}"
+
+
 BATTERY = [
     ("geometry 4x6x8x10", lambda o: pin_geometry(o, (4, 6, 8, 10))),
     ("phase anticommutation 4x6x8x10", lambda o: pin_phase_anticommutation(o, (4, 6, 8, 10))),
@@ -328,4 +431,7 @@ BATTERY = [
     ("free solve 4x4x6x8", lambda o: pin_free_solve(o, (4, 4, 6, 8), [0.0, 0.3, 7.0], (1, 3, 2, 5))),
     ("rational vs dense 4^4", lambda o: pin_rational_vs_dense(o, (4, 4, 4, 4))),
     ("rational free 4x4x6x8", pin_rational_free),
+    ("gauge action U=1", pin_gauge_action_unit),
+    ("gauge force = derivative of the action 4^4", pin_force_is_derivative),
+    ("MD energy conservation O(dt^2) 4^4", pin_md_energy),
 ]

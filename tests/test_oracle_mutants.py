@@ -18,6 +18,9 @@ MUTANTS = {
     10: "neighbours swapped in direction 1",
     11: "rational coefficients applied to the next pole",
     12: "rational action takes the imaginary part",
+    13: "rectangle staple (b) left out of the gauge force",
+    14: "links move with exp(-i eps H)",
+    15: "trace of the gauge force kept",
 }
 
 

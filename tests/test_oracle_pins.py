@@ -165,3 +165,37 @@ def test_inverse_sqrt_poles_converge():
     x = (0.01 * 4.01) ** 0.5
     assert abs(rational.evaluate(a0, a, s, [x])[0] * x ** 0.5 - 1.0) < 1e-14
     assert np.all(np.asarray(a) > 0) and np.all(np.diff(s) > 0)
+
+
+def test_gauge_action_of_unit_links(orc):
+    """Tree-level Symanzik action (Sec. 2.1): S(U = 1) = -9 beta V."""
+    ok, msg = pins.pin_gauge_action_unit(orc)
+    assert ok, msg
+
+
+def test_gauge_action_invariant_and_force_covariant(orc):
+    ok, msg = pins.pin_gauge_invariance(orc)
+    assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4)])
+def test_gauge_force_is_derivative_of_action(orc, dims):
+    """The force from the staple sums (Listing lst:rect_staples) against a
+    central difference of the action enumerated loop by loop."""
+    ok, msg = pins.pin_force_is_derivative(orc, dims)
+    assert ok, msg
+
+
+def test_su3_exponential(orc):
+    ok, msg = pins.pin_exp(orc)
+    assert ok, msg
+
+
+def test_md_leapfrog_reversible(orc):
+    ok, msg = pins.pin_md_reversible(orc)
+    assert ok, msg
+
+
+def test_md_energy_violation_second_order(orc):
+    ok, msg = pins.pin_md_energy(orc)
+    assert ok, msg
