@@ -288,6 +288,47 @@ int lqcd_profile_iteration(lqcd_ctx *ctx, double mass, const double *shifts, int
                            double tol, const void *b, int iters, double ms_out[4],
                            double *n_active_avg);
 
+/* ------------------------------------------------- gauge molecular dynamics */
+
+/* The gauge part of the molecular dynamics step (Sec. 4.2, Algorithm 2: the
+ * gauge cycle; Table md-norm), for the tree-level Symanzik improved action
+ * (Sec. 2.1), read as
+ *   S_g = -(beta/3) sum_x [ c0 sum_{mu<nu} Re Tr P_{mu nu}(x)
+ *                         + c1 sum_{mu!=nu} Re Tr R_{mu nu}(x) ],
+ *   c0 = 5/3, c1 = -1/12, P the plaquette, R the 2x1 rectangle (two links
+ *   along mu), every loop once;
+ * momenta H_mu(x) Hermitian and traceless, links moving as U -> exp(i e H) U,
+ * kinetic term (1/2) sum Tr H^2, so the force F_mu(x) (Hermitian, traceless)
+ * is the derivative of S_g along those motions and the momenta move as
+ * H -> H - e F.  The context keeps the momenta on the device.  prec:
+ * LQCD_PREC_FP64 (native FP64 arithmetic on the FP64 links) or
+ * LQCD_PREC_FP32 (FP32 arithmetic on FP32 copies of links and momenta,
+ * Algorithm 1 step 5: "possibly in single precision"; the copies are made
+ * when the precision changes and the FP32 links become the FP64 links again
+ * before any D_eo or solve).  All calls are synchronous. */
+
+/* Momenta in the canonical host layout [4][V][3][3] complex128 (n_doubles =
+ * 4*V*18), Hermitian and traceless to 1e-12 relative (else LQCD_EINVAL). */
+int lqcd_mom_upload(lqcd_ctx *ctx, const double *H, size_t n_doubles);
+int lqcd_mom_download(lqcd_ctx *ctx, double *H, size_t n_doubles);
+
+/* H <- H - eps F(U) on every link. */
+int lqcd_gauge_mom_update(lqcd_ctx *ctx, int prec, double beta, double eps);
+
+/* U <- exp(i eps H) U on every link (the exponential of the traceless
+ * Hermitian momentum to rounding). */
+int lqcd_gauge_link_update(lqcd_ctx *ctx, int prec, double eps);
+
+/* n_steps times: the momentum update, then the link update, each with eps
+ * (the unit that Table md-norm times per site); n_steps >= 0. */
+int lqcd_gauge_md_steps(lqcd_ctx *ctx, int prec, double beta, double eps, int n_steps);
+
+/* *S = S_g(U) of the current links (sums in FP64 in a fixed order). */
+int lqcd_gauge_action(lqcd_ctx *ctx, int prec, double beta, double *S);
+
+/* *K = (1/2) sum Tr H^2 of the current momenta. */
+int lqcd_mom_energy(lqcd_ctx *ctx, int prec, double *K);
+
 /* ----------------------------------------------------------------- serving */
 
 typedef struct lqcd_server lqcd_server;

@@ -19,7 +19,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblqcd.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-UNITS = ["api.cu", "deo.cu", "solver.cu", "mrhs.cu", "serve.cu", "noalloc.cu", "rational.cu"]
+UNITS = ["api.cu", "deo.cu", "solver.cu", "mrhs.cu", "serve.cu", "noalloc.cu", "rational.cu", "gauge.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

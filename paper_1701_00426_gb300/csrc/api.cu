@@ -53,7 +53,8 @@ void DevBuf::release()
 size_t ctx_device_bytes(const lqcd_ctx *c)
 {
     const DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->lnk_dfs,
-                         &c->err_word, &c->io_a, &c->io_b, &c->rat_x, &c->rat_part, &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
+                         &c->err_word, &c->io_a, &c->io_b, &c->rat_x, &c->rat_part, &c->mom64,
+                         &c->mom32, &c->md_part, &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
     size_t s = 0;
     for (const DevBuf *p : b) s += p->bytes;
     s += c->ws32.bytes();
@@ -136,7 +137,8 @@ void lqcd_destroy(lqcd_ctx *c)
     if (c->stream) cudaStreamSynchronize(c->stream);
     c->graph.reset();
     DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->lnk_dfs, &c->err_word,
-                   &c->io_a, &c->io_b, &c->rat_x, &c->rat_part, &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
+                   &c->io_a, &c->io_b, &c->rat_x, &c->rat_part, &c->mom64, &c->mom32, &c->md_part,
+                   &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
     for (DevBuf *p : b) p->release();
     c->ws32.release();
     for (Workspace &w : c->ref_ws) w.release();
@@ -176,7 +178,7 @@ int lqcd_deo_apply(lqcd_ctx *c, int out_parity, const void *in, void *out, int w
     if (where == 1) return deo_launch(c, out_parity, LQCD_PREC_FP64, 18, in, out, (cudaStream_t)stream ? (cudaStream_t)stream : c->stream);
     if (where != 0) return fail(LQCD_EINVAL, "where must be 0 (host) or 1 (device)");
     if (!in || !out) return fail(LQCD_EINVAL, "NULL spinor pointer");
-    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (int lr = links_ready(c)) return lr;
     const size_t bytes = c->Vh * 3 * sizeof(double2);
     DevBuf din, dout;
     int st;

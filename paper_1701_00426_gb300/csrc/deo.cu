@@ -108,6 +108,69 @@ __global__ void k_build_staged_df(Geom g, const float4 *__restrict__ L, float4 *
     st[t] = v;
 }
 
+// Every derived link format from the FP64 SoA master (after molecular
+// dynamics moved the links): one thread per (mu, parity, site), the same
+// conversions as k_convert_links.
+__global__ void k_derive_links(int Vh, const double2 *__restrict__ nat, float4 *df, float2 *f18, float2 *f12,
+                               uint32_t *h12)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    const int idx = (int)(t % Vh), mp = (int)(t / Vh);
+    const int mu = mp >> 1, par = mp & 1;
+    for (int c = 0; c < 9; ++c) {
+        const size_t o = link_base(mu, par, 9, Vh) + (size_t)c * Vh + idx;
+        const double2 d = nat[o];
+        const float2 re = f64_to_df_slow(d.x), im = f64_to_df_slow(d.y);
+        df[o] = make_float4(re.x, re.y, im.x, im.y);
+        const float2 f = make_float2((float)d.x, (float)d.y);
+        f18[o] = f;
+        if (c < 6) {
+            f12[(link_base(mu, par, 3, Vh) + (size_t)(c >> 1) * Vh + idx) * 2 + (c & 1)] = f;
+            const __half2 h = __floats2half2_rn(f.x, f.y);
+            const uint32_t w = *reinterpret_cast<const uint32_t *>(&h);
+            if (c < 4)
+                h12[((size_t)(mu * 2 + par) * Vh + idx) * 4 + c] = w;
+            else
+                h12[(size_t)8 * Vh * 4 + ((size_t)(mu * 2 + par) * Vh + idx) * 2 + (c - 4)] = w;
+        }
+    }
+}
+
+__global__ void k_promote_f32_links(const float2 *__restrict__ a, double2 *b, long n)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = make_double2((double)a[t].x, (double)a[t].y);
+}
+
+int links_ready(lqcd_ctx *c)
+{
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (!c->links_derived_stale) return LQCD_OK;
+    const long Vh = (long)c->Vh;
+    if (c->md_links_newest == LQCD_PREC_FP32) {
+        const long n = 72 * Vh;
+        k_promote_f32_links<<<(unsigned)((n + 255) / 256), 256, 0, c->stream>>>(c->lnk_f18.as<float2>(),
+                                                                           c->lnk_nat.as<double2>(), n);
+        c->launches += 1;
+        c->md_links_newest = LQCD_PREC_FP64;
+    }
+    k_derive_links<<<(unsigned)((8 * Vh + 255) / 256), 256, 0, c->stream>>>(
+        (int)Vh, c->lnk_nat.as<double2>(), c->lnk_df.as<float4>(), c->lnk_f18.as<float2>(), c->lnk_f12.as<float2>(),
+        c->lnk_h12.as<uint32_t>());
+    c->launches += 1;
+    if (c->lnk_dfs.ptr) {
+        const int ntiles = (int)((Vh + kTile - 1) / kTile);
+        const size_t ne = staged_df_elems(ntiles);
+        k_build_staged_df<<<(unsigned)((ne + 255) / 256), 256, 0, c->stream>>>(c->g, c->lnk_df.as<float4>(),
+                                                                          c->lnk_dfs.as<float4>(), ntiles);
+        c->launches += 1;
+    }
+    LQCD_CUDA(cudaGetLastError());
+    c->links_derived_stale = false;
+    return LQCD_OK;
+}
+
 int upload_links(lqcd_ctx *c, const double *host, size_t n)
 {
     const size_t want = 4 * c->V * 18;
@@ -159,6 +222,8 @@ int upload_links(lqcd_ctx *c, const double *host, size_t n)
         return fail(LQCD_EINVAL, "links: an entry is NaN/Inf or has magnitude >= 2^60");
     }
     c->links_ok = true;
+    c->md_links_newest = LQCD_PREC_FP64;
+    c->links_derived_stale = false;
     return LQCD_OK;
 }
 
@@ -166,7 +231,7 @@ int download_links(lqcd_ctx *c, double *host, size_t n)
 {
     const size_t want = 4 * c->V * 18;
     if (!host || n != want) return fail(LQCD_EINVAL, "links download: expected 4*V*18 doubles");
-    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (int lr = links_ready(c)) return lr;
     DevBuf stage;
     int st;
     if ((st = stage.ensure(want * sizeof(double)))) return st;
@@ -549,7 +614,7 @@ int deo_tuned_block(const lqcd_ctx *c, int variant)
 
 int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *out, cudaStream_t s)
 {
-    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (int lr = links_ready(c)) return lr;
     if (P != 0 && P != 1) return fail(LQCD_EINVAL, "out_parity must be 0 or 1");
     if (!in || !out) return fail(LQCD_EINVAL, "NULL spinor pointer");
     if (in == out) return fail(LQCD_EINVAL, "in and out must not overlap");

@@ -1,0 +1,812 @@
+// gauge.cu -- the gauge part of the molecular dynamics step (Sec. 2.1, the
+// tree-level Symanzik improved action; Sec. 4.2 and Algorithm 2, the gauge
+// cycle; Listing lst:rect_staples, the staples; Table md-norm, its cost per
+// site) in FP64 and in FP32 (Algorithm 1, step 5: "possibly in single
+// precision").
+//
+//   S_g = -(beta/3) sum_x [ c0 sum_{mu<nu} Re Tr P_{mu nu}(x) + c1 sum_{mu!=nu} Re Tr R_{mu nu}(x) ]
+//   c0 = 5/3, c1 = -1/12;  P: 1x1 plaquette, R: 2 links along mu, 1 along nu
+//   force:  F_mu(x) = traceless part of -(i beta/6)(M - M^dag), M = U_mu(x) A_mu(x)
+//   momenta: H <- H - eps F          links: U <- exp(i eps H) U
+// where A_mu(x) is the sum of the staples of U_mu(x): c0 times the 3-link
+// paths and c1 times the 5-link paths that close the plaquettes and
+// rectangles through U_mu(x), for nu != mu and both signs of nu.
+//
+// Storage: links in the context's SoA formats, [4 mu][2 parity][9 comp][V/2]
+// (double2 for FP64 -- the master copy -- and float2 for FP32); momenta as 8
+// reals per link (traceless Hermitian: h00, h11, re/im of h01, h02, h12),
+// [4][2][8][V/2].  One thread per link.  Neighbour links are gathered through
+// L1/L2 (every link is read by ~80 threads of nearby sites).
+#include <cmath>
+#include <mutex>
+
+#include "internal.h"
+
+namespace lqcd {
+
+constexpr double kSymC0 = 5.0 / 3.0;
+constexpr double kSymC1 = -1.0 / 12.0;
+constexpr int kGaugeThreads = 128;
+
+template <class T> struct Cplx { T re, im; };
+template <class T> struct Mat3 { Cplx<T> e[9]; };
+template <class T> struct Vec2T;
+template <> struct Vec2T<double> { using t = double2; };
+template <> struct Vec2T<float> { using t = float2; };
+
+template <class T>
+__device__ __forceinline__ void mat_mul(const Mat3<T> &a, const Mat3<T> &b, Mat3<T> &c)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T re = 0, im = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const Cplx<T> x = a.e[i * 3 + k], y = b.e[k * 3 + j];
+                re = fma(x.re, y.re, fma(-x.im, y.im, re));
+                im = fma(x.re, y.im, fma(x.im, y.re, im));
+            }
+            c.e[i * 3 + j] = {re, im};
+        }
+}
+
+// c = a b^dag
+template <class T>
+__device__ __forceinline__ void mat_mul_dag(const Mat3<T> &a, const Mat3<T> &b, Mat3<T> &c)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            T re = 0, im = 0;
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const Cplx<T> x = a.e[i * 3 + k], y = b.e[j * 3 + k];  // conj(b_jk)
+                re = fma(x.re, y.re, fma(x.im, y.im, re));
+                im = fma(-x.re, y.im, fma(x.im, y.re, im));
+            }
+            c.e[i * 3 + j] = {re, im};
+        }
+}
+
+template <class T>
+__device__ __forceinline__ void mat_dag(Mat3<T> &a)
+{
+    Mat3<T> t = a;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) a.e[i * 3 + j] = {t.e[j * 3 + i].re, -t.e[j * 3 + i].im};
+}
+
+template <class T>
+__device__ __forceinline__ void mat_axpy(T s, const Mat3<T> &x, Mat3<T> &y)
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) y.e[i] = {fma(s, x.e[i].re, y.e[i].re), fma(s, x.e[i].im, y.e[i].im)};
+}
+
+// ------------------------------------------------------------------ geometry of links
+struct LinkGeo {
+    int N[4];
+    int Vh;
+};
+
+__device__ __forceinline__ int wrap(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
+
+// (parity, half index) of x + d, |d_m| <= 2 <= N_m
+__device__ __forceinline__ void site_of(const LinkGeo &g, const int (&x)[4], int d0, int d1, int d2, int d3, int &par,
+                                        int &idx)
+{
+    const int y0 = wrap(x[0] + d0, g.N[0]), y1 = wrap(x[1] + d1, g.N[1]);
+    const int y2 = wrap(x[2] + d2, g.N[2]), y3 = wrap(x[3] + d3, g.N[3]);
+    par = (y0 + y1 + y2 + y3) & 1;
+    idx = (y0 + g.N[0] * (y1 + g.N[1] * (y2 + g.N[2] * y3))) >> 1;
+}
+
+template <class T>
+__device__ __forceinline__ void load_link_soa(const typename Vec2T<T>::t *__restrict__ L, int mu, int par, int idx,
+                                              int Vh, Mat3<T> &U)
+{
+    const typename Vec2T<T>::t *p = L + (size_t)((mu * 2 + par) * 9) * Vh + idx;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const typename Vec2T<T>::t v = __ldg(p + (size_t)c * Vh);
+        U.e[c] = {v.x, v.y};
+    }
+}
+
+// Link of the step from x + d in direction s * nu (s = +-1):
+// U_nu(x + d) for s = +1, U_nu(x + d - nu)^dag for s = -1.
+template <class T>
+__device__ __forceinline__ void step_link(const LinkGeo &g, const typename Vec2T<T>::t *L, const int (&x)[4],
+                                          const int (&d)[4], int nu, int s, Mat3<T> &U)
+{
+    int e[4] = {d[0], d[1], d[2], d[3]};
+    if (s < 0) e[nu] -= 1;
+    int par, idx;
+    site_of(g, x, e[0], e[1], e[2], e[3], par, idx);
+    load_link_soa<T>(L, nu, par, idx, g.Vh, U);
+    if (s < 0) mat_dag(U);
+}
+
+// U_mu(x + d)^dag (a step -mu from x + d + mu)
+template <class T>
+__device__ __forceinline__ void back_mu(const LinkGeo &g, const typename Vec2T<T>::t *L, const int (&x)[4],
+                                        const int (&d)[4], int mu, Mat3<T> &U)
+{
+    int par, idx;
+    site_of(g, x, d[0], d[1], d[2], d[3], par, idx);
+    load_link_soa<T>(L, mu, par, idx, g.Vh, U);
+    mat_dag(U);
+}
+
+__device__ __forceinline__ void coords_of(const LinkGeo &g, int P, int i, int (&x)[4])
+{
+    const int n0h = g.N[0] >> 1;
+    int r = i / n0h;
+    const int x0h = i - r * n0h;
+    x[1] = r % g.N[1];
+    r /= g.N[1];
+    x[2] = r % g.N[2];
+    x[3] = r / g.N[2];
+    x[0] = 2 * x0h + ((x[1] + x[2] + x[3] + P) & 1);
+}
+
+// Staple sum A of the link U_mu(x) (see the file header).  Prefix sharing
+// per (nu, s): P1 = step +s nu from x+mu, Q = P1 U_mu(x+s nu)^dag,
+// E = step from x+s nu back to x; plaquette = Q E, rectangle (b) =
+// Q U_mu(x-mu+s nu)^dag (step -s nu) U_mu(x-mu), rectangles (a) and (c)
+// end in E, so c0 Q + c1 (a' + c') is multiplied by E once.
+template <class T>
+__device__ void staple_sum_dev(const LinkGeo &g, const typename Vec2T<T>::t *L, const int (&x)[4], int mu,
+                               Mat3<T> &A)
+{
+#pragma unroll
+    for (int k = 0; k < 9; ++k) A.e[k] = {T(0), T(0)};
+    const T c0 = T(kSymC0), c1 = T(kSymC1);
+#pragma unroll 1
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+#pragma unroll 1
+        for (int s = -1; s <= 1; s += 2) {
+            int d[4] = {0, 0, 0, 0};
+            Mat3<T> P1, Q, W, t1, t2;
+            // P1 = step(x+mu, s nu)
+            d[mu] = 1;
+            step_link<T>(g, L, x, d, nu, s, P1);
+            // Q = P1 U_mu(x + s nu)^dag
+            d[mu] = 0;
+            d[nu] = s;
+            back_mu<T>(g, L, x, d, mu, t1);
+            mat_mul(P1, t1, Q);
+            // rectangle (b): Q U_mu(x - mu + s nu)^dag step(x-mu+s nu, -s nu) U_mu(x - mu)
+            d[mu] = -1;
+            back_mu<T>(g, L, x, d, mu, t1);
+            mat_mul(Q, t1, t2);
+            step_link<T>(g, L, x, d, nu, -s, t1);
+            mat_mul(t2, t1, W);
+            d[nu] = 0;
+            {
+                int par, idx;
+                site_of(g, x, d[0], d[1], d[2], d[3], par, idx);
+                load_link_soa<T>(L, mu, par, idx, g.Vh, t1);
+            }
+            mat_mul(W, t1, t2);
+            mat_axpy(c1, t2, A);
+            // W = c0 Q + c1 (a' + c'), multiplied by E below
+#pragma unroll
+            for (int k = 0; k < 9; ++k) W.e[k] = {c0 * Q.e[k].re, c0 * Q.e[k].im};
+            // c' = P1 step(x+mu+s nu, s nu) U_mu(x + 2 s nu)^dag step(x + 2 s nu, -s nu)
+            d[mu] = 1;
+            d[nu] = s;
+            step_link<T>(g, L, x, d, nu, s, t1);
+            mat_mul(P1, t1, t2);
+            d[mu] = 0;
+            d[nu] = 2 * s;
+            back_mu<T>(g, L, x, d, mu, t1);
+            mat_mul(t2, t1, Q);
+            step_link<T>(g, L, x, d, nu, -s, t1);
+            mat_mul(Q, t1, t2);
+            mat_axpy(c1, t2, W);
+            // a' = U_mu(x + mu) step(x + 2 mu, s nu) U_mu(x + mu + s nu)^dag U_mu(x + s nu)^dag
+            d[nu] = 0;
+            d[mu] = 1;
+            {
+                int par, idx;
+                site_of(g, x, d[0], d[1], d[2], d[3], par, idx);
+                load_link_soa<T>(L, mu, par, idx, g.Vh, P1);
+            }
+            d[mu] = 2;
+            step_link<T>(g, L, x, d, nu, s, t1);
+            mat_mul(P1, t1, t2);
+            d[mu] = 1;
+            d[nu] = s;
+            back_mu<T>(g, L, x, d, mu, t1);
+            mat_mul(t2, t1, Q);
+            d[mu] = 0;
+            back_mu<T>(g, L, x, d, mu, t1);
+            mat_mul(Q, t1, t2);
+            mat_axpy(c1, t2, W);
+            // E = step(x + s nu, -s nu);  A += W E
+            step_link<T>(g, L, x, d, nu, -s, t1);
+            mat_mul(W, t1, t2);
+            mat_axpy(T(1), t2, A);
+        }
+    }
+}
+
+// 8 reals <-> traceless Hermitian matrix
+template <class T>
+__device__ __forceinline__ void herm_unpack(const T (&h)[8], Mat3<T> &H)
+{
+    H.e[0] = {h[0], T(0)};
+    H.e[4] = {h[1], T(0)};
+    H.e[8] = {-h[0] - h[1], T(0)};
+    H.e[1] = {h[2], h[3]};
+    H.e[3] = {h[2], -h[3]};
+    H.e[2] = {h[4], h[5]};
+    H.e[6] = {h[4], -h[5]};
+    H.e[5] = {h[6], h[7]};
+    H.e[7] = {h[6], -h[7]};
+}
+
+template <class T>
+__device__ __forceinline__ const T *mom_ptr(const T *m, int mu, int P, int Vh)
+{
+    return m + (size_t)((mu * 2 + P) * 8) * Vh;
+}
+
+// H_mu(x) -= eps F_mu(x) for every link.  Thread = (mu, parity, site).
+template <class T>
+__global__ void __launch_bounds__(kGaugeThreads)
+    k_gauge_mom_update(LinkGeo g, const typename Vec2T<T>::t *__restrict__ L, T *__restrict__ mom, T beta6, T eps)
+{
+    const int Vh = g.Vh;
+    const long t = blockIdx.x * (long)kGaugeThreads + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    const int i = (int)(t % Vh);
+    const int mp = (int)(t / Vh);  // mu * 2 + P
+    const int mu = mp >> 1, P = mp & 1;
+    int x[4];
+    coords_of(g, P, i, x);
+    Mat3<T> A, U, M;
+    staple_sum_dev<T>(g, L, x, mu, A);
+    load_link_soa<T>(L, mu, P, i, Vh, U);
+    mat_mul(U, A, M);
+    // F = -(i beta/6)(M - M^dag): F_ij = (beta/6) * (i (conj(M_ji) - M_ij))
+    //   re F_ij = (beta/6) (M_ij.im + M_ji.im),  im F_ij = (beta/6) (M_ji.re - M_ij.re)
+    T f[8];
+    const T d0 = beta6 * (M.e[0].im + M.e[0].im), d1 = beta6 * (M.e[4].im + M.e[4].im),
+            d2 = beta6 * (M.e[8].im + M.e[8].im);
+    const T tr = (d0 + d1 + d2) / T(3);
+    f[0] = d0 - tr;
+    f[1] = d1 - tr;
+    f[2] = beta6 * (M.e[1].im + M.e[3].im);
+    f[3] = beta6 * (M.e[3].re - M.e[1].re);
+    f[4] = beta6 * (M.e[2].im + M.e[6].im);
+    f[5] = beta6 * (M.e[6].re - M.e[2].re);
+    f[6] = beta6 * (M.e[5].im + M.e[7].im);
+    f[7] = beta6 * (M.e[7].re - M.e[5].re);
+    T *h = mom + (size_t)(mp * 8) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[(size_t)k * Vh] = fma(-eps, f[k], h[(size_t)k * Vh]);
+}
+
+// E = exp(i t H): Z = i t H scaled by 2^-k to 1-norm <= 1/4, Taylor series of
+// degree 16 (FP64) or 9 (FP32), squared k times.
+template <class T>
+__device__ __forceinline__ void exp_iH_dev(const Mat3<T> &H, T t, Mat3<T> &E)
+{
+    T nrm = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        T c = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) c += sqrt(H.e[i * 3 + j].re * H.e[i * 3 + j].re + H.e[i * 3 + j].im * H.e[i * 3 + j].im);
+        nrm = c > nrm ? c : nrm;
+    }
+    nrm *= fabs(t);
+    int k = 0;
+    while (nrm > T(0.25) && k < 60) {
+        nrm *= T(0.5);
+        ++k;
+    }
+    T sc = t;
+    for (int q = 0; q < k; ++q) sc *= T(0.5);
+    Mat3<T> Z;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) Z.e[q] = {-sc * H.e[q].im, sc * H.e[q].re};
+    // Horner: E = I + Z (I + Z/2 (I + Z/3 (... (I + Z/n))))
+    constexpr int deg = sizeof(T) == 8 ? 16 : 9;
+    Mat3<T> R;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) R.e[q] = {(q % 4 == 0) ? T(1) : T(0), T(0)};
+#pragma unroll 1
+    for (int n = deg; n >= 1; --n) {
+        Mat3<T> ZR;
+        mat_mul(Z, R, ZR);
+        const T inv = T(1) / T(n);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) R.e[q] = {((q % 4 == 0) ? T(1) : T(0)) + inv * ZR.e[q].re, inv * ZR.e[q].im};
+    }
+#pragma unroll 1
+    for (int q = 0; q < k; ++q) {
+        Mat3<T> S2;
+        mat_mul(R, R, S2);
+        R = S2;
+    }
+    E = R;
+}
+
+// U_mu(x) <- exp(i eps H_mu(x)) U_mu(x) for every link.
+template <class T>
+__global__ void __launch_bounds__(kGaugeThreads)
+    k_gauge_link_update(int Vh, typename Vec2T<T>::t *__restrict__ L, const T *__restrict__ mom, T eps)
+{
+    const long t = blockIdx.x * (long)kGaugeThreads + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    const int i = (int)(t % Vh);
+    const int mp = (int)(t / Vh);
+    T h[8];
+    const T *hp = mom + (size_t)(mp * 8) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = hp[(size_t)k * Vh];
+    Mat3<T> H, E, U, R;
+    herm_unpack(h, H);
+    exp_iH_dev(H, eps, E);
+    typename Vec2T<T>::t *p = L + (size_t)(mp * 9) * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const typename Vec2T<T>::t v = p[(size_t)c * Vh];
+        U.e[c] = {v.x, v.y};
+    }
+    mat_mul(E, U, R);
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        typename Vec2T<T>::t v;
+        v.x = R.e[c].re;
+        v.y = R.e[c].im;
+        p[(size_t)c * Vh] = v;
+    }
+}
+
+// U_dir(x + d)
+template <class T>
+__device__ __forceinline__ void link_at(const LinkGeo &g, const typename Vec2T<T>::t *L, const int (&x)[4], int d0,
+                                        int d1, int d2, int d3, int dir, Mat3<T> &U)
+{
+    int par, idx;
+    site_of(g, x, d0, d1, d2, d3, par, idx);
+    load_link_soa<T>(L, dir, par, idx, g.Vh, U);
+}
+
+// Per-block partial of sum_x [c0 sum_{mu<nu} Re Tr P + c1 sum_{mu!=nu} Re Tr R]
+// (FP64 accumulation); thread = site (parity, half index):
+//   P = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag
+//   R = U_mu(x) U_mu(x+mu) U_nu(x+2mu) U_mu(x+mu+nu)^dag U_mu(x+nu)^dag U_nu(x)^dag
+template <class T>
+__global__ void __launch_bounds__(kGaugeThreads)
+    k_gauge_action_part(LinkGeo g, const typename Vec2T<T>::t *__restrict__ L, double *part)
+{
+    __shared__ double s_red[kGaugeThreads / 32];
+    const long t = blockIdx.x * (long)kGaugeThreads + threadIdx.x;
+    double acc = 0.0;
+    if (t < 2L * g.Vh) {
+        const int P = (int)(t / g.Vh), i = (int)(t % g.Vh);
+        int x[4];
+        coords_of(g, P, i, x);
+        double sp = 0.0, sr = 0.0;
+#pragma unroll 1
+        for (int mu = 0; mu < 4; ++mu)
+#pragma unroll 1
+            for (int nu = 0; nu < 4; ++nu) {
+                if (nu == mu) continue;
+                int em[4] = {0, 0, 0, 0}, en[4] = {0, 0, 0, 0};
+                em[mu] = 1;
+                en[nu] = 1;
+                Mat3<T> u, b, c, d;
+                link_at<T>(g, L, x, 0, 0, 0, 0, mu, u);
+                if (mu < nu) {
+                    link_at<T>(g, L, x, em[0], em[1], em[2], em[3], nu, b);
+                    mat_mul(u, b, c);
+                    link_at<T>(g, L, x, en[0], en[1], en[2], en[3], mu, b);
+                    mat_mul_dag(c, b, d);
+                    link_at<T>(g, L, x, 0, 0, 0, 0, nu, b);
+                    mat_mul_dag(d, b, c);
+                    sp += (double)c.e[0].re + (double)c.e[4].re + (double)c.e[8].re;
+                }
+                link_at<T>(g, L, x, em[0], em[1], em[2], em[3], mu, b);
+                mat_mul(u, b, c);
+                link_at<T>(g, L, x, 2 * em[0], 2 * em[1], 2 * em[2], 2 * em[3], nu, b);
+                mat_mul(c, b, d);
+                link_at<T>(g, L, x, em[0] + en[0], em[1] + en[1], em[2] + en[2], em[3] + en[3], mu, b);
+                mat_mul_dag(d, b, c);
+                link_at<T>(g, L, x, en[0], en[1], en[2], en[3], mu, b);
+                mat_mul_dag(c, b, d);
+                link_at<T>(g, L, x, 0, 0, 0, 0, nu, b);
+                mat_mul_dag(d, b, c);
+                sr += (double)c.e[0].re + (double)c.e[4].re + (double)c.e[8].re;
+            }
+        acc = kSymC0 * sp + kSymC1 * sr;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < kGaugeThreads / 32; ++k) s += s_red[k];
+        part[blockIdx.x] = s;
+    }
+}
+
+// Per-block partial of (1/2) sum Tr H^2.
+template <class T>
+__global__ void __launch_bounds__(kGaugeThreads) k_mom_energy_part(int Vh, const T *__restrict__ mom, double *part)
+{
+    __shared__ double s_red[kGaugeThreads / 32];
+    const long t = blockIdx.x * (long)kGaugeThreads + threadIdx.x;
+    double acc = 0.0;
+    if (t < 8L * Vh) {
+        const int i = (int)(t % Vh), mp = (int)(t / Vh);
+        const T *hp = mom + (size_t)(mp * 8) * Vh + i;
+        double h[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) h[k] = (double)hp[(size_t)k * Vh];
+        const double d2 = -h[0] - h[1];
+        acc = 0.5 * (h[0] * h[0] + h[1] * h[1] + d2 * d2 +
+                     2.0 * (h[2] * h[2] + h[3] * h[3] + h[4] * h[4] + h[5] * h[5] + h[6] * h[6] + h[7] * h[7]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xFFFFFFFFu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int k = 0; k < kGaugeThreads / 32; ++k) s += s_red[k];
+        part[blockIdx.x] = s;
+    }
+}
+
+// One block: sum of part[0..n) in a fixed order.
+__global__ void __launch_bounds__(256) k_gauge_sum_ordered(const double *__restrict__ part, int n, double *out)
+{
+    __shared__ double s_red[8];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += 256) s += part[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tot = 0.0;
+        for (int k = 0; k < 8; ++k) tot += s_red[k];
+        *out = tot;
+    }
+}
+
+// ------------------------------------------------------------------ format conversions
+// canonical host momenta [4][V][3][3] complex128 (staged on the device) -> 8 reals SoA (FP64 and FP32)
+__global__ void k_mom_from_canonical(LinkGeo g, const double2 *__restrict__ src, double *m64, float *m32, int *bad,
+                                     long V)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= 4 * V) return;
+    const int mu = (int)(t / V);
+    const long lex = t - (long)mu * V;
+    int x[4];
+    long r = lex;
+    for (int m = 0; m < 4; ++m) {
+        x[m] = (int)(r % g.N[m]);
+        r /= g.N[m];
+    }
+    const int P = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const int idx = (int)(lex >> 1);
+    const double2 *h = src + t * 9;
+    // Hermitian and traceless to 1e-12 relative, else rejected
+    double scale = 0.0;
+    for (int c = 0; c < 9; ++c) scale = fmax(scale, fmax(fabs(h[c].x), fabs(h[c].y)));
+    const double tol = 1e-12 * fmax(scale, 1e-300);
+    bool ok = isfinite(scale) && fabs(h[0].y) <= tol && fabs(h[4].y) <= tol && fabs(h[8].y) <= tol &&
+              fabs(h[0].x + h[4].x + h[8].x) <= 3 * tol;
+    const int off[3][2] = {{1, 3}, {2, 6}, {5, 7}};
+    for (int q = 0; q < 3; ++q)
+        ok = ok && fabs(h[off[q][0]].x - h[off[q][1]].x) <= tol && fabs(h[off[q][0]].y + h[off[q][1]].y) <= tol;
+    if (!ok) atomicOr(bad, 1);
+    const double v[8] = {h[0].x, h[4].x, h[1].x, h[1].y, h[2].x, h[2].y, h[5].x, h[5].y};
+    for (int k = 0; k < 8; ++k) {
+        const size_t o = (size_t)((mu * 2 + P) * 8 + k) * g.Vh + idx;
+        m64[o] = v[k];
+        m32[o] = (float)v[k];
+    }
+}
+
+template <class T>
+__global__ void k_mom_to_canonical(LinkGeo g, const T *__restrict__ m, double2 *dst, long V)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= 4 * V) return;
+    const int mu = (int)(t / V);
+    const long lex = t - (long)mu * V;
+    int x[4];
+    long r = lex;
+    for (int q = 0; q < 4; ++q) {
+        x[q] = (int)(r % g.N[q]);
+        r /= g.N[q];
+    }
+    const int P = (x[0] + x[1] + x[2] + x[3]) & 1;
+    const int idx = (int)(lex >> 1);
+    double h[8];
+    for (int k = 0; k < 8; ++k) h[k] = (double)m[(size_t)((mu * 2 + P) * 8 + k) * g.Vh + idx];
+    double2 *o = dst + t * 9;
+    o[0] = make_double2(h[0], 0.0);
+    o[4] = make_double2(h[1], 0.0);
+    o[8] = make_double2(-h[0] - h[1], 0.0);
+    o[1] = make_double2(h[2], h[3]);
+    o[3] = make_double2(h[2], -h[3]);
+    o[2] = make_double2(h[4], h[5]);
+    o[6] = make_double2(h[4], -h[5]);
+    o[5] = make_double2(h[6], h[7]);
+    o[7] = make_double2(h[6], -h[7]);
+}
+
+// FP64 <-> FP32 copies of links (SoA, same layout) and momenta
+__global__ void k_links_f64_to_f32(const double2 *__restrict__ a, float2 *b, long n)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = make_float2((float)a[t].x, (float)a[t].y);
+}
+__global__ void k_links_f32_to_f64(const float2 *__restrict__ a, double2 *b, long n)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = make_double2((double)a[t].x, (double)a[t].y);
+}
+__global__ void k_mom_f64_to_f32(const double *__restrict__ a, float *b, long n)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (float)a[t];
+}
+__global__ void k_mom_f32_to_f64(const float *__restrict__ a, double *b, long n)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t < n) b[t] = (double)a[t];
+}
+
+static LinkGeo link_geo(const lqcd_ctx *c)
+{
+    LinkGeo g;
+    for (int m = 0; m < 4; ++m) g.N[m] = c->dims[m];
+    g.Vh = (int)c->Vh;
+    return g;
+}
+
+static inline unsigned nblocks(long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ------------------------------------------------------------------ copies and staleness
+// links: the FP64 SoA (lnk_nat) is the master; an FP32 MD step works on lnk_f18
+// and makes it the newest copy; FP64 MD steps update lnk_nat and leave every
+// derived format stale until links_ready rebuilds them.
+static int links_to_prec(lqcd_ctx *c, int prec)
+{
+    const long n = 72L * (long)c->Vh;
+    if (prec == LQCD_PREC_FP32) {
+        if (c->md_links_newest == LQCD_PREC_FP64 && c->links_derived_stale) {
+            k_links_f64_to_f32<<<nblocks(n, 256), 256, 0, c->stream>>>(c->lnk_nat.as<double2>(), c->lnk_f18.as<float2>(), n);
+            LQCD_CUDA(cudaGetLastError());
+            c->launches += 1;
+        }
+    } else if (c->md_links_newest == LQCD_PREC_FP32) {
+        k_links_f32_to_f64<<<nblocks(n, 256), 256, 0, c->stream>>>(c->lnk_f18.as<float2>(), c->lnk_nat.as<double2>(), n);
+        LQCD_CUDA(cudaGetLastError());
+        c->launches += 1;
+        c->md_links_newest = LQCD_PREC_FP64;
+        c->links_derived_stale = true;
+    }
+    return LQCD_OK;
+}
+
+static int mom_to_prec(lqcd_ctx *c, int prec)
+{
+    if (c->mom_newest == prec) return LQCD_OK;
+    const long n = 64L * (long)c->Vh;
+    if (prec == LQCD_PREC_FP32)
+        k_mom_f64_to_f32<<<nblocks(n, 256), 256, 0, c->stream>>>(c->mom64.as<double>(), c->mom32.as<float>(), n);
+    else
+        k_mom_f32_to_f64<<<nblocks(n, 256), 256, 0, c->stream>>>(c->mom32.as<float>(), c->mom64.as<double>(), n);
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += 1;
+    c->mom_newest = prec;
+    return LQCD_OK;
+}
+
+static int check_md(lqcd_ctx *c, int prec)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (!c->mom64.ptr) return fail(LQCD_ESTATE, "no momenta uploaded");
+    if (prec != LQCD_PREC_FP64 && prec != LQCD_PREC_FP32) return fail(LQCD_EINVAL, "MD precision must be FP64 or FP32");
+    return LQCD_OK;
+}
+
+static void launch_mom_update(lqcd_ctx *c, int prec, double beta, double eps)
+{
+    const LinkGeo g = link_geo(c);
+    const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
+    if (prec == LQCD_PREC_FP64)
+        k_gauge_mom_update<double><<<nb, kGaugeThreads, 0, c->stream>>>(g, c->lnk_nat.as<double2>(), c->mom64.as<double>(),
+                                                                        beta / 6.0, eps);
+    else
+        k_gauge_mom_update<float><<<nb, kGaugeThreads, 0, c->stream>>>(g, c->lnk_f18.as<float2>(), c->mom32.as<float>(),
+                                                                       (float)(beta / 6.0), (float)eps);
+    c->launches += 1;
+}
+
+static void launch_link_update(lqcd_ctx *c, int prec, double eps)
+{
+    const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
+    if (prec == LQCD_PREC_FP64) {
+        k_gauge_link_update<double><<<nb, kGaugeThreads, 0, c->stream>>>((int)c->Vh, c->lnk_nat.as<double2>(),
+                                                                         c->mom64.as<double>(), eps);
+        c->md_links_newest = LQCD_PREC_FP64;
+    } else {
+        k_gauge_link_update<float><<<nb, kGaugeThreads, 0, c->stream>>>((int)c->Vh, c->lnk_f18.as<float2>(),
+                                                                        c->mom32.as<float>(), (float)eps);
+        c->md_links_newest = LQCD_PREC_FP32;
+    }
+    c->links_derived_stale = true;
+    c->launches += 1;
+}
+
+static int prepare(lqcd_ctx *c, int prec)
+{
+    int st;
+    if ((st = links_to_prec(c, prec))) return st;
+    return mom_to_prec(c, prec);
+}
+
+}  // namespace lqcd
+
+using namespace lqcd;
+
+extern "C" {
+
+int lqcd_mom_upload(lqcd_ctx *c, const double *H, size_t n)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    const size_t want = 4 * c->V * 18;
+    if (!H || n != want) return fail(LQCD_EINVAL, "momenta: expected 4*V*18 doubles");
+    int st;
+    if ((st = c->mom64.ensure(64 * c->Vh * sizeof(double))) || (st = c->mom32.ensure(64 * c->Vh * sizeof(float))))
+        return st;
+    DevBuf stage;
+    if ((st = stage.ensure(want * sizeof(double) + 16))) return st;
+    int *bad = (int *)((char *)stage.ptr + want * sizeof(double));
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage.ptr, H, want * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        k_mom_from_canonical<<<nblocks(4L * (long)c->V, 256), 256, 0, c->stream>>>(
+            link_geo(c), stage.as<double2>(), c->mom64.as<double>(), c->mom32.as<float>(), bad, (long)c->V);
+        e = cudaGetLastError();
+    }
+    int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    stage.release();
+    if (e != cudaSuccess) return cuda_fail(e, "momenta upload");
+    c->launches += 1;
+    c->mom_newest = LQCD_PREC_FP64;  // both copies written; FP64 is the exact one
+    if (hbad) {
+        c->mom64.release();
+        c->mom32.release();
+        return fail(LQCD_EINVAL, "momenta must be finite, Hermitian and traceless");
+    }
+    return LQCD_OK;
+}
+
+int lqcd_mom_download(lqcd_ctx *c, double *H, size_t n)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    const size_t want = 4 * c->V * 18;
+    if (!H || n != want) return fail(LQCD_EINVAL, "momenta: expected 4*V*18 doubles");
+    if (!c->mom64.ptr) return fail(LQCD_ESTATE, "no momenta uploaded");
+    DevBuf stage;
+    int st;
+    if ((st = stage.ensure(want * sizeof(double)))) return st;
+    const unsigned nb = nblocks(4L * (long)c->V, 256);
+    if (c->mom_newest == LQCD_PREC_FP32)
+        k_mom_to_canonical<float><<<nb, 256, 0, c->stream>>>(link_geo(c), c->mom32.as<float>(), stage.as<double2>(), (long)c->V);
+    else
+        k_mom_to_canonical<double><<<nb, 256, 0, c->stream>>>(link_geo(c), c->mom64.as<double>(), stage.as<double2>(), (long)c->V);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(H, stage.ptr, want * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    stage.release();
+    if (e != cudaSuccess) return cuda_fail(e, "momenta download");
+    c->launches += 1;
+    return LQCD_OK;
+}
+
+int lqcd_gauge_mom_update(lqcd_ctx *c, int prec, double beta, double eps)
+{
+    int st;
+    if ((st = check_md(c, prec)) || (st = prepare(c, prec))) return st;
+    launch_mom_update(c, prec, beta, eps);
+    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+
+int lqcd_gauge_link_update(lqcd_ctx *c, int prec, double eps)
+{
+    int st;
+    if ((st = check_md(c, prec)) || (st = prepare(c, prec))) return st;
+    launch_link_update(c, prec, eps);
+    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+
+int lqcd_gauge_md_steps(lqcd_ctx *c, int prec, double beta, double eps, int n_steps)
+{
+    int st;
+    if ((st = check_md(c, prec)) || (st = prepare(c, prec))) return st;
+    if (n_steps < 0) return fail(LQCD_EINVAL, "n_steps must be >= 0");
+    for (int k = 0; k < n_steps; ++k) {
+        launch_mom_update(c, prec, beta, eps);
+        launch_link_update(c, prec, eps);
+    }
+    LQCD_CUDA(cudaGetLastError());
+    LQCD_CUDA(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+
+int lqcd_gauge_action(lqcd_ctx *c, int prec, double beta, double *S)
+{
+    if (!c || !S) return fail(LQCD_EINVAL, "NULL argument");
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (prec != LQCD_PREC_FP64 && prec != LQCD_PREC_FP32) return fail(LQCD_EINVAL, "precision must be FP64 or FP32");
+    int st;
+    if ((st = links_to_prec(c, prec))) return st;
+    const unsigned nb = nblocks(2L * (long)c->Vh, kGaugeThreads);
+    if ((st = c->md_part.ensure(((size_t)nb + 1) * sizeof(double)))) return st;
+    double *part = c->md_part.as<double>();
+    if (prec == LQCD_PREC_FP64)
+        k_gauge_action_part<double><<<nb, kGaugeThreads, 0, c->stream>>>(link_geo(c), c->lnk_nat.as<double2>(), part);
+    else
+        k_gauge_action_part<float><<<nb, kGaugeThreads, 0, c->stream>>>(link_geo(c), c->lnk_f18.as<float2>(), part);
+    k_gauge_sum_ordered<<<1, 256, 0, c->stream>>>(part, (int)nb, part + nb);
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += 2;
+    LQCD_CUDA(cudaMemcpyAsync(c->h_pinned_d, part + nb, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LQCD_CUDA(cudaStreamSynchronize(c->stream));
+    *S = -(beta / 3.0) * c->h_pinned_d[0];
+    return LQCD_OK;
+}
+
+int lqcd_mom_energy(lqcd_ctx *c, int prec, double *K)
+{
+    int st;
+    if (!K) return fail(LQCD_EINVAL, "NULL argument");
+    if ((st = check_md(c, prec)) || (st = mom_to_prec(c, prec))) return st;
+    const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
+    if ((st = c->md_part.ensure(((size_t)nb + 1) * sizeof(double)))) return st;
+    double *part = c->md_part.as<double>();
+    if (prec == LQCD_PREC_FP64)
+        k_mom_energy_part<double><<<nb, kGaugeThreads, 0, c->stream>>>((int)c->Vh, c->mom64.as<double>(), part);
+    else
+        k_mom_energy_part<float><<<nb, kGaugeThreads, 0, c->stream>>>((int)c->Vh, c->mom32.as<float>(), part);
+    k_gauge_sum_ordered<<<1, 256, 0, c->stream>>>(part, (int)nb, part + nb);
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += 2;
+    LQCD_CUDA(cudaMemcpyAsync(c->h_pinned_d, part + nb, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    LQCD_CUDA(cudaStreamSynchronize(c->stream));
+    *K = c->h_pinned_d[0];
+    return LQCD_OK;
+}
+
+}  // extern "C"

@@ -152,6 +152,12 @@ struct lqcd_ctx {
     lqcd::DevBuf io_a, io_b;  // device staging of host spinors for where = 0
     lqcd::DevBuf rat_x;       // shifted solutions of a rational application [n][3][Vh] double2
     lqcd::DevBuf rat_part;    // per-block partials of its action (+ the total)
+    // gauge molecular dynamics (gauge.cu): momenta as 8 reals per link, SoA [4][2][8][Vh]
+    lqcd::DevBuf mom64, mom32;
+    lqcd::DevBuf md_part;     // partials of the action / kinetic energy (+ the total)
+    int md_links_newest = 0;  // LQCD_PREC_FP64: lnk_nat holds the newest links; FP32: lnk_f18
+    bool links_derived_stale = false;  // MD moved the links: derived formats need a rebuild
+    int mom_newest = 0;       // which momentum copy is current
     lqcd::Workspace ws;
     lqcd::Workspace ws32;                  // FP32 phase of a hybrid mixed-precision solve
     std::vector<lqcd::Workspace> ref_ws;   // per-shift refinement jobs
@@ -177,6 +183,9 @@ int upload_links(lqcd_ctx *c, const double *host, size_t n);
 bool staged_deo_ready();
 bool staged_solver_ready();
 bool staged_active(const lqcd_ctx *c);   // staged option on and the staged link stream built
+// LQCD_ESTATE before an upload; otherwise makes every link format current
+// after molecular-dynamics updates (FP32 copy promoted, formats rebuilt).
+int links_ready(lqcd_ctx *c);
 // LQCD_ETIMEOUT (and clears the word) if a stand-alone staged D_eo of this
 // context recorded a stall; synchronises the context's stream.
 int deo_check_stall(lqcd_ctx *c);

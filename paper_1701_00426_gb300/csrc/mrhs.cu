@@ -314,7 +314,7 @@ static void launch_deo2_R(const MrhsArgs &A, int R, unsigned nb, cudaStream_t s)
 
 int deo_mrhs_launch(lqcd_ctx *c, int P, int n, int recon, const void *in, void *out, cudaStream_t s)
 {
-    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (int lr = links_ready(c)) return lr;
     if (P != 0 && P != 1) return fail(LQCD_EINVAL, "out_parity must be 0 or 1");
     if (n < 1 || n > kMaxRhs) return fail(LQCD_EINVAL, "n_rhs must be in 1..16");
     if (!in || !out || in == out) return fail(LQCD_EINVAL, "bad spinor pointers");
@@ -560,7 +560,7 @@ int cg_solve_mrhs(lqcd_ctx *c, double mass, double sigma, int n, double tol, con
                   lqcd_solve_info *info)
 {
     const auto t0 = std::chrono::steady_clock::now();
-    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (int lr = links_ready(c)) return lr;
     if (n < 1 || n > kMaxRhs) return fail(LQCD_EINVAL, "n_rhs must be in 1..16");
     if (!b_host || !x_host) return fail(LQCD_EINVAL, "NULL argument");
     if (!(tol > 0) || !(sigma >= 0) || !std::isfinite(sigma) || !std::isfinite(mass) || !(mass * mass + sigma > 0))

@@ -57,7 +57,7 @@ extern "C" int lqcd_deo_apply_host_noalloc(lqcd_ctx *c, int out_parity, const do
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     if (!in || !out) return fail(LQCD_EINVAL, "NULL host buffer");
     if (out_parity != 0 && out_parity != 1) return fail(LQCD_EINVAL, "out_parity must be 0 or 1");
-    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (int lr = links_ready(c)) return lr;
     if ((long)c->Vh > kNoAllocMaxVh)
         return fail(LQCD_EINVAL, "lattice too large for lqcd_deo_apply_host_noalloc: V/2 = " +
                                      std::to_string(c->Vh) + " exceeds its fixed staging of " +

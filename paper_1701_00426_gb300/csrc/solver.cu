@@ -1077,7 +1077,7 @@ int job_init_prec(JobRun &J, lqcd_ctx *c, Workspace *W, int prec, double mass, c
                   double tol, const double2 *b, double2 *x)
 {
     int st = validate_solve(c, mass, shifts, n_shift, tol);
-    if (st) return st;
+    if (st || (st = links_ready(c))) return st;
     J.c = c;
     J.vp = prec == LQCD_PREC_FP64 || prec == LQCD_PREC_FP64_NATIVE ? VP_DF : VP_F32;
     J.lf = link_fmt_for(c, J.vp == VP_DF ? LQCD_PREC_FP64 : prec, &J.links);

@@ -48,6 +48,8 @@ EXPORTED = [
     "lqcd_mscg_solve_packed", "lqcd_profile_iteration",
     "lqcd_serve_create", "lqcd_serve_register_field", "lqcd_serve_submit", "lqcd_serve_poll",
     "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy", "lqcd_serve_set_opts",
+    "lqcd_mom_upload", "lqcd_mom_download", "lqcd_gauge_mom_update", "lqcd_gauge_link_update",
+    "lqcd_gauge_md_steps", "lqcd_gauge_action", "lqcd_mom_energy",
 ]
 
 
@@ -142,6 +144,13 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_serve_stats_get": (ctypes.c_int, [vp, ctypes.POINTER(lqcd_serve_stats)]),
         "lqcd_serve_destroy": (None, [vp]),
         "lqcd_serve_set_opts": (ctypes.c_int, [vp, ctypes.POINTER(lqcd_opts)]),
+        "lqcd_mom_upload": (ctypes.c_int, [vp, vp, sz]),
+        "lqcd_mom_download": (ctypes.c_int, [vp, vp, sz]),
+        "lqcd_gauge_mom_update": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double]),
+        "lqcd_gauge_link_update": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double]),
+        "lqcd_gauge_md_steps": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
+        "lqcd_gauge_action": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, dp]),
+        "lqcd_mom_energy": (ctypes.c_int, [vp, ctypes.c_int, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -251,6 +260,35 @@ class Context:
         u = np.empty((4, self.V, 3, 3), np.complex128)
         check(self.lib.lqcd_links_download(self.h, _ptr(u), u.size * 2))
         return u
+
+    # ------------------------------------------------- gauge molecular dynamics
+    def mom_upload(self, H: np.ndarray):
+        h = _c128(H, (4, self.V, 3, 3))
+        check(self.lib.lqcd_mom_upload(self.h, _ptr(h), h.size * 2))
+
+    def mom_download(self) -> np.ndarray:
+        h = np.empty((4, self.V, 3, 3), np.complex128)
+        check(self.lib.lqcd_mom_download(self.h, _ptr(h), h.size * 2))
+        return h
+
+    def gauge_mom_update(self, beta: float, eps: float, prec: int = 0):
+        check(self.lib.lqcd_gauge_mom_update(self.h, int(prec), float(beta), float(eps)))
+
+    def gauge_link_update(self, eps: float, prec: int = 0):
+        check(self.lib.lqcd_gauge_link_update(self.h, int(prec), float(eps)))
+
+    def gauge_md_steps(self, beta: float, eps: float, n_steps: int = 1, prec: int = 0):
+        check(self.lib.lqcd_gauge_md_steps(self.h, int(prec), float(beta), float(eps), int(n_steps)))
+
+    def gauge_action(self, beta: float, prec: int = 0) -> float:
+        s = ctypes.c_double()
+        check(self.lib.lqcd_gauge_action(self.h, int(prec), float(beta), ctypes.byref(s)))
+        return s.value
+
+    def mom_energy(self, prec: int = 0) -> float:
+        k = ctypes.c_double()
+        check(self.lib.lqcd_mom_energy(self.h, int(prec), ctypes.byref(k)))
+        return k.value
 
     # --------------------------------------------------------------- D_eo
     def deo_apply(self, out_parity: int, inp: np.ndarray) -> np.ndarray:
