@@ -485,6 +485,40 @@ class L2Flush:
         self.r.sum()
 
 
+# Table md-norm (gauge part of the MD step, ns per lattice site), 32^4 column;
+# other hardware, quoted as context only.
+PAPER_MD_NS_32 = {"P100": 51.72, "GK210": 201.82, "E5-2697v4": 944.40, "E5-2630v3": 1719.97}
+
+
+def gauge_md_bench(lqcd, inputs, L=32, beta=5.5, eps=0.01):
+    """One gauge MD step (momentum update with the tree-level Symanzik force,
+    then the link update) per lattice site on L^4, FP32 and FP64, as in
+    Table md-norm; flop count per site from the kernels' SU(3) products."""
+    dims = (L,) * 4
+    V = L ** 4
+    U = inputs.random_links(dims)
+    H = inputs.random_momenta(dims)
+    ctx = lqcd.Context(dims)
+    ctx.links_upload(U)
+    ctx.mom_upload(H)
+    del U, H
+    # per link: 67 SU(3) products in the staple sum, 1 for U A, about 16 in the
+    # exponential and 1 for exp(i eps H) U, 198 flops each; 4 links per site
+    flops_site = 4 * (67 + 1 + 16 + 1) * 198
+    out = {"lattice": list(dims), "beta": beta, "eps": eps, "flops_per_site_approx": flops_site,
+           "paper_ns_per_site_32^4_context": PAPER_MD_NS_32}
+    for name, prec, n in (("fp32", 1, 20), ("fp64", 0, 4), ("fp64_native", 3, 4)):
+        ctx.gauge_md_steps(beta, eps, 1, prec)  # warm-up (copies to the precision)
+        t0 = time.perf_counter()
+        ctx.gauge_md_steps(beta, eps, n, prec)
+        dt = (time.perf_counter() - t0) / n
+        out[name] = {"ns_per_site": round(dt * 1e9 / V, 3), "ms_per_step": round(dt * 1e3, 3),
+                     "tflops": round(flops_site * V / dt / 1e12, 3),
+                     "speedup_vs_paper_P100": round(PAPER_MD_NS_32["P100"] / (dt * 1e9 / V), 2)}
+    ctx.close()
+    return out
+
+
 def rational_bench(lqcd, inputs, torch):
     """RHMC rational function on the 32^4 workload: y = r(A) b with the 15
     quadrature poles of x^(-1/2) on [m^2, m^2 + 16] and the action Re <b, y>,
@@ -578,6 +612,11 @@ def run_ours(args, rank, world, local):
     barrier(world)
     lqcd.load()
     hbm_peak, peak_src = peaks()
+    if args.only_md:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": "ns/site", "config": {"only_md": True},
+                              "gauge_md": gauge_md_bench(lqcd, inputs, L=args.lattice)}), flush=True)
+        return
     if args.only_deo:
         if rank == 0:
             flush = L2Flush(torch)
@@ -695,6 +734,7 @@ def run_ours(args, rank, world, local):
     torch.cuda.empty_cache()
     extras = {}
     for name, fn in [("rational", lambda: rational_bench(lqcd, inputs, torch)),
+                     ("gauge_md", lambda: gauge_md_bench(lqcd, inputs)),
                      ("mixed_48", lambda: mixed_48_bench(lqcd, inputs, torch)),
                      ("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
                      ("packed", lambda: packed_bench(lqcd, inputs)),
@@ -749,9 +789,11 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sweep", type=int, nargs="*", default=[16, 24, 32, 48])
     ap.add_argument("--lattice", type=int, default=32, help="side of the solve lattice (default 32)")
-    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: rational mixed_48 batched packed serving serving_mixed")
+    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: rational gauge_md mixed_48 batched packed serving serving_mixed")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
+    ap.add_argument("--only-md", action="store_true",
+                    help="only the gauge MD step timing at --lattice (for profiling)")
     ap.add_argument("--only-deo", action="store_true",
                     help="run the D_eo sweep only (sizes from --sweep); for ncu captures of the stencil")
     ap.add_argument("--serving-requests", type=int, default=40, help="requests per serving run (default 40)")

@@ -301,11 +301,15 @@ int lqcd_profile_iteration(lqcd_ctx *ctx, double mass, const double *shifts, int
  * kinetic term (1/2) sum Tr H^2, so the force F_mu(x) (Hermitian, traceless)
  * is the derivative of S_g along those motions and the momenta move as
  * H -> H - e F.  The context keeps the momenta on the device.  prec:
- * LQCD_PREC_FP64 (native FP64 arithmetic on the FP64 links) or
- * LQCD_PREC_FP32 (FP32 arithmetic on FP32 copies of links and momenta,
- * Algorithm 1 step 5: "possibly in single precision"; the copies are made
- * when the precision changes and the FP32 links become the FP64 links again
- * before any D_eo or solve).  All calls are synchronous. */
+ *   LQCD_PREC_FP64: FP64 links and momenta, SU(3) products in double-float
+ *     arithmetic on the FP32 pipes (~48-bit products; GB300 issues FP32 64
+ *     times faster than FP64);
+ *   LQCD_PREC_FP64_NATIVE: the same with native FP64 (DFMA) arithmetic;
+ *   LQCD_PREC_FP32: FP32 arithmetic on FP32 copies of links and momenta
+ *     (Algorithm 1, step 5: "possibly in single precision"); the copies are
+ *     made when the precision changes, and the FP32 links become the FP64
+ *     links again before any D_eo or solve.
+ * All calls are synchronous. */
 
 /* Momenta in the canonical host layout [4][V][3][3] complex128 (n_doubles =
  * 4*V*18), Hermitian and traceless to 1e-12 relative (else LQCD_EINVAL). */

@@ -168,6 +168,7 @@ int links_ready(lqcd_ctx *c)
     }
     LQCD_CUDA(cudaGetLastError());
     c->links_derived_stale = false;
+    c->df_stale = false;
     return LQCD_OK;
 }
 
@@ -224,6 +225,7 @@ int upload_links(lqcd_ctx *c, const double *host, size_t n)
     c->links_ok = true;
     c->md_links_newest = LQCD_PREC_FP64;
     c->links_derived_stale = false;
+    c->df_stale = false;
     return LQCD_OK;
 }
 

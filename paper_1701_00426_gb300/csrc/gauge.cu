@@ -238,6 +238,293 @@ __device__ void staple_sum_dev(const LinkGeo &g, const typename Vec2T<T>::t *L, 
     }
 }
 
+// ------------------------------------------------------------------ double-float (FP64 on FP32 pipes)
+// The FP64 MD step in double-float arithmetic: an SU(3) element is 9
+// complex numbers of (hi, lo) float pairs (the context's df64 link copy, one
+// float4 per complex), products summed Dot2-style (common.cuh), so the
+// result carries ~48 significant bits on the FP32 pipes, which GB300 issues
+// 64 times faster than FP64.  The staple sum accumulates into A directly
+// with df64 coefficients (13 products per (nu, s)) to keep 5 matrices live.
+struct DC {
+    float2 re, im;
+};
+struct DM3 {
+    DC e[9];
+};
+
+__device__ __forceinline__ void dm_load(const float4 *__restrict__ L, int mu, int par, int idx, int Vh, DM3 &U)
+{
+    const float4 *p = L + (size_t)((mu * 2 + par) * 9) * Vh + idx;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const float4 v = __ldg(p + (size_t)c * Vh);
+        U.e[c].re = make_float2(v.x, v.y);
+        U.e[c].im = make_float2(v.z, v.w);
+    }
+}
+
+// c = a b (dg = false) or a b^dag (dg = true)
+template <bool dg>
+__device__ __forceinline__ void dm_mul(const DM3 &a, const DM3 &b, DM3 &c)
+{
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            Acc2 re, im;
+            acc_zero(re);
+            acc_zero(im);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const DC x = a.e[i * 3 + k];
+                const DC y = dg ? b.e[j * 3 + k] : b.e[k * 3 + j];
+                const float2 yi = dg ? df_neg(y.im) : y.im;  // conj for the dagger
+                acc_prod(re, x.re.x, x.re.y, y.re.x, y.re.y);
+                acc_prod(re, -x.im.x, -x.im.y, yi.x, yi.y);
+                acc_prod(im, x.re.x, x.re.y, yi.x, yi.y);
+                acc_prod(im, x.im.x, x.im.y, y.re.x, y.re.y);
+            }
+            c.e[i * 3 + j].re = acc_result(re);
+            c.e[i * 3 + j].im = acc_result(im);
+        }
+}
+
+// A += s t (s a df64 scalar)
+__device__ __forceinline__ void dm_axpy(float2 s, const DM3 &t, DM3 &A)
+{
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        A.e[q].re = df_fma(s, t.e[q].re, A.e[q].re);
+        A.e[q].im = df_fma(s, t.e[q].im, A.e[q].im);
+    }
+}
+
+__device__ __forceinline__ void dm_at(const LinkGeo &g, const float4 *L, const int (&x)[4], const int (&d)[4], int dir,
+                                      DM3 &U)
+{
+    int par, idx;
+    site_of(g, x, d[0], d[1], d[2], d[3], par, idx);
+    dm_load(L, dir, par, idx, g.Vh, U);
+}
+
+// t = a * (link of the step from x + d in direction s nu)
+__device__ __forceinline__ void dm_mul_step(const LinkGeo &g, const float4 *L, const int (&x)[4], const int (&d)[4],
+                                            int nu, int s, const DM3 &a, DM3 &t)
+{
+    int e[4] = {d[0], d[1], d[2], d[3]};
+    if (s < 0) e[nu] -= 1;
+    DM3 u;
+    dm_at(g, L, x, e, nu, u);
+    if (s > 0)
+        dm_mul<false>(a, u, t);
+    else
+        dm_mul<true>(a, u, t);
+}
+
+// t = a * U_mu(x + d)^dag
+__device__ __forceinline__ void dm_mul_back(const LinkGeo &g, const float4 *L, const int (&x)[4], const int (&d)[4],
+                                            int mu, const DM3 &a, DM3 &t)
+{
+    DM3 u;
+    dm_at(g, L, x, d, mu, u);
+    dm_mul<true>(a, u, t);
+}
+
+__device__ void staple_sum_df(const LinkGeo &g, const float4 *L, const int (&x)[4], int mu, DM3 &A)
+{
+#pragma unroll
+    for (int q = 0; q < 9; ++q) A.e[q].re = A.e[q].im = make_float2(0.f, 0.f);
+    // c0 and c1 as (hi, lo) pairs, split at compile time
+    const float2 c0 = make_float2((float)kSymC0, (float)(kSymC0 - (double)(float)kSymC0));
+    const float2 c1 = make_float2((float)kSymC1, (float)(kSymC1 - (double)(float)kSymC1));
+#pragma unroll 1
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+#pragma unroll 1
+        for (int s = -1; s <= 1; s += 2) {
+            int d[4] = {0, 0, 0, 0}, e[4] = {0, 0, 0, 0};
+            DM3 P1, Q, t, t2;
+            // P1 = step(x + mu, s nu)
+            d[mu] = 1;
+            {
+                int f[4] = {d[0], d[1], d[2], d[3]};
+                if (s < 0) f[nu] -= 1;
+                dm_at(g, L, x, f, nu, P1);
+                if (s < 0) {
+                    DM3 tmp = P1;
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) {
+                            P1.e[i * 3 + j].re = tmp.e[j * 3 + i].re;
+                            P1.e[i * 3 + j].im = df_neg(tmp.e[j * 3 + i].im);
+                        }
+                }
+            }
+            // rectangle (c): P1 step(x+mu+s nu, s nu) U_mu(x+2 s nu)^dag step(x+2 s nu, -s nu) E
+            d[nu] = s;
+            dm_mul_step(g, L, x, d, nu, s, P1, t);
+            e[nu] = 2 * s;
+            dm_mul_back(g, L, x, e, mu, t, t2);
+            dm_mul_step(g, L, x, e, nu, -s, t2, t);
+            e[nu] = s;
+            dm_mul_step(g, L, x, e, nu, -s, t, t2);
+            dm_axpy(c1, t2, A);
+            // Q = P1 U_mu(x + s nu)^dag;  plaquette Q E
+            dm_mul_back(g, L, x, e, mu, P1, Q);
+            dm_mul_step(g, L, x, e, nu, -s, Q, t);
+            dm_axpy(c0, t, A);
+            // rectangle (b): Q U_mu(x - mu + s nu)^dag step(x-mu+s nu, -s nu) U_mu(x - mu)
+            e[mu] = -1;
+            dm_mul_back(g, L, x, e, mu, Q, t);
+            dm_mul_step(g, L, x, e, nu, -s, t, t2);
+            e[nu] = 0;
+            {
+                DM3 u;
+                dm_at(g, L, x, e, mu, u);
+                dm_mul<false>(t2, u, t);
+            }
+            dm_axpy(c1, t, A);
+            // rectangle (a): U_mu(x+mu) step(x+2mu, s nu) U_mu(x+mu+s nu)^dag U_mu(x+s nu)^dag E
+            e[mu] = 1;
+            dm_at(g, L, x, e, mu, P1);
+            e[mu] = 2;
+            dm_mul_step(g, L, x, e, nu, s, P1, t);
+            e[mu] = 1;
+            e[nu] = s;
+            dm_mul_back(g, L, x, e, mu, t, t2);
+            e[mu] = 0;
+            dm_mul_back(g, L, x, e, mu, t2, t);
+            dm_mul_step(g, L, x, e, nu, -s, t, t2);
+            dm_axpy(c1, t2, A);
+        }
+    }
+}
+
+// H_mu(x) -= eps F_mu(x) with the staple sum and U A in double-float; F
+// and the update itself in native FP64 (about 20 operations per link).
+__global__ void __launch_bounds__(kGaugeThreads)
+    k_gauge_mom_update_df(LinkGeo g, const float4 *__restrict__ L, double *__restrict__ mom, double beta6, double eps)
+{
+    const int Vh = g.Vh;
+    const long t = blockIdx.x * (long)kGaugeThreads + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    const int i = (int)(t % Vh);
+    const int mp = (int)(t / Vh);
+    const int mu = mp >> 1, P = mp & 1;
+    int x[4];
+    coords_of(g, P, i, x);
+    DM3 A, U, M;
+    staple_sum_df(g, L, x, mu, A);
+    dm_load(L, mu, P, i, Vh, U);
+    dm_mul<false>(U, A, M);
+    double mre[9], mim[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        mre[q] = df_to_f64(M.e[q].re);
+        mim[q] = df_to_f64(M.e[q].im);
+    }
+    double f[8];
+    const double d0 = 2.0 * beta6 * mim[0], d1 = 2.0 * beta6 * mim[4], d2 = 2.0 * beta6 * mim[8];
+    const double tr = (d0 + d1 + d2) / 3.0;
+    f[0] = d0 - tr;
+    f[1] = d1 - tr;
+    f[2] = beta6 * (mim[1] + mim[3]);
+    f[3] = beta6 * (mre[3] - mre[1]);
+    f[4] = beta6 * (mim[2] + mim[6]);
+    f[5] = beta6 * (mre[6] - mre[2]);
+    f[6] = beta6 * (mim[5] + mim[7]);
+    f[7] = beta6 * (mre[7] - mre[5]);
+    double *h = mom + (size_t)(mp * 8) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[(size_t)k * Vh] = fma(-eps, f[k], h[(size_t)k * Vh]);
+}
+
+// U <- exp(i eps H) U in double-float: Z = i eps H scaled by 2^-k to
+// 1-norm <= 1/4 (scaling in FP64), Taylor series of degree 14 by Horner,
+// squared k times; the product is written to the IEEE master and to the
+// df64 copy.
+__global__ void __launch_bounds__(kGaugeThreads)
+    k_gauge_link_update_df(int Vh, double2 *__restrict__ nat, float4 *__restrict__ Ldf,
+                           const double *__restrict__ mom, double eps)
+{
+    const long t = blockIdx.x * (long)kGaugeThreads + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    const int i = (int)(t % Vh);
+    const int mp = (int)(t / Vh);
+    double h[8];
+    const double *hp = mom + (size_t)(mp * 8) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = hp[(size_t)k * Vh];
+    // 1-norm of H (columns), in FP64
+    const double h22 = -h[0] - h[1];
+    const double a01 = sqrt(h[2] * h[2] + h[3] * h[3]), a02 = sqrt(h[4] * h[4] + h[5] * h[5]),
+                 a12 = sqrt(h[6] * h[6] + h[7] * h[7]);
+    double nrm = fmax(fabs(h[0]) + a01 + a02, fmax(a01 + fabs(h[1]) + a12, a02 + a12 + fabs(h22)));
+    nrm *= fabs(eps);
+    int k = 0;
+    double sc = eps;
+    while (nrm > 0.25 && k < 60) {
+        nrm *= 0.5;
+        sc *= 0.5;
+        ++k;
+    }
+    // Z = i sc H: Z_ab = i sc H_ab -> re = -sc Im H_ab, im = sc Re H_ab
+    DM3 Z;
+    {
+        const double hr[9] = {h[0], h[2], h[4], h[2], h[1], h[6], h[4], h[6], h22};
+        const double hi[9] = {0.0, h[3], h[5], -h[3], 0.0, h[7], -h[5], -h[7], 0.0};
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            Z.e[q].re = f64_to_df_slow(-sc * hi[q]);
+            Z.e[q].im = f64_to_df_slow(sc * hr[q]);
+        }
+    }
+    DM3 R, ZR;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        R.e[q].re = make_float2(q % 4 == 0 ? 1.f : 0.f, 0.f);
+        R.e[q].im = make_float2(0.f, 0.f);
+    }
+#pragma unroll 1
+    for (int n = 14; n >= 1; --n) {
+        dm_mul<false>(Z, R, ZR);
+        const float2 inv = f64_to_df_slow(1.0 / n);
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            R.e[q].re = df_mul(inv, ZR.e[q].re);
+            R.e[q].im = df_mul(inv, ZR.e[q].im);
+            if (q % 4 == 0) R.e[q].re = df_add(R.e[q].re, make_float2(1.f, 0.f));
+        }
+    }
+#pragma unroll 1
+    for (int q = 0; q < k; ++q) {
+        dm_mul<false>(R, R, ZR);
+        R = ZR;
+    }
+    DM3 U;
+    dm_load(Ldf, mp >> 1, mp & 1, i, Vh, U);
+    dm_mul<false>(R, U, ZR);
+    double2 *pn = nat + (size_t)(mp * 9) * Vh + i;
+    float4 *pd = Ldf + (size_t)(mp * 9) * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        const float2 re = ZR.e[c].re, im = ZR.e[c].im;
+        pn[(size_t)c * Vh] = make_double2(df_to_f64(re), df_to_f64(im));
+        pd[(size_t)c * Vh] = make_float4(re.x, re.y, im.x, im.y);
+    }
+}
+
+// IEEE master -> df64 copy (the form k_convert_links writes)
+__global__ void k_links_nat_to_df(const double2 *__restrict__ nat, float4 *Ldf, long n)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double2 d = nat[t];
+    const float2 re = f64_to_df_slow(d.x), im = f64_to_df_slow(d.y);
+    Ldf[t] = make_float4(re.x, re.y, im.x, im.y);
+}
+
 // 8 reals <-> traceless Hermitian matrix
 template <class T>
 __device__ __forceinline__ void herm_unpack(const T (&h)[8], Mat3<T> &H)
@@ -600,18 +887,31 @@ static int links_to_prec(lqcd_ctx *c, int prec)
             LQCD_CUDA(cudaGetLastError());
             c->launches += 1;
         }
-    } else if (c->md_links_newest == LQCD_PREC_FP32) {
+        return LQCD_OK;
+    }
+    if (c->md_links_newest == LQCD_PREC_FP32) {
         k_links_f32_to_f64<<<nblocks(n, 256), 256, 0, c->stream>>>(c->lnk_f18.as<float2>(), c->lnk_nat.as<double2>(), n);
         LQCD_CUDA(cudaGetLastError());
         c->launches += 1;
         c->md_links_newest = LQCD_PREC_FP64;
         c->links_derived_stale = true;
+        c->df_stale = true;
+    }
+    if (prec == LQCD_PREC_FP64 && c->df_stale) {  // double-float steps work on the df64 copy
+        k_links_nat_to_df<<<nblocks(n, 256), 256, 0, c->stream>>>(c->lnk_nat.as<double2>(), c->lnk_df.as<float4>(), n);
+        LQCD_CUDA(cudaGetLastError());
+        c->launches += 1;
+        c->df_stale = false;
     }
     return LQCD_OK;
 }
 
+// FP64 and native FP64 share the FP64 momenta
+static inline int mom_prec(int prec) { return prec == LQCD_PREC_FP32 ? LQCD_PREC_FP32 : LQCD_PREC_FP64; }
+
 static int mom_to_prec(lqcd_ctx *c, int prec)
 {
+    prec = mom_prec(prec);
     if (c->mom_newest == prec) return LQCD_OK;
     const long n = 64L * (long)c->Vh;
     if (prec == LQCD_PREC_FP32)
@@ -629,7 +929,8 @@ static int check_md(lqcd_ctx *c, int prec)
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
     if (!c->mom64.ptr) return fail(LQCD_ESTATE, "no momenta uploaded");
-    if (prec != LQCD_PREC_FP64 && prec != LQCD_PREC_FP32) return fail(LQCD_EINVAL, "MD precision must be FP64 or FP32");
+    if (prec != LQCD_PREC_FP64 && prec != LQCD_PREC_FP32 && prec != LQCD_PREC_FP64_NATIVE)
+        return fail(LQCD_EINVAL, "MD precision must be FP64, FP64_NATIVE or FP32");
     return LQCD_OK;
 }
 
@@ -638,6 +939,9 @@ static void launch_mom_update(lqcd_ctx *c, int prec, double beta, double eps)
     const LinkGeo g = link_geo(c);
     const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
     if (prec == LQCD_PREC_FP64)
+        k_gauge_mom_update_df<<<nb, kGaugeThreads, 0, c->stream>>>(g, c->lnk_df.as<float4>(), c->mom64.as<double>(),
+                                                                   beta / 6.0, eps);
+    else if (prec == LQCD_PREC_FP64_NATIVE)
         k_gauge_mom_update<double><<<nb, kGaugeThreads, 0, c->stream>>>(g, c->lnk_nat.as<double2>(), c->mom64.as<double>(),
                                                                         beta / 6.0, eps);
     else
@@ -650,13 +954,19 @@ static void launch_link_update(lqcd_ctx *c, int prec, double eps)
 {
     const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
     if (prec == LQCD_PREC_FP64) {
+        k_gauge_link_update_df<<<nb, kGaugeThreads, 0, c->stream>>>((int)c->Vh, c->lnk_nat.as<double2>(),
+                                                                    c->lnk_df.as<float4>(), c->mom64.as<double>(), eps);
+        c->md_links_newest = LQCD_PREC_FP64;
+    } else if (prec == LQCD_PREC_FP64_NATIVE) {
         k_gauge_link_update<double><<<nb, kGaugeThreads, 0, c->stream>>>((int)c->Vh, c->lnk_nat.as<double2>(),
                                                                          c->mom64.as<double>(), eps);
         c->md_links_newest = LQCD_PREC_FP64;
+        c->df_stale = true;
     } else {
         k_gauge_link_update<float><<<nb, kGaugeThreads, 0, c->stream>>>((int)c->Vh, c->lnk_f18.as<float2>(),
                                                                         c->mom32.as<float>(), (float)eps);
         c->md_links_newest = LQCD_PREC_FP32;
+        c->df_stale = true;
     }
     c->links_derived_stale = true;
     c->launches += 1;
@@ -769,9 +1079,11 @@ int lqcd_gauge_action(lqcd_ctx *c, int prec, double beta, double *S)
 {
     if (!c || !S) return fail(LQCD_EINVAL, "NULL argument");
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
-    if (prec != LQCD_PREC_FP64 && prec != LQCD_PREC_FP32) return fail(LQCD_EINVAL, "precision must be FP64 or FP32");
+    if (prec != LQCD_PREC_FP64 && prec != LQCD_PREC_FP32 && prec != LQCD_PREC_FP64_NATIVE)
+        return fail(LQCD_EINVAL, "precision must be FP64, FP64_NATIVE or FP32");
+    if (prec == LQCD_PREC_FP64_NATIVE) prec = LQCD_PREC_FP64;  // the action is computed from the IEEE master
     int st;
-    if ((st = links_to_prec(c, prec))) return st;
+    if ((st = links_to_prec(c, prec == LQCD_PREC_FP64 ? LQCD_PREC_FP64_NATIVE : prec))) return st;
     const unsigned nb = nblocks(2L * (long)c->Vh, kGaugeThreads);
     if ((st = c->md_part.ensure(((size_t)nb + 1) * sizeof(double)))) return st;
     double *part = c->md_part.as<double>();
@@ -796,7 +1108,7 @@ int lqcd_mom_energy(lqcd_ctx *c, int prec, double *K)
     const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
     if ((st = c->md_part.ensure(((size_t)nb + 1) * sizeof(double)))) return st;
     double *part = c->md_part.as<double>();
-    if (prec == LQCD_PREC_FP64)
+    if (mom_prec(prec) == LQCD_PREC_FP64)
         k_mom_energy_part<double><<<nb, kGaugeThreads, 0, c->stream>>>((int)c->Vh, c->mom64.as<double>(), part);
     else
         k_mom_energy_part<float><<<nb, kGaugeThreads, 0, c->stream>>>((int)c->Vh, c->mom32.as<float>(), part);

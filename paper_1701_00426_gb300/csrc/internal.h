@@ -157,6 +157,7 @@ struct lqcd_ctx {
     lqcd::DevBuf md_part;     // partials of the action / kinetic energy (+ the total)
     int md_links_newest = 0;  // LQCD_PREC_FP64: lnk_nat holds the newest links; FP32: lnk_f18
     bool links_derived_stale = false;  // MD moved the links: derived formats need a rebuild
+    bool df_stale = false;    // the df64 link copy lags the IEEE master (double-float MD reads it)
     int mom_newest = 0;       // which momentum copy is current
     lqcd::Workspace ws;
     lqcd::Workspace ws32;                  // FP32 phase of a hybrid mixed-precision solve
