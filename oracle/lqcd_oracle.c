@@ -436,6 +436,90 @@ int oracle_rational_apply(const int N[4], const cplx *links, double mass, double
 }
 
 /* ------------------------------------------------------------------------ */
+/* Fermion force of the rational pseudofermion action (Sec. 2.2)            */
+/* ------------------------------------------------------------------------ */
+
+/* S_f = phi^dag r(A) phi with r(A) = a0 + sum_i a_i (A + sigma_i)^{-1}
+ * (Eq. rooting with the rational approximation of Eq. shlineq).  Written
+ * out from the derivative: with x_i = (A + sigma_i)^{-1} phi (even sites),
+ * y_i = D_oe x_i (odd sites) and D_oe^dag = -D_eo (Eq. diracblock),
+ *   dS_f = sum_i a_i [ x_i^dag (dD) y_i - y_i^dag (dD) x_i ],
+ * and a link U_mu(n) enters D through (1/2) s_mu(n) U_mu(n) psi(n+mu) at n
+ * and -(1/2) s_mu(n) U_mu(n)^dag psi(n) at n+mu.  Along
+ * U_mu(n) -> exp(i e X) U_mu(n) this gives d/de S_f = Tr(X F_mu(n)) with
+ *   F_mu(n) = traceless part of (i s_mu(n) / 2) c sum_i a_i (W_i - W_i^dag),
+ *   n even:  W_i = U_mu(n) y_i(n+mu) x_i(n)^dag,   c = +1,
+ *   n odd:   W_i = U_mu(n) x_i(n+mu) y_i(n)^dag,   c = -1.
+ * F: [4][V][3][3]; *action = Re <phi, r(A) phi>.  Returns the status of the
+ * multi-shift solve (tolerance tol on every pole). */
+static void m_mul(const cplx *a, const cplx *b, cplx *c);
+
+int oracle_fermion_force(const int N[4], const cplx *links, double mass, double a0, const double *a,
+                         const double *shifts, int n_shift, const cplx *phi, double tol, int max_iter,
+                         cplx *F, double *action)
+{
+    const long V = volume(N), Vh = V / 2, n3 = Vh * 3;
+    if (n_shift < 1 || n_shift > 64) return -2;
+    cplx *x = malloc(sizeof(cplx) * n3 * n_shift), *y = malloc(sizeof(cplx) * n3 * n_shift);
+    int iters[2], shift_iters[64];
+    double resid[64];
+    const int status = oracle_mscg(N, links, mass, shifts, n_shift, phi, x, tol, max_iter, iters, shift_iters,
+                                   resid);
+    for (int i = 0; i < n_shift; ++i) oracle_deo(N, 1, links, x + i * n3, y + i * n3);
+    double act = 0.0;
+    for (long k = 0; k < n3; ++k) {
+        cplx v = a0 * phi[k];
+        for (int i = 0; i < n_shift; ++i) v += a[i] * x[i * n3 + k];
+        act += creal(conj(phi[k]) * v);
+    }
+    *action = act;
+#pragma omp parallel for schedule(static)
+    for (long lex = 0; lex < V; ++lex) {
+        int xn[4];
+        long r = lex;
+        for (int m = 0; m < 4; ++m) { xn[m] = (int)(r % N[m]); r /= N[m]; }
+        const int par = oracle_parity(xn);
+        for (int mu = 0; mu < 4; ++mu) {
+            int xp[4] = {xn[0], xn[1], xn[2], xn[3]};
+            xp[mu] = (xp[mu] + 1) % N[mu];
+            const long hn = oracle_idxh(N, xn), hp = oracle_idxh(N, xp);
+            /* O = sum_i a_i (left)(right)^dag: left at n + mu, right at n */
+            cplx O[9];
+            for (int q = 0; q < 9; ++q) O[q] = 0;
+            for (int i = 0; i < n_shift; ++i) {
+                const cplx *left = (par == 0 ? y : x) + i * n3 + hp * 3;
+                const cplx *right = (par == 0 ? x : y) + i * n3 + hn * 3;
+                for (int p = 0; p < 3; ++p)
+                    for (int q = 0; q < 3; ++q) O[p * 3 + q] += a[i] * left[p] * conj(right[q]);
+            }
+            cplx W[9];
+            m_mul(links + ((long)mu * V + lex) * 9, O, W);
+#if ORACLE_MUTANT == 17
+            /* planted: the staggered sign of the link is dropped from the force */
+            const double s = 1.0;
+#else
+            const double s = oracle_link_sign(N, xn, mu);
+#endif
+#if ORACLE_MUTANT == 16
+            /* planted: the odd-site terms keep the even-site sign */
+            const double c = 1.0;
+#else
+            const double c = (par == 0) ? 1.0 : -1.0;
+#endif
+            cplx *f = F + ((long)mu * V + lex) * 9;
+            for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q)
+                    f[p * 3 + q] = I * 0.5 * s * c * (W[p * 3 + q] - conj(W[q * 3 + p]));
+            const cplx tr = (f[0] + f[4] + f[8]) / 3.0;
+            f[0] -= tr; f[4] -= tr; f[8] -= tr;
+        }
+    }
+    free(x);
+    free(y);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Gauge part of the molecular dynamics step (Sec. 2.1, Sec. 4.2)           */
 /* ------------------------------------------------------------------------ */
 

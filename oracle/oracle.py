@@ -75,6 +75,9 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.oracle_rational_apply.argtypes = [ip, vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int,
                                           vp, vp, ctypes.c_double, ctypes.c_int, dp]
     lib.oracle_rational_apply.restype = ctypes.c_int
+    lib.oracle_fermion_force.argtypes = [ip, vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int, vp,
+                                         ctypes.c_double, ctypes.c_int, vp, dp]
+    lib.oracle_fermion_force.restype = ctypes.c_int
     lib.oracle_gauge_action.argtypes = [ip, vp, ctypes.c_double]
     lib.oracle_gauge_action.restype = ctypes.c_double
     lib.oracle_gauge_force.argtypes = [ip, vp, ctypes.c_double, vp]
@@ -215,6 +218,21 @@ class Oracle:
                                             self._ptr(b), self._ptr(y), float(tol), int(max_iter),
                                             ctypes.byref(act))
         return y, act.value, st
+
+    def fermion_force(self, dims, links, mass, a0, a, shifts, phi, tol, max_iter=20000):
+        """Force of S_f = phi^dag r(A) phi on every link; returns (F [4][V][3][3], S_f, status)."""
+        V = int(np.prod(dims))
+        links = self._c128(links, (4, V, 3, 3))
+        phi = self._c128(phi, (V // 2, 3))
+        aa = np.ascontiguousarray(a, dtype=np.float64)
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        F = np.empty_like(links)
+        act = ctypes.c_double()
+        dp = ctypes.POINTER(ctypes.c_double)
+        st = self.lib.oracle_fermion_force(self._dims(dims), self._ptr(links), float(mass), float(a0),
+                                           aa.ctypes.data_as(dp), sh.ctypes.data_as(dp), sh.size, self._ptr(phi),
+                                           float(tol), int(max_iter), self._ptr(F), ctypes.byref(act))
+        return F, act.value, st
 
     # ------------------------------------------------- gauge MD (Symanzik)
     def gauge_action(self, dims, links, beta: float) -> float:

@@ -419,6 +419,47 @@ def pin_md_energy(orc, dims=(4, 4, 4, 4), beta=BETA, seed=75) -> tuple[bool, str
     return ok, f"|dH| {dH[0]:.2e} {dH[1]:.2e} {dH[2]:.2e}, ratios {r1:.2f} {r2:.2f}"
 
 
+# --------------------------------------------------- fermion force (f4)
+FF_MASS, FF_A0 = 0.3, 0.2
+FF_A, FF_SIGMA = [0.3, 0.8, 1.5], [0.05, 0.5, 3.0]
+
+
+def pin_fermion_force_is_derivative(orc, dims=(4, 4, 4, 4), h=1e-4, tol=1e-13, seed=95) -> tuple[bool, str]:
+    """d/de S_f(exp(i e X) U) at e = 0, S_f = phi^dag r(A) phi evaluated by the
+    oracle's rational application (central difference), equals sum Tr(X F_f);
+    F_f Hermitian and traceless."""
+    U = inputs.random_links(dims, seed=seed)
+    phi = inputs.gaussian_field(dims, k=seed)
+    X = inputs.random_momenta(dims, seed=seed + 1)
+    F, S, st = orc.fermion_force(dims, U, FF_MASS, FF_A0, FF_A, FF_SIGMA, phi, tol)
+    if st != 0:
+        return False, f"status {st}"
+    Sp = orc.rational_apply(dims, orc.link_update(dims, U, X, h), FF_MASS, FF_A0, FF_A, FF_SIGMA, phi, tol)[1]
+    Sm = orc.rational_apply(dims, orc.link_update(dims, U, X, -h), FF_MASS, FF_A0, FF_A, FF_SIGMA, phi, tol)[1]
+    num = (Sp - Sm) / (2.0 * h)
+    ana = float(np.einsum("mvij,mvji->", X, F).real)
+    e = abs(num - ana) / abs(ana)
+    herm = float(np.abs(F - np.conj(np.swapaxes(F, -1, -2))).max())
+    trace = float(np.abs(np.trace(F, axis1=-2, axis2=-1)).max())
+    ok = e <= 1e-6 and herm <= 1e-13 * np.abs(F).max() and trace <= 1e-13 * np.abs(F).max()
+    return ok, f"derivative defect {e:.2e}, hermiticity {herm:.1e}, trace {trace:.1e}"
+
+
+def pin_fermion_force_covariant(orc, dims=(4, 4, 4, 6), tol=1e-13, seed=96) -> tuple[bool, str]:
+    """U -> U^Omega, phi -> Omega phi on the even sites: F_f_mu(x) -> Omega(x) F_f_mu(x) Omega(x)^dag
+    and S_f unchanged."""
+    U = inputs.random_links(dims, seed=seed)
+    Om = inputs.random_gauge_transform(dims, seed=seed + 1)
+    phi = inputs.gaussian_field(dims, k=seed)
+    evens = [n for n, x in enumerate(sites(dims)) if sum(x) % 2 == 0]
+    phip = np.stack([Om[n] @ phi[i] for i, n in enumerate(evens)])
+    F, S, _ = orc.fermion_force(dims, U, FF_MASS, FF_A0, FF_A, FF_SIGMA, phi, tol)
+    Fp, Sp, _ = orc.fermion_force(dims, gauge_transform_links(dims, U, Om), FF_MASS, FF_A0, FF_A, FF_SIGMA, phip, tol)
+    Frot = np.einsum("vij,mvjk,vlk->mvil", Om, F, Om.conj())
+    eF, eS = rel(Fp, Frot), abs(Sp - S) / abs(S)
+    return eF <= 1e-10 and eS <= 1e-12, f"force covariance {eF:.2e}, action {eS:.2e}"
+
+
 BATTERY = [
     ("geometry 4x6x8x10", lambda o: pin_geometry(o, (4, 6, 8, 10))),
     ("phase anticommutation 4x6x8x10", lambda o: pin_phase_anticommutation(o, (4, 6, 8, 10))),
@@ -434,4 +475,5 @@ BATTERY = [
     ("gauge action U=1", pin_gauge_action_unit),
     ("gauge force = derivative of the action 4^4", pin_force_is_derivative),
     ("MD energy conservation O(dt^2) 4^4", pin_md_energy),
+    ("fermion force = derivative of the rational action 4^4", pin_fermion_force_is_derivative),
 ]

@@ -21,6 +21,8 @@ MUTANTS = {
     13: "rectangle staple (b) left out of the gauge force",
     14: "links move with exp(-i eps H)",
     15: "trace of the gauge force kept",
+    16: "fermion force: odd-site terms with the even-site sign",
+    17: "fermion force without the staggered sign",
 }
 
 

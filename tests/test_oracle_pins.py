@@ -199,3 +199,16 @@ def test_md_leapfrog_reversible(orc):
 def test_md_energy_violation_second_order(orc):
     ok, msg = pins.pin_md_energy(orc)
     assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 2, 6)])
+def test_fermion_force_is_derivative_of_rational_action(orc, dims):
+    """Force of phi^dag r(A) phi (Sec. 2.2) against a central difference of
+    the oracle's rational application along random algebra directions."""
+    ok, msg = pins.pin_fermion_force_is_derivative(orc, dims)
+    assert ok, msg
+
+
+def test_fermion_force_gauge_covariant(orc):
+    ok, msg = pins.pin_fermion_force_covariant(orc)
+    assert ok, msg
