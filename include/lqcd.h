@@ -327,6 +327,25 @@ int lqcd_gauge_link_update(lqcd_ctx *ctx, int prec, double eps);
  * (the unit that Table md-norm times per site); n_steps >= 0. */
 int lqcd_gauge_md_steps(lqcd_ctx *ctx, int prec, double beta, double eps, int n_steps);
 
+/* Fermion force of the rational pseudofermion action (Sec. 2.2: Eq. rooting
+ * with the rational function of Eq. shlineq; the fermion force steps of
+ * Algorithm 2): S_f = phi^dag r(A) phi, r(A) = a0 + sum_i a[i] (A + shifts[i])^{-1},
+ * A = m^2 - D_eo D_oe.  Solves (A + shifts[i]) x_i = phi to the FP64 true
+ * residual tol for every pole (as lqcd_rational_apply), forms y_i = D_oe x_i,
+ * and updates the context's momenta H <- H - eps F_f with the Hermitian
+ * traceless force F_f_mu(n) = traceless part of (i s_mu(n)/2) c sum_i a_i
+ * (W_i - W_i^dag), W_i = U_mu(n) y_i(n+mu) x_i(n)^dag for even n (c = +1),
+ * U_mu(n) x_i(n+mu) y_i(n)^dag for odd n (c = -1), s_mu(n) the staggered
+ * sign of the link with the antiperiodic time boundary: the derivative of
+ * S_f along U -> exp(i e X) U is sum Tr(X F_f).  phi: host canonical even
+ * spinor ([Vh][3] complex128); *action (may be NULL) receives S_f.  The
+ * force is computed in native FP64 from the FP64 links; momenta must have
+ * been uploaded.  Synchronous.  LQCD_ENOCONV at max_iter (the update is
+ * still applied). */
+int lqcd_fermion_force_update(lqcd_ctx *ctx, double mass, double a0, const double *a,
+                              const double *shifts, int n_shift, double tol, const double *phi,
+                              double eps, double *action, lqcd_solve_info *info);
+
 /* *S = S_g(U) of the current links (sums in FP64 in a fixed order). */
 int lqcd_gauge_action(lqcd_ctx *ctx, int prec, double beta, double *S);
 

@@ -104,6 +104,7 @@ struct lqcd_ctx {
     // gauge molecular dynamics (gauge.cu): momenta as 8 reals per link, SoA [4][2][8][Vh]
     lqcd::DevBuf mom64, mom32;
     lqcd::DevBuf md_part;     // partials of the action / kinetic energy (+ the total)
+    lqcd::DevBuf ff_y;        // D_oe x_i of the fermion force [n][3][Vh] double2
     int md_links_newest = 0;  // LQCD_PREC_FP64: lnk_nat holds the newest links; FP32: lnk_f18
     bool links_derived_stale = false;  // MD moved the links: derived formats need a rebuild
     bool df_stale = false;    // the df64 link copy lags the IEEE master (double-float MD reads it)
@@ -192,6 +193,12 @@ void k_res_nat2_ext(const Geom &g, const double2 *L, const double2 *t, const dou
 double unit_scale_pub(double n2, double n);
 void init_state_pub(SolverState &S, double mass, const double *shifts, int n_shift, double tol_iter, double b2,
                     int max_iter);
+
+// rational.cu: y = a0 b + sum_i a_i (A + sigma_i)^{-1} b on device buffers; the
+// shifted solutions stay in c->rat_x.
+int rational_apply_dev(lqcd_ctx *c, double mass, double a0, const double *a, const double *shifts, int n_shift,
+                       double tol, const double2 *b, double2 *y, double *action, lqcd_solve_info *info,
+                       cudaStream_t s_user);
 
 // mrhs.cu
 int deo_mrhs_launch(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const void *in, void *out, cudaStream_t s);

@@ -49,7 +49,7 @@ EXPORTED = [
     "lqcd_serve_create", "lqcd_serve_register_field", "lqcd_serve_submit", "lqcd_serve_poll",
     "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy", "lqcd_serve_set_opts",
     "lqcd_mom_upload", "lqcd_mom_download", "lqcd_gauge_mom_update", "lqcd_gauge_link_update",
-    "lqcd_gauge_md_steps", "lqcd_gauge_action", "lqcd_mom_energy",
+    "lqcd_gauge_md_steps", "lqcd_gauge_action", "lqcd_mom_energy", "lqcd_fermion_force_update",
 ]
 
 
@@ -151,6 +151,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_gauge_md_steps": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int]),
         "lqcd_gauge_action": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_double, dp]),
         "lqcd_mom_energy": (ctypes.c_int, [vp, ctypes.c_int, dp]),
+        "lqcd_fermion_force_update": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int,
+                                                     ctypes.c_double, vp, ctypes.c_double, dp,
+                                                     ctypes.POINTER(lqcd_solve_info)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -284,6 +287,21 @@ class Context:
         s = ctypes.c_double()
         check(self.lib.lqcd_gauge_action(self.h, int(prec), float(beta), ctypes.byref(s)))
         return s.value
+
+    def fermion_force_update(self, mass: float, a0: float, a, shifts, tol: float, phi: np.ndarray, eps: float):
+        """H <- H - eps F_f for S_f = phi^dag r(A) phi; returns (S_f, info)."""
+        aa = np.ascontiguousarray(a, dtype=np.float64)
+        sh = np.ascontiguousarray(shifts, dtype=np.float64)
+        if aa.size != sh.size:
+            raise ValueError("one coefficient per pole")
+        pp = _c128(phi, (self.Vh, 3))
+        act = ctypes.c_double()
+        info = lqcd_solve_info()
+        dp = ctypes.POINTER(ctypes.c_double)
+        check(self.lib.lqcd_fermion_force_update(self.h, float(mass), float(a0), aa.ctypes.data_as(dp),
+                                                 sh.ctypes.data_as(dp), sh.size, float(tol), _ptr(pp), float(eps),
+                                                 ctypes.byref(act), ctypes.byref(info)))
+        return act.value, info.as_dict()
 
     def mom_energy(self, prec: int = 0) -> float:
         k = ctypes.c_double()
