@@ -519,6 +519,34 @@ def gauge_md_bench(lqcd, inputs, L=32, beta=5.5, eps=0.01):
     return out
 
 
+def fermion_force_bench(lqcd, inputs):
+    """Fermion force of phi^dag r(A) phi on the 32^4 workload (15 quadrature
+    poles of x^(-1/2), m = 0.01, tol 1e-10): one momentum update against the
+    rational application alone (the difference is the 15 D_oe applications
+    and the force kernel)."""
+    from paper_1701_00426_gb300 import rational
+    a0, a, sg = rational.inverse_sqrt_poles(N_SHIFT, MASS * MASS, MASS * MASS + 16.0)
+    U = inputs.random_links(DIMS)
+    phi = inputs.gaussian_field(DIMS, k=0)
+    ctx = lqcd.Context(DIMS)
+    ctx.links_upload(U)
+    ctx.mom_upload(inputs.random_momenta(DIMS))
+    del U
+    ctx.fermion_force_update(MASS, a0, a, sg, TOL, phi, 0.0)  # warm-up (graphs, workspaces)
+    t0 = time.perf_counter()
+    act, info = ctx.fermion_force_update(MASS, a0, a, sg, TOL, phi, 0.01)
+    dt_f = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    ctx.rational_apply(MASS, a0, a, sg, TOL, phi)
+    dt_r = time.perf_counter() - t1
+    ctx.close()
+    V = int(np.prod(DIMS))
+    return {"poles": N_SHIFT, "force_updates_per_s": round(1.0 / dt_f, 4), "s": round(dt_f, 4),
+            "rational_apply_s": round(dt_r, 4), "force_beyond_solve_ms": round(1e3 * (dt_f - dt_r), 2),
+            "force_beyond_solve_ns_per_site": round(1e9 * (dt_f - dt_r) / V, 2), "action": act,
+            "iters": info["iters"], "max_true_resid": max(info["true_resid"][:N_SHIFT])}
+
+
 def rational_bench(lqcd, inputs, torch):
     """RHMC rational function on the 32^4 workload: y = r(A) b with the 15
     quadrature poles of x^(-1/2) on [m^2, m^2 + 16] and the action Re <b, y>,
@@ -735,6 +763,7 @@ def run_ours(args, rank, world, local):
     extras = {}
     for name, fn in [("rational", lambda: rational_bench(lqcd, inputs, torch)),
                      ("gauge_md", lambda: gauge_md_bench(lqcd, inputs)),
+                     ("fermion_force", lambda: fermion_force_bench(lqcd, inputs)),
                      ("mixed_48", lambda: mixed_48_bench(lqcd, inputs, torch)),
                      ("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
                      ("packed", lambda: packed_bench(lqcd, inputs)),
@@ -789,7 +818,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sweep", type=int, nargs="*", default=[16, 24, 32, 48])
     ap.add_argument("--lattice", type=int, default=32, help="side of the solve lattice (default 32)")
-    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: rational gauge_md mixed_48 batched packed serving serving_mixed")
+    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: rational gauge_md fermion_force mixed_48 batched packed serving serving_mixed")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
     ap.add_argument("--only-md", action="store_true",
