@@ -268,7 +268,7 @@ def batched_bench(lqcd, inputs, torch, hbm_peak):
         c.links_upload(U)
         del U
         s = torch.cuda.current_stream()
-        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        flush = L2Flush(torch)
         for n in (1, 4, 8, 16):
             x = torch.randn((3, c.Vh, n), dtype=torch.complex64, device="cuda")
             o = torch.empty_like(x)

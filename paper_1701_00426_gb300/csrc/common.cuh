@@ -398,6 +398,45 @@ __device__ __forceinline__ float4 ldg4_stream(const float4 *p, uint64_t pol)
 #endif
 }
 __device__ __forceinline__ float2 ldg2(const float2 *p) { return __ldg(p); }
+
+// 8- and 16-byte streamed loads with the evict-first policy (FP32 / FP16 links)
+__device__ __forceinline__ float2 ldg2_stream(const float2 *p, uint64_t pol)
+{
+#ifdef LQCD_NO_L2_HINTS
+    (void)pol;
+    return __ldg(p);
+#else
+    float2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0,%1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(p), "l"(pol));
+    return v;
+#endif
+}
+
+__device__ __forceinline__ uint4 ldg4u_stream(const uint4 *p, uint64_t pol)
+{
+#ifdef LQCD_NO_L2_HINTS
+    (void)pol;
+    return __ldg(p);
+#else
+    uint4 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p), "l"(pol));
+    return v;
+#endif
+}
+
+__device__ __forceinline__ uint2 ldg2u_stream(const uint2 *p, uint64_t pol)
+{
+#ifdef LQCD_NO_L2_HINTS
+    (void)pol;
+    return __ldg(p);
+#else
+    uint2 v;
+    asm volatile("ld.global.nc.L2::cache_hint.v2.u32 {%0,%1}, [%2], %3;" : "=r"(v.x), "=r"(v.y) : "l"(p), "l"(pol));
+    return v;
+#endif
+}
 __device__ __forceinline__ double2 ldg2d(const double2 *p) { return __ldg(p); }
 
 // Streaming loads/stores for data touched once per kernel (Krylov vectors).

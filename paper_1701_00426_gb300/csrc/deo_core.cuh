@@ -229,18 +229,21 @@ __device__ __forceinline__ float2 h2f(uint32_t w)
     return __half22float2(h);
 }
 
+// Links are streamed once per application: loads carry the L2 evict-first
+// policy so that the re-read spinors keep their place in L2.
 template <int LF>
 __device__ __forceinline__ void load_link_f32(const void *L, int mu, int par, int idx, int Vh, float2 (&U)[9])
 {
+    const uint64_t pol = l2_evict_first_policy();
     if (LF == LF_F32_18) {
         const float2 *p = (const float2 *)L + link_base(mu, par, 9, Vh) + idx;
 #pragma unroll
-        for (int c = 0; c < 9; ++c) U[c] = ldg2(p + (size_t)c * Vh);
+        for (int c = 0; c < 9; ++c) U[c] = ldg2_stream(p + (size_t)c * Vh, pol);
     } else if (LF == LF_F32_12) {
         const float4 *p = (const float4 *)L + link_base(mu, par, 3, Vh) + idx;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            const float4 t = ldg4(p + (size_t)k * Vh);
+            const float4 t = ldg4_stream(p + (size_t)k * Vh, pol);
             U[2 * k] = make_float2(t.x, t.y);
             U[2 * k + 1] = make_float2(t.z, t.w);
         }
@@ -248,8 +251,8 @@ __device__ __forceinline__ void load_link_f32(const void *L, int mu, int par, in
     } else {  // LF_F16_12: [8 Vh] uint4 (c00 c01 c02 c10) then [8 Vh] uint2 (c11 c12)
         const uint4 *pa = (const uint4 *)L;
         const uint2 *pb = (const uint2 *)(pa + (size_t)8 * Vh);
-        const uint4 a = __ldg(pa + (size_t)(mu * 2 + par) * Vh + idx);
-        const uint2 b = __ldg(pb + (size_t)(mu * 2 + par) * Vh + idx);
+        const uint4 a = ldg4u_stream(pa + (size_t)(mu * 2 + par) * Vh + idx, pol);
+        const uint2 b = ldg2u_stream(pb + (size_t)(mu * 2 + par) * Vh + idx, pol);
         U[0] = h2f(a.x); U[1] = h2f(a.y); U[2] = h2f(a.z); U[3] = h2f(a.w);
         U[4] = h2f(b.x); U[5] = h2f(b.y);
         reconstruct_row2(U);

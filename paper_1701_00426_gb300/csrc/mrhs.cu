@@ -16,6 +16,10 @@
 // on its own.  The iteration kernels carry per-field reductions with the same
 // deterministic tile-ordered scheme as the multi-shift solver.
 #include <algorithm>
+#include <cstdio>
+#include <string>
+#include <mutex>
+#include <map>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -292,7 +296,9 @@ static int pick_R(int n) { return (n % 4 == 0) ? 4 : (n % 2 == 0 ? 2 : 1); }
 template <int LF>
 static void launch_deo_mrhs_R(const MrhsArgs &A, int R, unsigned nb, cudaStream_t s)
 {
-    if (R == 4) k_deo_mrhs<LF, 4><<<nb, kTile, 0, s>>>(A);
+    if (R == 16) k_deo_mrhs<LF, 16><<<nb, kTile, 0, s>>>(A);
+    else if (R == 8) k_deo_mrhs<LF, 8><<<nb, kTile, 0, s>>>(A);
+    else if (R == 4) k_deo_mrhs<LF, 4><<<nb, kTile, 0, s>>>(A);
     else if (R == 2) k_deo_mrhs<LF, 2><<<nb, kTile, 0, s>>>(A);
     else k_deo_mrhs<LF, 1><<<nb, kTile, 0, s>>>(A);
 }
@@ -312,6 +318,54 @@ static void launch_deo2_R(const MrhsArgs &A, int R, unsigned nb, cudaStream_t s)
     else k_mrhs_deo2<LF, 1><<<nb, kTile, 0, s>>>(A);
 }
 
+// Fields per thread of the stand-alone multi-RHS D_eo, picked per (n, recon,
+// lattice) on the first call by timing every R that divides n (1..16) with
+// CUDA events on the call's stream; cached for the process.  Each field's
+// sum does not depend on R, so every choice gives the same bits.  During
+// stream capture the default (4, 2 or 1) is used without tuning.
+static std::mutex g_mr_mu;
+static std::map<std::string, int> g_mr_tune;
+
+static int mrhs_pick_R(lqcd_ctx *c, MrhsArgs A, int lf, cudaStream_t s)
+{
+    char key[96];
+    snprintf(key, sizeof key, "n%d lf%d %dx%dx%dx%d", A.n, lf, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
+    {
+        std::lock_guard<std::mutex> lk(g_mr_mu);
+        auto it = g_mr_tune.find(key);
+        if (it != g_mr_tune.end()) return it->second;
+    }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(s, &cap);
+    if (cap != cudaStreamCaptureStatusNone) return pick_R(A.n);
+    int best_R = pick_R(A.n);
+    float best = 1e30f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return best_R;
+    for (int R = 1; R <= 16; R <<= 1) {
+        if (A.n % R) continue;
+        A.G = A.n / R;
+        const unsigned nb = (unsigned)(((long)c->Vh * A.G + kTile - 1) / kTile);
+        launch_deo_mrhs(A, lf, R, nb, s);  // warm
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch_deo_mrhs(A, lf, R, nb, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        c->launches += 4;
+        if (t < best) {
+            best = t;
+            best_R = R;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_mr_mu);
+    g_mr_tune[key] = best_R;
+    return best_R;
+}
+
 int deo_mrhs_launch(lqcd_ctx *c, int P, int n, int recon, const void *in, void *out, cudaStream_t s)
 {
     if (int lr = links_ready(c)) return lr;
@@ -324,13 +378,14 @@ int deo_mrhs_launch(lqcd_ctx *c, int P, int n, int recon, const void *in, void *
     A.g = c->g;
     A.links = recon == 18 ? c->lnk_f18.ptr : c->lnk_f12.ptr;
     A.n = n;
-    const int R = pick_R(n);
-    A.G = n / R;
     A.P = P;
     A.in = (const float2 *)in;
     A.out = (float2 *)out;
+    const int lf = recon == 18 ? LF_F32_18 : LF_F32_12;
+    const int R = mrhs_pick_R(c, A, lf, s);
+    A.G = n / R;
     const unsigned nb = (unsigned)(((long)c->Vh * A.G + kTile - 1) / kTile);
-    launch_deo_mrhs(A, recon == 18 ? LF_F32_18 : LF_F32_12, R, nb, s);
+    launch_deo_mrhs(A, lf, R, nb, s);
     LQCD_CUDA(cudaGetLastError());
     c->launches += 1;
     return LQCD_OK;
