@@ -164,24 +164,33 @@ __device__ __forceinline__ void deo_site_df_staged(RingDF &R, uint32_t &q, bool 
 #pragma unroll
     for (int k = 0; k < 6; ++k) acc_zero(acc[k]);
     const int t = threadIdx.x;
+    // The neighbour spinor of the next half-hop is loaded before the current
+    // half-hop is computed, so its L2 latency overlaps the arithmetic (the
+    // stage release, a memory barrier for the compiler, would otherwise keep
+    // every gather behind the previous hop).
+    int f, b;
+    uint32_t nf, nb;
+    hop(g, S, 0, f, b, nf, nb);
+    float4 vf[3], vb[3];
+    load_spinor_df<SF>(in, f, Vh, nf, vf, bad);
 #pragma unroll 1
     for (int mu = 0; mu < 4; ++mu) {
-        int f, b;
-        uint32_t nf, nb;
-        hop(g, S, mu, f, b, nf, nb);
-        float4 U[9], v[3];
+        float4 U[9];
         float ch[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        load_spinor_df<SF>(in, f, Vh, nf, v, bad);
+        load_spinor_df<SF>(in, b, Vh, nb, vb, bad);
         int s = ring_acquire(R, q++, dead);
 #pragma unroll
         for (int c = 0; c < 9; ++c) U[c] = R.U[s][c][t];
-        hop_fwd_df(acc, ch, U, v);
+        hop_fwd_df(acc, ch, U, vf);
         ring_release(R, s);
-        load_spinor_df<SF>(in, b, Vh, nb, v, bad);
+        if (mu < 3) {
+            hop(g, S, mu + 1, f, b, nf, nb);
+            load_spinor_df<SF>(in, f, Vh, nf, vf, bad);
+        }
         s = ring_acquire(R, q++, dead);
 #pragma unroll
         for (int c = 0; c < 9; ++c) U[c] = R.U[s][c][t];
-        hop_bwd_df(acc, ch, U, v);
+        hop_bwd_df(acc, ch, U, vb);
         ring_release(R, s);
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc_flush(acc[k], ch[k]);
