@@ -685,9 +685,12 @@ def run_ours(args, rank, world, local):
     it = infos[-1]
     if args.only_solve:
         if rank == 0:
+            # per-kernel ms of the iteration (kernels launched one by one, CUDA events)
+            kms, _ = ctx.profile_iteration(MASS, shifts, bd, tol=TOL, iters=it["iters"])
             print(json.dumps({"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                               "iters": it["iters"], "max_true_resid": worst_res, "gpu_launches": launches,
+                              "kernel_ms": [round(m, 4) for m in kms],
                               "config": {"workload": WORKLOAD, "only_solve": True, "prec": args.solve_prec}}),
                   flush=True)
         ctx.close()

@@ -45,6 +45,25 @@ __device__ __forceinline__ int job_tile(const IterBatch<NJ> &B, int j)
     return (int)blockIdx.x - B.tile_start[j];
 }
 
+// s = (((0 + part[k0]) + part[k0 + d]) + part[k0 + 2d]) ..., k < n: the loads
+// go out eight at a time, so the sum waits on one round trip per eight
+// partials instead of one per partial; the order of the additions, and so
+// the result, is that of the plain strided loop.
+__device__ __forceinline__ double sum_strided(const double *part, int n, int k0, int d)
+{
+    double s = 0.0;
+    int k = k0;
+    for (; k + 7 * d < n; k += 8 * d) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(part + k + u * d);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; k < n; k += d) s += __ldcg(part + k);
+    return s;
+}
+
 // Sum per-tile partials in tile order and hand the total to fn (thread 0 of
 // the last block to finish).  Every block of the reduction must call this.
 template <class Fn>
@@ -62,8 +81,7 @@ __device__ __forceinline__ void reduce_finish(double *part, unsigned *ticket, in
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double s = 0.0;
-    for (int k = threadIdx.x; k < ntiles; k += blockDim.x) s += __ldcg(part + k);
+    double s = sum_strided(part, ntiles, (int)threadIdx.x, (int)blockDim.x);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
@@ -87,22 +105,21 @@ __device__ __forceinline__ void tile_finish(const IterJob &J, int tile, double v
 // As reduce_finish, but every thread of the last block calls fn(total), so
 // that the finaliser can spread per-shift work over the block.
 template <class Fn>
-__device__ __forceinline__ void tile_finish_block(const IterJob &J, int tile, double v, Fn fn)
+__device__ __forceinline__ void reduce_finish_block(double *part, unsigned *ticket, int n, int idx, double v, Fn fn)
 {
     __shared__ int s_last;
     __shared__ double s_red[32];
     __shared__ double s_tot;
     if (threadIdx.x == 0) {
-        J.part[tile] = v;
+        part[idx] = v;
         __threadfence();
-        const unsigned prev = atomicAdd(J.ticket, 1u);
-        s_last = (prev == (unsigned)(J.ntiles - 1));
+        const unsigned prev = atomicAdd(ticket, 1u);
+        s_last = (prev == (unsigned)(n - 1));
     }
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    double s = 0.0;
-    for (int k = threadIdx.x; k < J.ntiles; k += blockDim.x) s += __ldcg(J.part + k);
+    double s = sum_strided(part, n, (int)threadIdx.x, (int)blockDim.x);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xFFFFFFFFu, s, o);
     if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = s;
@@ -112,11 +129,17 @@ __device__ __forceinline__ void tile_finish_block(const IterJob &J, int tile, do
         const int nw = blockDim.x >> 5;
         for (int k = 0; k < nw; ++k) tot += s_red[k];
         s_tot = tot;
-        *J.ticket = 0u;
+        *ticket = 0u;
     }
     __syncthreads();
     fn(s_tot);
     __threadfence();
+}
+
+template <class Fn>
+__device__ __forceinline__ void tile_finish_block(const IterJob &J, int tile, double v, Fn fn)
+{
+    reduce_finish_block(J.part, J.ticket, J.ntiles, tile, v, fn);
 }
 
 __device__ __forceinline__ float2 split_scalar(double d)
@@ -168,16 +191,9 @@ __device__ inline void finalize_pq_warp(SolverState *st, double pq)
     const int lane = threadIdx.x & 31;
     const int ns = st->n_shift;
     const double rho = st->rho, alpha_old = st->alpha, beta_old = st->beta;
-    int act = 0;
-    double zo = 0.0, zc = 0.0, srel = 0.0;
-    if (lane < ns) {
-        act = st->active_next[lane];
-        if (act) {
-            zo = st->zeta[lane];
-            zc = st->zeta_new[lane];
-            srel = st->shift_rel[lane];
-        }
-    }
+    // every lane loads its shift's slots (kMaxShifts == 32) in one round trip
+    const int act = (lane < ns) ? st->active_next[lane] : 0;
+    const double zo = st->zeta[lane], zc = st->zeta_new[lane], srel = st->shift_rel[lane];
     const unsigned m = __ballot_sync(0xFFFFFFFFu, act);
     const double alpha = rho / pq;
     const bool ok = (pq > 0.0) && isfinite(alpha);
@@ -221,14 +237,20 @@ __device__ inline void finalize_rr_warp(SolverState *st, double rr)
     // loaded up front so that lane 0's decisions wait on no further round trip
     const int base = st->base, max_iter = st->max_iter;
     const double rel_stop2 = st->rel_stop2;
+    // lane l loads slot l of every per-shift array; lane k of the active list
+    // takes shift s = act_list[k]'s values by shuffle (one round trip)
+    const int s = st->act_list[lane] & (kMaxShifts - 1);
+    const double zc_l = st->zeta[lane], zn_l = st->zeta_new[lane];
+    const int it_l = st->shift_iters[lane];
+    const double zc = __shfl_sync(0xFFFFFFFFu, zc_l, s);
+    const double zn = __shfl_sync(0xFFFFFFFFu, zn_l, s);
+    const int its = __shfl_sync(0xFFFFFFFFu, it_l, s);
     int open = 0;
     if (ok && lane < n_act) {
-        const int s = st->act_list[lane];
-        const double zc = st->zeta[s], zn = st->zeta_new[s];
         const double ratio = zn / zc;
         st->beta_s_df[s] = split_scalar(beta * ratio * ratio);
         const bool conv = zn * zn * rr <= tol2_b2;
-        if (conv && st->shift_iters[s] == 0) st->shift_iters[s] = iters;
+        if (conv && its == 0) st->shift_iters[s] = iters;
         st->active_next[s] = conv ? 0 : 1;
         open = !conv;
     }
@@ -501,20 +523,28 @@ __device__ __forceinline__ void k1_staged_consume(RingDF &R, const IterBatch<NJ>
     }
 }
 
-// Consumers of K2: q = a p - D_eo t, the tile partial of <p, q>, and on the
-// job's last tile the tile-ordered total and the alpha / zeta finaliser.
+// Consumers of K2: q = a p - D_eo t and the tile partials of <p, q>; after
+// its last tile, the block that completes a job's tile count forms the
+// tile-ordered total and runs the alpha / zeta finaliser.  The tile partials
+// are plain stores; one fence and one ticket per job and block, after the
+// block's last tile, publish them, so no tile waits on a fence.
 struct K2Shared {
-    double red[kStagedConsumers / 32];
+    double red[2][kStagedConsumers / 32];
     double tot;
-    int last;
+    unsigned cnt[kMaxJobs];
+    unsigned long long last;
 };
 
 template <int NJ>
 __device__ __forceinline__ void k2_staged_consume(RingDF &R, K2Shared &sh, const IterBatch<NJ> &B, int ntot)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    static_assert(kMaxJobs <= 64, "job mask is 64 bits");
+    if (threadIdx.x < NJ) sh.cnt[threadIdx.x] = 0u;
+    consumer_sync();
     uint32_t q = 0;
     bool dead = false;
+    int nb = 0;
     for (int gt = (int)blockIdx.x; gt < ntot; gt += gridDim.x) {
         int j, tile;
         tile_of(B, gt, j, tile);
@@ -546,38 +576,57 @@ __device__ __forceinline__ void k2_staged_consume(RingDF &R, K2Shared &sh, const
                 acc_prod(dot, pv.z, pv.w, qi.x, qi.y);
             }
         }
-        // tile partial: the order of block_reduce_acc_n<256>
+        // tile partial: the order of block_reduce_acc_n<256>.  The warp sums
+        // alternate between two buffers: thread 0 has read buffer b before it
+        // reaches the barrier of the next tile, which every warp passes before
+        // it writes b again.
+        const int b = nb & 1;
         warp_reduce_acc(dot);
-        if (lane == 0) sh.red[w] = (double)dot.s + (double)dot.c;
+        if (lane == 0) sh.red[b][w] = (double)dot.s + (double)dot.c;
         consumer_sync();
         if (threadIdx.x == 0) {
             double v = 0.0;
 #pragma unroll
-            for (int k = 0; k < kStagedConsumers / 32; ++k) v += sh.red[k];
+            for (int k = 0; k < kStagedConsumers / 32; ++k) v += sh.red[b][k];
             J.part[tile] = v;
-            __threadfence();
-            const unsigned prev = atomicAdd(J.ticket, 1u);
-            sh.last = (prev == (unsigned)(J.ntiles - 1));
+            sh.cnt[j] += 1u;
         }
-        consumer_sync();
-        if (!sh.last) continue;
-        // last tile of the job: partials in tile order (the order of tile_finish_block)
+        ++nb;
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long last = 0ull;
         __threadfence();
-        double sum = 0.0;
-        for (int k = threadIdx.x; k < J.ntiles; k += kStagedConsumers) sum += __ldcg(J.part + k);
+        for (int j = 0; j < B.njobs; ++j) {
+            const unsigned n = sh.cnt[j];
+            if (!n) continue;
+            const unsigned prev = atomicAdd(B.job[j].ticket, n);
+            if (prev + n == (unsigned)B.job[j].ntiles) last |= 1ull << j;
+        }
+        sh.last = last;
+    }
+    consumer_sync();
+    unsigned long long last = sh.last;
+    while (last) {
+        const int j = __ffsll((long long)last) - 1;
+        last &= last - 1ull;
+        const IterJob &J = B.job[j];
+        // partials in tile order (the order of tile_finish_block)
+        __threadfence();
+        double sum = sum_strided(J.part, J.ntiles, (int)threadIdx.x, kStagedConsumers);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
-        if (lane == 0) sh.red[w] = sum;
+        if (lane == 0) sh.red[0][w] = sum;
         consumer_sync();
         if (threadIdx.x == 0) {
             double tot = 0.0;
-            for (int k = 0; k < kStagedConsumers / 32; ++k) tot += sh.red[k];
+            for (int k = 0; k < kStagedConsumers / 32; ++k) tot += sh.red[0][k];
             sh.tot = tot;
             *J.ticket = 0u;
         }
         consumer_sync();
-        if (threadIdx.x < 32) finalize_pq_warp(st, sh.tot);
+        if (threadIdx.x < 32) finalize_pq_warp(J.st, sh.tot);
         __threadfence();
+        consumer_sync();
     }
 }
 
