@@ -71,6 +71,7 @@ int validate_opts(const lqcd_opts *o)
     if (o->check_every < 1 || o->check_every > 4096) return fail(LQCD_EINVAL, "opts.check_every must be in 1..4096");
     if (!(o->fp64_until >= 0.0 && o->fp64_until < 1.0)) return fail(LQCD_EINVAL, "opts.fp64_until must be in [0,1)");
     if (o->staged != 0 && o->staged != 1) return fail(LQCD_EINVAL, "opts.staged must be 0 or 1");
+    if (o->pdl != 0 && o->pdl != 1) return fail(LQCD_EINVAL, "opts.pdl must be 0 or 1");
     return LQCD_OK;
 }
 
@@ -90,6 +91,7 @@ void lqcd_default_opts(lqcd_opts *o)
     o->check_every = 32;
     o->fp64_until = 3e-4;
     o->staged = 1;
+    o->pdl = 0;
 }
 
 const char *lqcd_last_error(void) { return g_err.c_str(); }

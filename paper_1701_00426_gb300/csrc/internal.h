@@ -180,7 +180,9 @@ int job_switch_to_f32(JobRun &D, JobRun &F, cudaStream_t s);
 int validate_opts(const lqcd_opts *o);
 void job_fill(const JobRun &J, IterJob &out);
 int job_finish(JobRun &J, cudaStream_t s);
-void launch_iteration_packed(const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s);
+// One iteration of a packed batch; pdl: programmatic dependent launches,
+// chained: the previous launch on s is the batch's previous iteration.
+void launch_iteration_packed(const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s, bool pdl, bool chained);
 int run_packed_until_halt(lqcd_ctx *c, const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s);
 int mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, const double *const *shifts,
                       const int *n_shift, const double *tol, const double *const *b, double *const *x,

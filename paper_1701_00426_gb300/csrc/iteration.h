@@ -55,7 +55,7 @@ struct IterJob {
 template <int NJ>
 struct IterBatch {
     int njobs;
-    int max_shift;              // largest n_shift of the jobs (grid height of the shift update)
+    int max_shift;              // largest n_shift of the jobs
     int interleave;             // 1: jobs on one lattice, block b belongs to job b % njobs
     int tile_start[NJ + 1];
     IterJob job[NJ];

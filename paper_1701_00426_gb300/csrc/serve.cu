@@ -231,13 +231,14 @@ int lqcd_server::tick()
         const unsigned char *p = (const unsigned char *)&B[g];
         for (size_t k = 0; k < sizeof B[g]; ++k) key = (key ^ p[k]) * 1099511628211ull;
         key = (key ^ (uint64_t)lf[g]) * 1099511628211ull;
+        key = (key ^ (uint64_t)opts.pdl) * 1099511628211ull;
         if (key != batch_key[g] || !exec[g]) {
             if (exec[g]) cudaGraphExecDestroy(exec[g]);
             exec[g] = nullptr;
             cudaGraph_t gr;
             e = cudaStreamBeginCapture(stream, cudaStreamCaptureModeThreadLocal);
             if (e != cudaSuccess) return cuda_fail(e, "serve capture");
-            for (int k = 0; k < chunk; ++k) launch_iteration_packed(B[g], g, lf[g], stream);
+            for (int k = 0; k < chunk; ++k) launch_iteration_packed(B[g], g, lf[g], stream, opts.pdl != 0, k > 0);
             e = cudaStreamEndCapture(stream, &gr);
             if (e != cudaSuccess) return cuda_fail(e, "serve capture");
             e = cudaGraphInstantiate(&exec[g], gr, 0);

@@ -419,39 +419,64 @@ static bool batch_staged(const IterBatch<NJ> &B)
 }
 
 // ------------------------------------------------------------------ iteration chunks
-// Kernel k (0: K1 .. 3: K4) of one iteration.
-template <int NJ>
-static void launch_kernel_k(const IterBatch<NJ> &B, int k, int ntot, int vp, int lf, cudaStream_t s)
+// Launch with programmatic stream serialisation when dep is set: the kernel
+// may start while the previous kernel of the stream drains (its prologue
+// overlaps that kernel's tail; see dep_wait in solver_kernels.cuh).  Only
+// for a kernel whose predecessor in the stream is the previous kernel of the
+// same iteration sequence.
+template <class... P, class... A>
+static void launch_dep(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool dep, A... args)
 {
-    const dim3 g4((unsigned)ntot, (unsigned)(B.max_shift > 0 ? B.max_shift : 1));
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = dep ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+// Kernel k (0: K1 .. 3: K4) of one iteration; dep: launch it dependent on
+// the kernel before it (K1: on the previous iteration's K4).
+template <int NJ>
+static void launch_kernel_k(const IterBatch<NJ> &B, int k, int ntot, int vp, int lf, cudaStream_t s, bool dep)
+{
+    const dim3 g1((unsigned)ntot), tb(kIterThreads);
     if (vp == VP_DF) {
         const int sb = (k < 2 && batch_staged(B)) ? std::min(ntot, staged_solver_blocks()) : 0;
-        if (k == 0 && sb > 0) k_it_deo1_st<NJ><<<sb, kStagedThreads, kStagedIterSmem, s>>>(B, ntot);
-        if (k == 1 && sb > 0) k_it_deo2_st<NJ><<<sb, kStagedThreads, kStagedIterSmem, s>>>(B, ntot);
-        if (k == 0 && sb == 0) k_it_deo1<NJ, VP_DF, LF_DF18><<<ntot, kIterThreads, 0, s>>>(B);
-        if (k == 1 && sb == 0) k_it_deo2<NJ, VP_DF, LF_DF18><<<ntot, kIterThreads, 0, s>>>(B);
-        if (k == 2) k_it_upd_r<NJ, VP_DF><<<ntot, kIterThreads, 0, s>>>(B);
-        if (k == 3) k_it_upd_shifts<NJ, VP_DF><<<g4, kIterThreads, 0, s>>>(B);
+        const dim3 gs((unsigned)sb), ts(kStagedThreads);
+        if (k == 0 && sb > 0) launch_dep(k_it_deo1_st<NJ>, gs, ts, kStagedIterSmem, s, dep, B, ntot);
+        if (k == 1 && sb > 0) launch_dep(k_it_deo2_st<NJ>, gs, ts, kStagedIterSmem, s, dep, B, ntot);
+        if (k == 0 && sb == 0) launch_dep(k_it_deo1<NJ, VP_DF, LF_DF18>, g1, tb, 0, s, dep, B);
+        if (k == 1 && sb == 0) launch_dep(k_it_deo2<NJ, VP_DF, LF_DF18>, g1, tb, 0, s, dep, B);
+        if (k == 2) launch_dep(k_it_upd_r<NJ, VP_DF>, g1, tb, 0, s, dep, B);
+        if (k == 3) launch_dep(k_it_upd_shifts<NJ, VP_DF>, g1, tb, 0, s, dep, B);
         return;
     }
     if (k == 0) {
-        if (lf == LF_F32_18) k_it_deo1<NJ, VP_F32, LF_F32_18><<<ntot, kIterThreads, 0, s>>>(B);
-        else if (lf == LF_F32_12) k_it_deo1<NJ, VP_F32, LF_F32_12><<<ntot, kIterThreads, 0, s>>>(B);
-        else k_it_deo1<NJ, VP_F32, LF_F16_12><<<ntot, kIterThreads, 0, s>>>(B);
+        if (lf == LF_F32_18) launch_dep(k_it_deo1<NJ, VP_F32, LF_F32_18>, g1, tb, 0, s, dep, B);
+        else if (lf == LF_F32_12) launch_dep(k_it_deo1<NJ, VP_F32, LF_F32_12>, g1, tb, 0, s, dep, B);
+        else launch_dep(k_it_deo1<NJ, VP_F32, LF_F16_12>, g1, tb, 0, s, dep, B);
     }
     if (k == 1) {
-        if (lf == LF_F32_18) k_it_deo2<NJ, VP_F32, LF_F32_18><<<ntot, kIterThreads, 0, s>>>(B);
-        else if (lf == LF_F32_12) k_it_deo2<NJ, VP_F32, LF_F32_12><<<ntot, kIterThreads, 0, s>>>(B);
-        else k_it_deo2<NJ, VP_F32, LF_F16_12><<<ntot, kIterThreads, 0, s>>>(B);
+        if (lf == LF_F32_18) launch_dep(k_it_deo2<NJ, VP_F32, LF_F32_18>, g1, tb, 0, s, dep, B);
+        else if (lf == LF_F32_12) launch_dep(k_it_deo2<NJ, VP_F32, LF_F32_12>, g1, tb, 0, s, dep, B);
+        else launch_dep(k_it_deo2<NJ, VP_F32, LF_F16_12>, g1, tb, 0, s, dep, B);
     }
-    if (k == 2) k_it_upd_r<NJ, VP_F32><<<ntot, kIterThreads, 0, s>>>(B);
-    if (k == 3) k_it_upd_shifts<NJ, VP_F32><<<g4, kIterThreads, 0, s>>>(B);
+    if (k == 2) launch_dep(k_it_upd_r<NJ, VP_F32>, g1, tb, 0, s, dep, B);
+    if (k == 3) launch_dep(k_it_upd_shifts<NJ, VP_F32>, g1, tb, 0, s, dep, B);
 }
 
+// One iteration.  K2..K4 always follow their predecessor kernel; K1 does
+// only when `chained` (the previous iteration's K4 is the last launch).
 template <int NJ>
-static void launch_iteration(const IterBatch<NJ> &B, int ntot, int vp, int lf, cudaStream_t s)
+static void launch_iteration(const IterBatch<NJ> &B, int ntot, int vp, int lf, cudaStream_t s, bool pdl, bool chained)
 {
-    for (int k = 0; k < 4; ++k) launch_kernel_k<NJ>(B, k, ntot, vp, lf, s);
+    for (int k = 0; k < 4; ++k) launch_kernel_k<NJ>(B, k, ntot, vp, lf, s, pdl && (k > 0 || chained));
 }
 
 void GraphCache::reset()
@@ -509,12 +534,14 @@ static int chunk_graph(lqcd_ctx *c, const IterBatch<NJ> &B, int vp, int lf, int 
     key = fnv1a(&vp, sizeof vp, key);
     key = fnv1a(&lf, sizeof lf, key);
     key = fnv1a(&chunk, sizeof chunk, key);
+    const int pdl = c->opts.pdl;
+    key = fnv1a(&pdl, sizeof pdl, key);
     key ^= (uint64_t)NJ * 0x9E3779B97F4A7C15ull;
     out = c->graph.find(key);
     if (out) return LQCD_OK;
     cudaGraph_t g;
     LQCD_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-    for (int k = 0; k < chunk; ++k) launch_iteration<NJ>(B, ntot, vp, lf, s);
+    for (int k = 0; k < chunk; ++k) launch_iteration<NJ>(B, ntot, vp, lf, s, pdl != 0, k > 0);
     cudaError_t e = cudaStreamEndCapture(s, &g);
     if (e != cudaSuccess) return cuda_fail(e, "graph capture");
     e = cudaGraphInstantiate(&out, g, 0);
@@ -1142,9 +1169,9 @@ int job_switch_to_f32(JobRun &D, JobRun &F, cudaStream_t s)
 }
 
 // One packed iteration launch over several jobs (serving ticks).
-void launch_iteration_packed(const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s)
+void launch_iteration_packed(const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s, bool pdl, bool chained)
 {
-    launch_iteration<kMaxJobs>(B, B.tile_start[B.njobs], vp, lf, s);
+    launch_iteration<kMaxJobs>(B, B.tile_start[B.njobs], vp, lf, s, pdl, chained);
 }
 
 int run_packed_until_halt(lqcd_ctx *c, const IterBatch<kMaxJobs> &B, int vp, int lf, cudaStream_t s)
@@ -1237,7 +1264,7 @@ int profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n_shif
         cudaEvent_t *E = &ev[5 * (size_t)k];
         cudaEventRecord(E[0], s);
         for (int q = 0; q < 4; ++q) {
-            launch_kernel_k<1>(B, q, ntot, J.vp, J.lf, s);
+            launch_kernel_k<1>(B, q, ntot, J.vp, J.lf, s, false);
             cudaEventRecord(E[q + 1], s);
         }
         c->launches += 4;

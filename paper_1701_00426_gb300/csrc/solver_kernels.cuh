@@ -356,11 +356,25 @@ __device__ __forceinline__ double block_reduce_acc_n(Acc2 A, double *smem)
     return r;
 }
 
+// Programmatic dependent launch.  The iteration kernels may be launched with
+// programmatic stream serialisation: the next kernel of the stream then
+// starts while this one drains.  dep_wait() returns once the previous kernel
+// has completed and its writes are visible; dep_launch() lets the next
+// kernel start.  Every iteration kernel calls dep_launch() only after
+// dep_wait(), so the code of a kernel before its dep_wait() (its prologue)
+// may read what the kernel two launches back, or any earlier one, wrote, but
+// nothing the previous kernel writes; it writes nothing.  Prologue loads
+// bypass L1 (ld.global.cg).  Without the launch attribute both are no-ops.
+__device__ __forceinline__ void dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ------------------------------------------------------------------ K1
 template <int NJ, int VP, int LF>
 __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo1(const __grid_constant__ IterBatch<NJ> B)
 {
     using T = typename VecT<VP>::T;
+    dep_wait();
+    dep_launch();
     const int j = find_job(B);
     const IterJob &J = B.job[j];
     SolverState *st = J.st;
@@ -395,6 +409,8 @@ __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo2(const 
 {
     using T = typename VecT<VP>::T;
     __shared__ double s_red[kIterThreads / 32];
+    dep_wait();
+    dep_launch();
     const int j = find_job(B);
     const IterJob &J = B.job[j];
     SolverState *st = J.st;
@@ -483,7 +499,9 @@ __device__ __forceinline__ void staged_iter_produce(RingDF &R, const IterBatch<N
             int j, tile;
             tile_of(B, gt, j, tile);
             const IterJob &J = B.job[j];
-            if (J.st->halt) continue;
+            // prologue read (no dep_wait on this lane): the halt word is
+            // written by finalisers at least two launches back
+            if (__ldcg(&J.st->halt)) continue;
             base = staged_tile_base(J.links_st, P, J.ntiles, tile);
             gt += gridDim.x;
             return true;
@@ -496,6 +514,8 @@ __device__ __forceinline__ void staged_iter_produce(RingDF &R, const IterBatch<N
 template <int NJ>
 __device__ __forceinline__ void k1_staged_consume(RingDF &R, const IterBatch<NJ> &B, int ntot)
 {
+    dep_wait();
+    dep_launch();
     uint32_t q = 0;
     bool dead = false;
     for (int gt = (int)blockIdx.x; gt < ntot; gt += gridDim.x) {
@@ -540,6 +560,8 @@ __device__ __forceinline__ void k2_staged_consume(RingDF &R, K2Shared &sh, const
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     static_assert(kMaxJobs <= 64, "job mask is 64 bits");
+    dep_wait();
+    dep_launch();
     if (threadIdx.x < NJ) sh.cnt[threadIdx.x] = 0u;
     consumer_sync();
     uint32_t q = 0;
@@ -674,21 +696,29 @@ __global__ void __launch_bounds__(kIterThreads) k_it_upd_r(const __grid_constant
     __shared__ double s_red[kIterThreads / 32];
     const int j = find_job(B);
     const IterJob &J = B.job[j];
-    SolverState *st = J.st;
-    if (st->halt) return;
     const int Vh = J.g.Vh;
     const int tile = job_tile(B, j);
     const int i = tile * kSites + threadIdx.x;
+    T *r = (T *)J.r;
+    // prologue: r was last written by the previous iteration's K3
+    T rp[3];
+    if (i < Vh) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) rp[c] = __ldcg(r + (size_t)c * Vh + i);
+    }
+    dep_wait();
+    dep_launch();
+    SolverState *st = J.st;
+    if (st->halt) return;
     Acc2 nrm;
     acc_zero(nrm);
     if (i < Vh) {
-        T *r = (T *)J.r;
         const T *q = (const T *)J.q;
         if constexpr (VP == VP_DF) {
             const float2 na = df_neg(st->alpha_df);
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float4 rv = r[(size_t)c * Vh + i], qv = q[(size_t)c * Vh + i];
+                const float4 rv = rp[c], qv = q[(size_t)c * Vh + i];
                 const float2 x = df_fma(na, make_float2(qv.x, qv.y), make_float2(rv.x, rv.y));
                 const float2 y = df_fma(na, make_float2(qv.z, qv.w), make_float2(rv.z, rv.w));
                 r[(size_t)c * Vh + i] = make_float4(x.x, x.y, y.x, y.y);
@@ -700,7 +730,7 @@ __global__ void __launch_bounds__(kIterThreads) k_it_upd_r(const __grid_constant
             float d = 0.f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float2 rv = r[(size_t)c * Vh + i], qv = q[(size_t)c * Vh + i];
+                const float2 rv = rp[c], qv = q[(size_t)c * Vh + i];
                 const float2 w = make_float2(__fmaf_rn(na, qv.x, rv.x), __fmaf_rn(na, qv.y, rv.y));
                 r[(size_t)c * Vh + i] = w;
                 d = __fmaf_rn(w.x, w.x, __fmaf_rn(w.y, w.y, d));
@@ -715,48 +745,84 @@ __global__ void __launch_bounds__(kIterThreads) k_it_upd_r(const __grid_constant
 }
 
 // ------------------------------------------------------------------ K4
-// 2-D grid: blockIdx.x = tile, blockIdx.y = slot k of the active shift list;
-// one thread per (site, shift), so the streams of all active shifts are in
-// flight together.  Slots beyond the active count exit at once.
+// x_s += alpha_s p_s, p_s = zeta_s r + beta_s p_s for every active shift s.
+// One thread per site walks the active list: r is read once per site, the
+// scalar chain (do_k4, the active list) is paid once per thread, and the
+// next shift's x_s, p_s loads are issued before this shift's stores, so two
+// shifts' streams are in flight per thread.  Per element the arithmetic is
+// that of one thread per (site, shift).
+template <int VP>
+struct K4Slot {
+    using T = typename VecT<VP>::T;
+    T p[3], x[3];
+};
+
+template <int VP>
+__device__ __forceinline__ void k4_load(K4Slot<VP> &L, const typename VecT<VP>::T *ps, const typename VecT<VP>::T *x,
+                                        size_t off, int Vh)
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        L.p[c] = ps[off + (size_t)c * Vh];
+        L.x[c] = x[off + (size_t)c * Vh];
+    }
+}
+
 template <int NJ, int VP>
 __global__ void __launch_bounds__(kIterThreads) k_it_upd_shifts(const __grid_constant__ IterBatch<NJ> B)
 {
     using T = typename VecT<VP>::T;
+    dep_wait();
+    dep_launch();
     const int j = find_job(B);
     const IterJob &J = B.job[j];
     const SolverState *st = J.st;
     if (!st->do_k4) return;
-    const int k = blockIdx.y;
-    if (k >= st->n_act) return;
+    const int n_act = st->n_act;
     const int Vh = J.g.Vh;
     const int i = job_tile(B, j) * kSites + threadIdx.x;
-    if (i >= Vh) return;
-    const int s = st->act_list[k];
-    const size_t off = (size_t)s * 3 * Vh + i;
+    if (i >= Vh || n_act <= 0) return;
     T *x = (T *)J.x, *ps = (T *)J.ps;
     const T *r = (const T *)J.r;
-    if constexpr (VP == VP_DF) {
-        const float2 as = st->alpha_s_df[s], zn = st->zeta_new_df[s], bs = st->beta_s_df[s];
+    T rv[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float4 rv = r[(size_t)c * Vh + i];
-            const float4 pv = ps[off + (size_t)c * Vh], xv = x[off + (size_t)c * Vh];
-            const float2 xr = df_fma(as, make_float2(pv.x, pv.y), make_float2(xv.x, xv.y));
-            const float2 xi = df_fma(as, make_float2(pv.z, pv.w), make_float2(xv.z, xv.w));
-            const float2 pr = df_mul2(zn, make_float2(rv.x, rv.y), bs, make_float2(pv.x, pv.y));
-            const float2 pi = df_mul2(zn, make_float2(rv.z, rv.w), bs, make_float2(pv.z, pv.w));
-            x[off + (size_t)c * Vh] = make_float4(xr.x, xr.y, xi.x, xi.y);
-            ps[off + (size_t)c * Vh] = make_float4(pr.x, pr.y, pi.x, pi.y);
+    for (int c = 0; c < 3; ++c) rv[c] = r[(size_t)c * Vh + i];
+    int s = st->act_list[0];
+    K4Slot<VP> cur;
+    k4_load<VP>(cur, ps, x, (size_t)s * 3 * Vh + i, Vh);
+#pragma unroll 1
+    for (int k = 0; k < n_act; ++k) {
+        const size_t off = (size_t)s * 3 * Vh + i;
+        K4Slot<VP> nxt;
+        int sn = s;
+        if (k + 1 < n_act) {
+            sn = st->act_list[k + 1];
+            k4_load<VP>(nxt, ps, x, (size_t)sn * 3 * Vh + i, Vh);
         }
-    } else {
-        const float as = st->alpha_s_df[s].x, zn = st->zeta_new_df[s].x, bs = st->beta_s_df[s].x;
+        if constexpr (VP == VP_DF) {
+            const float2 as = st->alpha_s_df[s], zn = st->zeta_new_df[s], bs = st->beta_s_df[s];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float2 rv = r[(size_t)c * Vh + i];
-            const float2 pv = ps[off + (size_t)c * Vh], xv = x[off + (size_t)c * Vh];
-            x[off + (size_t)c * Vh] = make_float2(__fmaf_rn(as, pv.x, xv.x), __fmaf_rn(as, pv.y, xv.y));
-            ps[off + (size_t)c * Vh] = make_float2(__fmaf_rn(zn, rv.x, bs * pv.x), __fmaf_rn(zn, rv.y, bs * pv.y));
+            for (int c = 0; c < 3; ++c) {
+                const float4 pv = cur.p[c], xv = cur.x[c];
+                const float2 xr = df_fma(as, make_float2(pv.x, pv.y), make_float2(xv.x, xv.y));
+                const float2 xi = df_fma(as, make_float2(pv.z, pv.w), make_float2(xv.z, xv.w));
+                const float2 pr = df_mul2(zn, make_float2(rv[c].x, rv[c].y), bs, make_float2(pv.x, pv.y));
+                const float2 pi = df_mul2(zn, make_float2(rv[c].z, rv[c].w), bs, make_float2(pv.z, pv.w));
+                x[off + (size_t)c * Vh] = make_float4(xr.x, xr.y, xi.x, xi.y);
+                ps[off + (size_t)c * Vh] = make_float4(pr.x, pr.y, pi.x, pi.y);
+            }
+        } else {
+            const float as = st->alpha_s_df[s].x, zn = st->zeta_new_df[s].x, bs = st->beta_s_df[s].x;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 pv = cur.p[c], xv = cur.x[c];
+                x[off + (size_t)c * Vh] = make_float2(__fmaf_rn(as, pv.x, xv.x), __fmaf_rn(as, pv.y, xv.y));
+                ps[off + (size_t)c * Vh] =
+                    make_float2(__fmaf_rn(zn, rv[c].x, bs * pv.x), __fmaf_rn(zn, rv[c].y, bs * pv.y));
+            }
         }
+        cur = nxt;
+        s = sn;
     }
 }
 

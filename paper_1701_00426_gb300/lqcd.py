@@ -56,7 +56,7 @@ EXPORTED = [
 class lqcd_opts(ctypes.Structure):
     _fields_ = [("prec", ctypes.c_int), ("recon", ctypes.c_int), ("delta_reliable", ctypes.c_double),
                 ("max_iter", ctypes.c_int), ("check_every", ctypes.c_int), ("fp64_until", ctypes.c_double),
-                ("staged", ctypes.c_int)]
+                ("staged", ctypes.c_int), ("pdl", ctypes.c_int)]
 
 
 class lqcd_solve_info(ctypes.Structure):

@@ -40,7 +40,7 @@ def test_binding_loads_and_reports_version(lib):
     o = lqcd.default_opts()
     assert o.prec == lqcd.PREC_FP64 and o.recon == 18 and o.max_iter == 20000
     assert o.fp64_until == 3e-4 and o.check_every == 32 and o.delta_reliable == 0.1
-    assert o.staged == 1
+    assert o.staged == 1 and o.pdl == 0
 
 
 def test_create_rejects_odd_sides_without_gpu(lib):
@@ -61,6 +61,9 @@ def test_create_rejects_odd_sides_without_gpu(lib):
     o = lqcd.default_opts(staged=2)
     st = L.lqcd_create((ctypes.c_int * 4)(4, 4, 4, 4), ctypes.byref(o), ctypes.byref(h))
     assert st == lqcd.LQCD_EINVAL and b"staged" in L.lqcd_last_error()
+    o = lqcd.default_opts(pdl=-1)
+    st = L.lqcd_create((ctypes.c_int * 4)(4, 4, 4, 4), ctypes.byref(o), ctypes.byref(h))
+    assert st == lqcd.LQCD_EINVAL and b"pdl" in L.lqcd_last_error()
 
 
 def test_no_oracle_in_product_path():
