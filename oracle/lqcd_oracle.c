@@ -773,6 +773,261 @@ double oracle_mom_energy(const int N[4], const cplx *mom)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Stout smearing of the fermion links (Sec. 2.1: stout-improved staggered  */
+/* action, Ref. Morningstar:2003gk; Sec. 2.2: up to a few stout levels)      */
+/* ------------------------------------------------------------------------ */
+
+/* Reading (the paper cites the method and prints no formula): isotropic
+ * smearing with one weight rho per level,
+ *   C_mu(x) = rho sum_{nu != mu} [ U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+ *                                 + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) ],
+ *   Omega = C U^dag,  Q = (i/2)(Omega^dag - Omega) - (i/6) Tr(Omega^dag - Omega),
+ *   U'_mu(x) = exp(i Q_mu(x)) U_mu(x);
+ * n levels apply the map n times.  Q is Hermitian and traceless, so U' stays
+ * in SU(3). */
+static void stout_C(const int N[4], const cplx *links, const int x[4], int mu, double rho, cplx *C)
+{
+    cplx P[9];
+    for (int i = 0; i < 9; ++i) C[i] = 0;
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        const int dir[3] = {nu, mu, nu};
+        const int up[3] = {1, 1, -1}, dn[3] = {-1, 1, 1};
+        path_product(N, links, x, 3, dir, up, P);
+        for (int i = 0; i < 9; ++i) C[i] += rho * P[i];
+        path_product(N, links, x, 3, dir, dn, P);
+        for (int i = 0; i < 9; ++i) C[i] += rho * P[i];
+    }
+}
+
+static void stout_Q(const cplx *C, const cplx *U, cplx *Q)
+{
+    cplx Ud[9], Om[9];
+    m_dag(U, Ud);
+    m_mul(C, Ud, Om);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) Q[i * 3 + j] = 0.5 * I * (conj(Om[j * 3 + i]) - Om[i * 3 + j]);
+    const cplx tr = (Q[0] + Q[4] + Q[8]) / 3.0;
+    Q[0] -= tr; Q[4] -= tr; Q[8] -= tr;
+}
+
+/* out = one stout level of in (both [4][V][3][3]). */
+void oracle_stout_smear(const int N[4], const cplx *in, double rho, cplx *out)
+{
+    const long V = volume(N);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < V; ++n) {
+        int x[4];
+        long r = n;
+        for (int m = 0; m < 4; ++m) { x[m] = (int)(r % N[m]); r /= N[m]; }
+        for (int mu = 0; mu < 4; ++mu) {
+            cplx C[9], Q[9], E[9];
+            stout_C(N, in, x, mu, rho, C);
+            const cplx *U = in + ((long)mu * V + n) * 9;
+#if ORACLE_MUTANT == 18
+            /* planted: the links move with exp(-iQ) */
+            stout_Q(C, U, Q);
+            oracle_exp_iH(Q, -1.0, E);
+#else
+            stout_Q(C, U, Q);
+            oracle_exp_iH(Q, 1.0, E);
+#endif
+            m_mul(E, U, out + ((long)mu * V + n) * 9);
+        }
+    }
+}
+
+/* exp of an n x n complex matrix Z (n <= 6): power series after scaling by
+ * 2^-k until the 1-norm is below 1/4, then k squarings. */
+static void expm_n(int n, const cplx *Z, cplx *E)
+{
+    cplx S[36], T[36], W[36], Zs[36];
+    double nrm = 0.0;
+    for (int j = 0; j < n; ++j) {
+        double c = 0.0;
+        for (int i = 0; i < n; ++i) c += cabs(Z[i * n + j]);
+        if (c > nrm) nrm = c;
+    }
+    int k = 0;
+    while (nrm > 0.25 && k < 60) { nrm *= 0.5; ++k; }
+    for (int i = 0; i < n * n; ++i) {
+        Zs[i] = ldexp(1.0, -k) * Z[i];
+        S[i] = T[i] = (i / n == i % n) ? 1.0 : 0.0;
+    }
+    for (int m = 1; m < 40; ++m) {
+        double tn = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                cplx a = 0;
+                for (int l = 0; l < n; ++l) a += T[i * n + l] * Zs[l * n + j];
+                W[i * n + j] = a / m;
+            }
+        for (int i = 0; i < n * n; ++i) { T[i] = W[i]; S[i] += T[i]; tn += cabs(T[i]); }
+        if (tn < 1e-18) break;
+    }
+    for (int q = 0; q < k; ++q) {
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                cplx a = 0;
+                for (int l = 0; l < n; ++l) a += S[i * n + l] * S[l * n + j];
+                W[i * n + j] = a;
+            }
+        memcpy(S, W, sizeof(cplx) * n * n);
+    }
+    memcpy(E, S, sizeof(cplx) * n * n);
+}
+
+/* D = d/dt exp(X + t A) at t = 0 (the Frechet derivative of exp at X in
+ * the direction A) = the upper-right 3x3 block of exp([[X, A], [0, X]]). */
+static void frechet_exp(const cplx *X, const cplx *A, cplx *D)
+{
+    cplx Z[36], E[36];
+    for (int i = 0; i < 36; ++i) Z[i] = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            Z[i * 6 + j] = X[i * 3 + j];
+            Z[(i + 3) * 6 + j + 3] = X[i * 3 + j];
+            Z[i * 6 + j + 3] = A[i * 3 + j];
+        }
+    expm_n(6, Z, E);
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) D[i * 3 + j] = E[i * 6 + j + 3];
+}
+
+static void m_add_scaled(cplx *G, double a, const cplx *B)
+{
+    for (int i = 0; i < 9; ++i) G[i] += a * B[i];
+}
+
+/* Force on the links of one stout level from the force on the smeared links
+ * (Ref. Morningstar:2003gk, restated from the definitions).  Fp: Hermitian
+ * traceless, d/de S(exp(i e X) U') = sum Tr(X Fp) for U' = smear(U); output
+ * F, the same for U.  With Sigma' = -i U'^dag Fp, dS = Re Tr(Sigma' dU')
+ * summed over the links for every variation that keeps U' in SU(3), and
+ *   dU' = exp(iQ) dU + Dexp_{iQ}[i dQ] U,
+ *   Re Tr(Sigma' Dexp_{iQ}[i dQ] U) = Re Tr(i Gamma dQ),  Gamma = Dexp_{iQ}[U Sigma']
+ *     (the derivative of exp is self-adjoint under Tr(A B)),
+ *   Re Tr(i Gamma dQ) = Re Tr(L dOmega),  L = traceless anti-Hermitian part of Gamma,
+ *   dOmega = dC U^dag + C dU^dag.
+ * The gradient G_mu(x) of S (dS = Re Tr(G dU) over the links) collects
+ *   Sigma' exp(iQ) - C^dag L         at the link itself, and
+ *   for each staple product P1 P2 P3 of C_mu(x), with M = U_mu(x)^dag L_mu(x)
+ *   (times rho): Re Tr(M A dX B) -> G_X += B M A, Re Tr(M A dX^dag B) ->
+ *   G_X += A^dag M^dag B^dag.
+ * Then F = traceless part of (i/2)(U G - G^dag U^dag). */
+void oracle_stout_force(const int N[4], const cplx *links, double rho, const cplx *Fp, cplx *F)
+{
+    const long V = volume(N), nl = 4 * V;
+    cplx *G = calloc((size_t)nl * 9, sizeof(cplx));
+    cplx *Mall = malloc(sizeof(cplx) * nl * 9);
+    /* local terms and M per link */
+    for (long n = 0; n < V; ++n) {
+        int x[4];
+        long r = n;
+        for (int m = 0; m < 4; ++m) { x[m] = (int)(r % N[m]); r /= N[m]; }
+        for (int mu = 0; mu < 4; ++mu) {
+            const long l = (long)mu * V + n;
+            const cplx *U = links + l * 9;
+            cplx C[9], Q[9], E[9], Up[9], Upd[9], Sp[9], iQ[9], USp[9], Gam[9], L[9], Cd[9], t[9];
+            stout_C(N, links, x, mu, rho, C);
+            stout_Q(C, U, Q);
+            oracle_exp_iH(Q, 1.0, E);
+            m_mul(E, U, Up);
+            m_dag(Up, Upd);
+            m_mul(Upd, Fp + l * 9, Sp);
+            for (int i = 0; i < 9; ++i) { Sp[i] *= -I; iQ[i] = I * Q[i]; }
+            m_mul(U, Sp, USp);
+            frechet_exp(iQ, USp, Gam);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) L[i * 3 + j] = 0.5 * (Gam[i * 3 + j] - conj(Gam[j * 3 + i]));
+            const cplx tr = (L[0] + L[4] + L[8]) / 3.0;
+            L[0] -= tr; L[4] -= tr; L[8] -= tr;
+            m_mul(Sp, E, t);
+            m_add_scaled(G + l * 9, 1.0, t);
+            m_dag(C, Cd);
+            m_mul(Cd, L, t);
+#if ORACLE_MUTANT == 19
+            /* planted: the C^dag L term enters with the wrong sign */
+            m_add_scaled(G + l * 9, 1.0, t);
+#else
+            m_add_scaled(G + l * 9, -1.0, t);
+#endif
+            cplx Ud[9];
+            m_dag(U, Ud);
+            m_mul(Ud, L, Mall + l * 9);
+        }
+    }
+    /* staple terms, scattered to the links of each staple */
+    for (long n = 0; n < V; ++n) {
+        int x[4];
+        long r = n;
+        for (int m = 0; m < 4; ++m) { x[m] = (int)(r % N[m]); r /= N[m]; }
+        for (int mu = 0; mu < 4; ++mu) {
+            const cplx *M = Mall + ((long)mu * V + n) * 9;
+            cplx Md[9];
+            m_dag(M, Md);
+            for (int nu = 0; nu < 4; ++nu) {
+                if (nu == mu) continue;
+                int dm[4] = {0, 0, 0, 0}, dn[4] = {0, 0, 0, 0}, dmn[4] = {0, 0, 0, 0}, dnm[4] = {0, 0, 0, 0};
+                const int z[4] = {0, 0, 0, 0};
+                dm[mu] = 1;
+                dn[nu] = 1;
+                dmn[mu] = 1; dmn[nu] = -1;
+                dnm[nu] = -1;
+                int y[4];
+                /* upper: U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag */
+                const cplx *a1 = link(N, links, x, z, nu), *a2 = link(N, links, x, dn, mu),
+                           *a3 = link(N, links, x, dm, nu);
+                cplx a3d[9], B[9], T1[9], T2[9], a1d[9], a2d[9];
+                m_dag(a3, a3d);
+                m_mul(a2, a3d, B);                 /* X = a1, A = 1, B = a2 a3^dag: G += B M */
+                m_mul(B, M, T1);
+                shifted(N, x, z, y);
+                m_add_scaled(G + ((long)nu * V + lex_index(N, y)) * 9, rho, T1);
+                m_mul(a3d, M, T1);                 /* X = a2, A = a1, B = a3^dag: G += B M A */
+                m_mul(T1, a1, T2);
+                shifted(N, x, dn, y);
+                m_add_scaled(G + ((long)mu * V + lex_index(N, y)) * 9, rho, T2);
+                m_dag(a1, a1d);                    /* X = a3 (dag), A = a1 a2, B = 1: G += A^dag M^dag */
+                m_dag(a2, a2d);
+                m_mul(a2d, a1d, T1);
+                m_mul(T1, Md, T2);
+                shifted(N, x, dm, y);
+                m_add_scaled(G + ((long)nu * V + lex_index(N, y)) * 9, rho, T2);
+                /* lower: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) */
+                const cplx *b1 = link(N, links, x, dnm, nu), *b2 = link(N, links, x, dnm, mu),
+                           *b3 = link(N, links, x, dmn, nu);
+                cplx b1d[9], Bd[9];
+                m_mul(b2, b3, B);                  /* X = b1 (dag), A = 1, B = b2 b3: G += M^dag B^dag */
+                m_dag(B, Bd);
+                m_mul(Md, Bd, T1);
+                shifted(N, x, dnm, y);
+                m_add_scaled(G + ((long)nu * V + lex_index(N, y)) * 9, rho, T1);
+                m_dag(b1, b1d);                    /* X = b2, A = b1^dag, B = b3: G += B M A */
+                m_mul(b3, M, T1);
+                m_mul(T1, b1d, T2);
+                m_add_scaled(G + ((long)mu * V + lex_index(N, y)) * 9, rho, T2);
+                m_mul(M, b1d, T1);                 /* X = b3, A = b1^dag b2, B = 1: G += M A */
+                m_mul(T1, b2, T2);
+                shifted(N, x, dmn, y);
+                m_add_scaled(G + ((long)nu * V + lex_index(N, y)) * 9, rho, T2);
+            }
+        }
+    }
+    for (long l = 0; l < nl; ++l) {
+        cplx UG[9];
+        m_mul(links + l * 9, G + l * 9, UG);
+        cplx *f = F + l * 9;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) f[i * 3 + j] = 0.5 * I * (UG[i * 3 + j] - conj(UG[j * 3 + i]));
+        const cplx tr = (f[0] + f[4] + f[8]) / 3.0;
+        f[0] -= tr; f[4] -= tr; f[8] -= tr;
+    }
+    free(G);
+    free(Mall);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Timing support                                                            */
 /* ------------------------------------------------------------------------ */
 

@@ -90,6 +90,10 @@ def _bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     lib.oracle_link_update.restype = None
     lib.oracle_mom_energy.argtypes = [ip, vp]
     lib.oracle_mom_energy.restype = ctypes.c_double
+    lib.oracle_stout_smear.argtypes = [ip, vp, ctypes.c_double, vp]
+    lib.oracle_stout_smear.restype = None
+    lib.oracle_stout_force.argtypes = [ip, vp, ctypes.c_double, vp, vp]
+    lib.oracle_stout_force.restype = None
     lib.oracle_set_threads.argtypes = [ctypes.c_int]
     lib.oracle_set_threads.restype = ctypes.c_int
     lib.oracle_mutant.restype = ctypes.c_int
@@ -273,6 +277,33 @@ class Oracle:
         V = int(np.prod(dims))
         H = self._c128(mom, (4, V, 3, 3))
         return self.lib.oracle_mom_energy(self._dims(dims), self._ptr(H))
+
+    # ------------------------------------------------- stout smearing
+    def stout_smear(self, dims, links, rho: float, levels: int = 1) -> np.ndarray:
+        """U^(levels): the stout map applied `levels` times (a new array)."""
+        return self.stout_levels(dims, links, rho, levels)[-1]
+
+    def stout_levels(self, dims, links, rho: float, levels: int) -> list:
+        """[U^(0) = U, U^(1), ..., U^(levels)]."""
+        V = int(np.prod(dims))
+        out = [np.array(self._c128(links, (4, V, 3, 3)), copy=True)]
+        for _ in range(int(levels)):
+            nxt = np.empty_like(out[-1])
+            self.lib.oracle_stout_smear(self._dims(dims), self._ptr(out[-1]), float(rho), self._ptr(nxt))
+            out.append(nxt)
+        return out
+
+    def stout_force(self, dims, links, rho: float, F_smeared, levels: int = 1) -> np.ndarray:
+        """Force on the thin links U from the force on U^(levels), chained
+        back one level at a time (oracle_stout_force)."""
+        V = int(np.prod(dims))
+        lv = self.stout_levels(dims, links, rho, levels)
+        F = np.array(self._c128(F_smeared, (4, V, 3, 3)), copy=True)
+        for k in range(int(levels) - 1, -1, -1):
+            Fk = np.empty_like(F)
+            self.lib.oracle_stout_force(self._dims(dims), self._ptr(lv[k]), float(rho), self._ptr(F), self._ptr(Fk))
+            F = Fk
+        return F
 
     def set_threads(self, n: int = 0) -> int:
         return self.lib.oracle_set_threads(int(n))

@@ -460,6 +460,98 @@ def pin_fermion_force_covariant(orc, dims=(4, 4, 4, 6), tol=1e-13, seed=96) -> t
     return eF <= 1e-10 and eS <= 1e-12, f"force covariance {eF:.2e}, action {eS:.2e}"
 
 
+# Stout smearing (isotropic weight per level; Sec. 2.1 stout-improved action)
+STOUT_RHO = 0.15
+STOUT_LEVELS = 2
+
+
+def pin_stout_basic(orc, dims=(4, 4, 4, 6), seed=97) -> tuple[bool, str]:
+    """rho = 0 leaves the links unchanged (bit for bit); smeared links stay in
+    SU(3); smearing commutes with gauge transformations, U^Omega ->
+    smear(U)^Omega."""
+    U = inputs.random_links(dims, seed=seed)
+    same = np.array_equal(orc.stout_smear(dims, U, 0.0, 1), U)
+    Us = orc.stout_smear(dims, U, STOUT_RHO, STOUT_LEVELS)
+    unit = float(np.abs(np.einsum("mvij,mvkj->mvik", Us, Us.conj()) - np.eye(3)).max())
+    det = float(np.abs(np.linalg.det(Us) - 1.0).max())
+    Om = inputs.random_gauge_transform(dims, seed=seed + 1)
+    lhs = orc.stout_smear(dims, gauge_transform_links(dims, U, Om), STOUT_RHO, STOUT_LEVELS)
+    cov = rel(lhs, gauge_transform_links(dims, Us, Om))
+    ok = same and unit <= 1e-13 and det <= 1e-13 and cov <= 1e-13
+    return ok, f"rho=0 identity {same}, unitarity {unit:.1e}, det {det:.1e}, covariance {cov:.1e}"
+
+
+def pin_stout_smooths(orc, dims=(4, 4, 4, 4), seed=98) -> tuple[bool, str]:
+    """A stout step with small rho moves the links along the descent direction
+    of the plaquette action (the staple sum C U^dag is the negative gradient
+    of the Wilson action), so the Wilson action of the smeared links is lower
+    than that of the thin links and falls further as rho grows."""
+    U = inputs.random_links(dims, seed=seed)
+
+    def wilson(Ut):
+        return sum(-float(np.trace(plaq(dims, Ut, mu, nu), axis1=1, axis2=2).real.sum())
+                   for mu in range(4) for nu in range(mu + 1, 4))
+
+    s = [wilson(orc.stout_smear(dims, U, r, 1)) for r in (0.0, 0.01, 0.02)]
+    return s[0] > s[1] > s[2], f"Wilson action at rho = 0, 0.01, 0.02: {s}"
+
+
+def plaq(dims, U, mu, nu):
+    """P_{mu nu}(x) for every site by plain enumeration."""
+    coords = list(sites(dims))
+    lex_of = {x: n for n, x in enumerate(coords)}
+    out = np.empty((len(coords), 3, 3), complex)
+    for n, x in enumerate(coords):
+        xm = list(x); xm[mu] = (xm[mu] + 1) % dims[mu]
+        xn = list(x); xn[nu] = (xn[nu] + 1) % dims[nu]
+        out[n] = U[mu, n] @ U[nu, lex_of[tuple(xm)]] @ U[mu, lex_of[tuple(xn)]].conj().T @ U[nu, n].conj().T
+    return out
+
+
+def pin_stout_force_is_derivative(orc, dims=(4, 4, 4, 4), beta=BETA, h=1e-4, seed=99) -> tuple[bool, str]:
+    """For S(U) = S_g(smear^2(U)) (Symanzik action of twice-smeared links):
+    d/de S(exp(i e X) U) at e = 0 equals sum Tr(X F) with F the force on the
+    smeared links chained back to the thin ones (central difference)."""
+    U = inputs.random_links(dims, seed=seed)
+    X = inputs.random_momenta(dims, seed=seed + 1)
+    Us = orc.stout_smear(dims, U, STOUT_RHO, STOUT_LEVELS)
+    F = orc.stout_force(dims, U, STOUT_RHO, orc.gauge_force(dims, Us, beta), STOUT_LEVELS)
+
+    def S(Ut):
+        return orc.gauge_action(dims, orc.stout_smear(dims, Ut, STOUT_RHO, STOUT_LEVELS), beta)
+
+    num = (S(orc.link_update(dims, U, X, h)) - S(orc.link_update(dims, U, X, -h))) / (2.0 * h)
+    ana = float(np.einsum("mvij,mvji->", X, F).real)
+    e = abs(num - ana) / abs(ana)
+    herm = float(np.abs(F - np.conj(np.swapaxes(F, -1, -2))).max())
+    trace = float(np.abs(np.trace(F, axis1=-2, axis2=-1)).max())
+    ok = e <= 1e-6 and herm <= 1e-13 * np.abs(F).max() and trace <= 1e-13 * np.abs(F).max()
+    return ok, f"derivative defect {e:.2e}, hermiticity {herm:.1e}, trace {trace:.1e}"
+
+
+def pin_stout_fermion_force(orc, dims=(4, 4, 4, 4), h=1e-4, tol=1e-13, seed=100) -> tuple[bool, str]:
+    """The rational pseudofermion action on smeared links, S_f(smear^2(U)):
+    its central difference along thin-link directions equals sum Tr(X F)
+    with F = the fermion force on the smeared links chained back."""
+    U = inputs.random_links(dims, seed=seed)
+    phi = inputs.gaussian_field(dims, k=seed)
+    X = inputs.random_momenta(dims, seed=seed + 1)
+    Us = orc.stout_smear(dims, U, STOUT_RHO, STOUT_LEVELS)
+    Fs, _, st = orc.fermion_force(dims, Us, FF_MASS, FF_A0, FF_A, FF_SIGMA, phi, tol)
+    if st != 0:
+        return False, f"status {st}"
+    F = orc.stout_force(dims, U, STOUT_RHO, Fs, STOUT_LEVELS)
+
+    def S(Ut):
+        Ust = orc.stout_smear(dims, Ut, STOUT_RHO, STOUT_LEVELS)
+        return orc.rational_apply(dims, Ust, FF_MASS, FF_A0, FF_A, FF_SIGMA, phi, tol)[1]
+
+    num = (S(orc.link_update(dims, U, X, h)) - S(orc.link_update(dims, U, X, -h))) / (2.0 * h)
+    ana = float(np.einsum("mvij,mvji->", X, F).real)
+    e = abs(num - ana) / abs(ana)
+    return e <= 1e-6, f"derivative defect {e:.2e}"
+
+
 BATTERY = [
     ("geometry 4x6x8x10", lambda o: pin_geometry(o, (4, 6, 8, 10))),
     ("phase anticommutation 4x6x8x10", lambda o: pin_phase_anticommutation(o, (4, 6, 8, 10))),
@@ -476,4 +568,7 @@ BATTERY = [
     ("gauge force = derivative of the action 4^4", pin_force_is_derivative),
     ("MD energy conservation O(dt^2) 4^4", pin_md_energy),
     ("fermion force = derivative of the rational action 4^4", pin_fermion_force_is_derivative),
+    ("stout: rho=0, SU(3), gauge covariance 4x4x4x6", pin_stout_basic),
+    ("stout smearing lowers the Wilson action 4^4", pin_stout_smooths),
+    ("stout force chain = derivative 4^4", pin_stout_force_is_derivative),
 ]

@@ -23,6 +23,8 @@ MUTANTS = {
     15: "trace of the gauge force kept",
     16: "fermion force: odd-site terms with the even-site sign",
     17: "fermion force without the staggered sign",
+    18: "stout links move with exp(-iQ)",
+    19: "stout force: C^dag L term with the wrong sign",
 }
 
 

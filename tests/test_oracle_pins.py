@@ -212,3 +212,24 @@ def test_fermion_force_is_derivative_of_rational_action(orc, dims):
 def test_fermion_force_gauge_covariant(orc):
     ok, msg = pins.pin_fermion_force_covariant(orc)
     assert ok, msg
+
+
+def test_stout_identity_unitarity_covariance(orc):
+    ok, msg = pins.pin_stout_basic(orc)
+    assert ok, msg
+
+
+def test_stout_smearing_lowers_wilson_action(orc):
+    ok, msg = pins.pin_stout_smooths(orc)
+    assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (2, 4, 2, 4)])
+def test_stout_force_chain_is_derivative(orc, dims):
+    ok, msg = pins.pin_stout_force_is_derivative(orc, dims=dims)
+    assert ok, msg
+
+
+def test_stout_fermion_force_is_derivative(orc):
+    ok, msg = pins.pin_stout_fermion_force(orc)
+    assert ok, msg
