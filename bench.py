@@ -46,7 +46,7 @@ COUNTS_KEY = "mscg_32x32x32x32_m0.01_15shifts_tol1e-10"
 # with the even sites (links stream from HBM at both sizes, spinors hit L2), so
 # a launch at V/2 sites moves bytes_per_site * V/2.  Reported only while the
 # kernel sources still hash to the captured version.
-K2_TRAFFIC = {"bytes_per_site": 1257.7, "src_sha256_16": "4e26af6ee527a02a",
+K2_TRAFFIC = {"bytes_per_site": 1257.9, "src_sha256_16": "ec50f1e5a9e4a84e",
               "sources": ["solver_kernels.cuh", "stencil_staged.cuh", "bulk.cuh", "deo_core.cuh", "common.cuh", "iteration.h"]}
 
 
@@ -547,6 +547,47 @@ def fermion_force_bench(lqcd, inputs):
             "iters": info["iters"], "max_true_resid": max(info["true_resid"][:N_SHIFT])}
 
 
+def stout_bench(lqcd, inputs, rho=0.15, levels=2):
+    """Stout smearing on the 32^4 workload (native FP64): smearing the links
+    `levels` times, the force chain through the levels (lqcd_stout_force: a
+    host call that uploads the force on the smeared links and downloads the
+    one on the thin links, 2 x 604 MB of transfers included), and the fermion
+    force update on the smeared links (solve, force and chain)."""
+    from paper_1701_00426_gb300 import rational
+    V = int(np.prod(DIMS))
+    U = inputs.random_links(DIMS)
+    ctx = lqcd.Context(DIMS)
+    ctx.links_upload(U)
+    ctx.mom_upload(inputs.random_momenta(DIMS))
+    ts = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        ctx.stout_smear(rho, levels)
+        ts.append(time.perf_counter() - t0)
+        ctx.stout_restore()
+    ctx.stout_smear(rho, levels)
+    F = np.asarray(inputs.random_momenta(DIMS, seed=5))
+    ctx.stout_force(F)  # warm-up (scratch buffers)
+    t0 = time.perf_counter()
+    ctx.stout_force(F)
+    dt_chain = time.perf_counter() - t0
+    del F, U
+    a0, a, sg = rational.inverse_sqrt_poles(N_SHIFT, MASS * MASS, MASS * MASS + 16.0)
+    phi = inputs.gaussian_field(DIMS, k=0)
+    ctx.fermion_force_update(MASS, a0, a, sg, TOL, phi, 0.0)  # warm-up
+    t0 = time.perf_counter()
+    act, info = ctx.fermion_force_update(MASS, a0, a, sg, TOL, phi, 0.01)
+    dt_f = time.perf_counter() - t0
+    ctx.close()
+    smear = min(ts)
+    return {"rho": rho, "levels": levels, "smear_ms": round(1e3 * smear, 2),
+            "smear_ns_per_site_per_level": round(1e9 * smear / V / levels, 2),
+            "force_chain_host_call_s": round(dt_chain, 4),
+            "force_chain_ns_per_site_per_level_incl_transfers": round(1e9 * dt_chain / V / levels, 2),
+            "fermion_force_update_smeared_s": round(dt_f, 4), "iters_on_smeared_links": info["iters"],
+            "max_true_resid": max(info["true_resid"][:N_SHIFT])}
+
+
 def rational_bench(lqcd, inputs, torch):
     """RHMC rational function on the 32^4 workload: y = r(A) b with the 15
     quadrature poles of x^(-1/2) on [m^2, m^2 + 16] and the action Re <b, y>,
@@ -767,6 +808,7 @@ def run_ours(args, rank, world, local):
     for name, fn in [("rational", lambda: rational_bench(lqcd, inputs, torch)),
                      ("gauge_md", lambda: gauge_md_bench(lqcd, inputs)),
                      ("fermion_force", lambda: fermion_force_bench(lqcd, inputs)),
+                     ("stout", lambda: stout_bench(lqcd, inputs)),
                      ("mixed_48", lambda: mixed_48_bench(lqcd, inputs, torch)),
                      ("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
                      ("packed", lambda: packed_bench(lqcd, inputs)),
@@ -821,7 +863,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sweep", type=int, nargs="*", default=[16, 24, 32, 48])
     ap.add_argument("--lattice", type=int, default=32, help="side of the solve lattice (default 32)")
-    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: rational gauge_md fermion_force mixed_48 batched packed serving serving_mixed")
+    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: rational gauge_md fermion_force stout mixed_48 batched packed serving "
+                         "serving_mixed")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
     ap.add_argument("--only-md", action="store_true",

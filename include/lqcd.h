@@ -347,7 +347,10 @@ int lqcd_gauge_md_steps(lqcd_ctx *ctx, int prec, double beta, double eps, int n_
  * S_f along U -> exp(i e X) U is sum Tr(X F_f).  phi: host canonical even
  * spinor ([Vh][3] complex128); *action (may be NULL) receives S_f.  The
  * force is computed in native FP64 from the FP64 links; momenta must have
- * been uploaded.  Synchronous.  LQCD_ENOCONV at max_iter (the update is
+ * been uploaded.  While the links are stout-smeared (lqcd_stout_smear) the
+ * action is that of the smeared links and the force is chained back to the
+ * thin links (as lqcd_stout_force) before the update: the momenta belong to
+ * the thin links.  Synchronous.  LQCD_ENOCONV at max_iter (the update is
  * still applied). */
 int lqcd_fermion_force_update(lqcd_ctx *ctx, double mass, double a0, const double *a,
                               const double *shifts, int n_shift, double tol, const double *phi,
@@ -415,6 +418,41 @@ int lqcd_serve_stats_get(lqcd_server *srv, lqcd_serve_stats *stats);
 
 /* Stop the scheduler, free every resource.  Unpolled results are dropped. */
 void lqcd_serve_destroy(lqcd_server *srv);
+
+/* ---------------------------------------------------------------- stout smearing
+ * Stout smearing of the fermion links (Sec. 2.1: stout-improved staggered
+ * action, Ref. Morningstar:2003gk; Sec. 2.2: a few stout levels).  One level
+ * maps every link to U' = exp(iQ) U with
+ *   C_mu(x) = rho sum_{nu != mu} [ U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+ *                                 + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) ],
+ *   Omega = C U^dag,  Q = (i/2)(Omega^dag - Omega) - (i/6) Tr(Omega^dag - Omega).
+ * Native FP64. */
+
+/* Smear the context's links n_levels times (1..8) with weight rho >= 0.  The
+ * smeared links become the links of every later D_eo, solve, rational
+ * application, fermion force and lqcd_links_download; levels 0 .. n-1 (level
+ * 0 = the links before smearing) stay on the device for the force chain
+ * (n_levels x 1152 B per even site).  LQCD_ESTATE without links or when
+ * already smeared.  Synchronous. */
+int lqcd_stout_smear(lqcd_ctx *ctx, double rho, int n_levels);
+
+/* Put the links from before lqcd_stout_smear back (no-op when not smeared).
+ * The gauge MD updates (lqcd_gauge_mom_update, lqcd_gauge_link_update,
+ * lqcd_gauge_md_steps) move the thin links and return LQCD_ESTATE while the
+ * links are smeared.  lqcd_links_upload also ends the smearing. */
+int lqcd_stout_restore(lqcd_ctx *ctx);
+
+/* Force on the thin links from a force on the smeared links: F_smeared and
+ * F_thin are host [4][V][3][3] complex128 (n_doubles = 4*V*18), Hermitian
+ * and traceless (else LQCD_EINVAL), with d/de S(exp(i e X) U') = sum Tr(X F)
+ * for the smeared links U'; F_thin is the same for the thin links U of the
+ * smearing, chained through every level: with Sigma' = -i U'^dag F_smeared,
+ * Gamma = the derivative of exp at iQ in the direction U Sigma', L its
+ * traceless anti-Hermitian part, the gradient G of each link collects
+ * Sigma' exp(iQ) - C^dag L and rho times the staple products that carry
+ * U^dag L of the links whose C contains it, and F = traceless part of
+ * (i/2)(U G - G^dag U^dag).  LQCD_ESTATE when not smeared.  Synchronous. */
+int lqcd_stout_force(lqcd_ctx *ctx, const double *F_smeared, double *F_thin, size_t n_doubles);
 
 #ifdef __cplusplus
 }

@@ -792,7 +792,7 @@ __global__ void k_mom_from_canonical(LinkGeo g, const double2 *__restrict__ src,
     for (int k = 0; k < 8; ++k) {
         const size_t o = (size_t)((mu * 2 + P) * 8 + k) * g.Vh + idx;
         m64[o] = v[k];
-        m32[o] = (float)v[k];
+        if (m32) m32[o] = (float)v[k];
     }
 }
 
@@ -938,6 +938,329 @@ __global__ void __launch_bounds__(kGaugeThreads)
     for (int k = 0; k < 8; ++k) h[(size_t)k * Vh] = fma(-eps, fv[k], h[(size_t)k * Vh]);
 }
 
+// ------------------------------------------------------------------ stout smearing
+// Stout smearing of the links (Sec. 2.1, stout-improved staggered action,
+// after Morningstar and Peardon), isotropic weight rho per level:
+//   C_mu(x) = rho sum_{nu != mu} [ U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+//                                 + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) ],
+//   Omega = C U^dag, Q = (i/2)(Omega^dag - Omega) - (i/6) Tr(Omega^dag - Omega),
+//   U' = exp(iQ) U.
+// Native FP64, one thread per link, the SoA layout of the IEEE links.
+
+__device__ __forceinline__ void stout_C(const LinkGeo &g, const double2 *L, const int (&x)[4], int mu, double rho,
+                                        Mat3<double> &C)
+{
+#pragma unroll
+    for (int q = 0; q < 9; ++q) C.e[q] = {0.0, 0.0};
+#pragma unroll 1
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        int dn[4] = {0, 0, 0, 0}, dm[4] = {0, 0, 0, 0}, dmn[4] = {0, 0, 0, 0};
+        dn[nu] = 1;
+        dm[mu] = 1;
+        dmn[mu] = 1;
+        dmn[nu] = -1;
+        Mat3<double> a, b, t, u;
+        // upper: U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+        link_at<double>(g, L, x, 0, 0, 0, 0, nu, a);
+        link_at<double>(g, L, x, dn[0], dn[1], dn[2], dn[3], mu, b);
+        mat_mul(a, b, t);
+        link_at<double>(g, L, x, dm[0], dm[1], dm[2], dm[3], nu, a);
+        mat_mul_dag(t, a, u);
+        mat_axpy(rho, u, C);
+        // lower: U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+        link_at<double>(g, L, x, -dn[0], -dn[1], -dn[2], -dn[3], nu, a);
+        mat_dag(a);
+        link_at<double>(g, L, x, -dn[0], -dn[1], -dn[2], -dn[3], mu, b);
+        mat_mul(a, b, t);
+        link_at<double>(g, L, x, dmn[0], dmn[1], dmn[2], dmn[3], nu, a);
+        mat_mul(t, a, u);
+        mat_axpy(rho, u, C);
+    }
+}
+
+// Q from C and U (Hermitian, traceless)
+__device__ __forceinline__ void stout_Q(const Mat3<double> &C, const Mat3<double> &U, Mat3<double> &Q)
+{
+    Mat3<double> Om;
+    mat_mul_dag(C, U, Om);
+    // Q_ij = (i/2)(conj(Om_ji) - Om_ij):  re = (Om_ij.im + Om_ji.im)/2, im = (Om_ji.re - Om_ij.re)/2
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Q.e[i * 3 + j] = {0.5 * (Om.e[i * 3 + j].im + Om.e[j * 3 + i].im),
+                              0.5 * (Om.e[j * 3 + i].re - Om.e[i * 3 + j].re)};
+    const double tr = (Q.e[0].re + Q.e[4].re + Q.e[8].re) / 3.0;
+    Q.e[0].re -= tr;
+    Q.e[4].re -= tr;
+    Q.e[8].re -= tr;
+}
+
+// E = exp(X) and D = d/dt exp(X + t A) at t = 0, from the block matrix
+// B = [[X, A], [0, X]], exp(B) = [[E, D], [0, E]]: B scaled by 2^-k to
+// 1-norm <= 1/4 (the norm of X bounds the scaling; A scales with it),
+// Horner on the block form (P <- 1 + X P / n, R <- (X R + A P) / n, degree
+// 18), then k block squarings (P, R) <- (P P, P R + R P).
+__device__ void exp_frechet_dev(const Mat3<double> &X, const Mat3<double> &A, Mat3<double> &E, Mat3<double> &D)
+{
+    // D is linear in A: run with A / ||A||_1 and scale D back
+    double nx = 0.0, na = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        double c = 0.0, ca = 0.0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            c += hypot(X.e[i * 3 + j].re, X.e[i * 3 + j].im);
+            ca += hypot(A.e[i * 3 + j].re, A.e[i * 3 + j].im);
+        }
+        nx = fmax(nx, c);
+        na = fmax(na, ca);
+    }
+    const double an = na > 0.0 ? 1.0 / na : 0.0;
+    double nrm = nx + (na > 0.0 ? 1.0 : 0.0);
+    int k = 0;
+    while (nrm > 0.25 && k < 60) {
+        nrm *= 0.5;
+        ++k;
+    }
+    const double sc = ldexp(1.0, -k);
+    Mat3<double> Xs, As, P, R;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+        Xs.e[q] = {sc * X.e[q].re, sc * X.e[q].im};
+        As.e[q] = {sc * an * A.e[q].re, sc * an * A.e[q].im};
+        P.e[q] = {(q % 4 == 0) ? 1.0 : 0.0, 0.0};
+        R.e[q] = {0.0, 0.0};
+    }
+#pragma unroll 1
+    for (int n = 18; n >= 1; --n) {
+        Mat3<double> XP, XR, AP;
+        mat_mul(Xs, P, XP);
+        mat_mul(Xs, R, XR);
+        mat_mul(As, P, AP);
+        const double inv = 1.0 / n;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            P.e[q] = {((q % 4 == 0) ? 1.0 : 0.0) + inv * XP.e[q].re, inv * XP.e[q].im};
+            R.e[q] = {inv * (XR.e[q].re + AP.e[q].re), inv * (XR.e[q].im + AP.e[q].im)};
+        }
+    }
+#pragma unroll 1
+    for (int q = 0; q < k; ++q) {
+        Mat3<double> PP, PR, RP;
+        mat_mul(P, P, PP);
+        mat_mul(P, R, PR);
+        mat_mul(R, P, RP);
+        P = PP;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) R.e[c] = {PR.e[c].re + RP.e[c].re, PR.e[c].im + RP.e[c].im};
+    }
+    E = P;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) D.e[c] = {na * R.e[c].re, na * R.e[c].im};
+}
+
+__device__ __forceinline__ void store_link_soa(double2 *L, int mu, int P, int i, int Vh, const Mat3<double> &U)
+{
+    double2 *p = L + (size_t)((mu * 2 + P) * 9) * Vh + i;
+#pragma unroll
+    for (int c = 0; c < 9; ++c) p[(size_t)c * Vh] = make_double2(U.e[c].re, U.e[c].im);
+}
+
+// Lout = one stout level of Lin.  Thread = (mu, parity, site).
+__global__ void __launch_bounds__(kGaugeThreads)
+    k_stout_level(LinkGeo g, const double2 *__restrict__ Lin, double2 *__restrict__ Lout, double rho)
+{
+    const int Vh = g.Vh;
+    const long t = blockIdx.x * (long)kGaugeThreads + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    const int i = (int)(t % Vh);
+    const int mp = (int)(t / Vh);
+    const int mu = mp >> 1, P = mp & 1;
+    int x[4];
+    coords_of(g, P, i, x);
+    Mat3<double> C, U, Q, E, R;
+    stout_C(g, Lin, x, mu, rho, C);
+    load_link_soa<double>(Lin, mu, P, i, Vh, U);
+    stout_Q(C, U, Q);
+    exp_iH_dev(Q, 1.0, E);
+    mat_mul(E, U, R);
+    store_link_soa(Lout, mu, P, i, Vh, R);
+}
+
+// First pass of the force chain of one level (the force on U' = smear(U),
+// Fp as 8 reals per link, to the force on U): per link
+//   Sigma' = -i U'^dag Fp,  Gamma = Dexp_{iQ}[U Sigma'],  L = traceless
+//   anti-Hermitian part of Gamma,
+//   Gl = Sigma' exp(iQ) - C^dag L  (the link's own terms of the gradient),
+//   M = U^dag L                    (what the staples of C carry to their links).
+__global__ void __launch_bounds__(kGaugeThreads)
+    k_stout_local(LinkGeo g, const double2 *__restrict__ L, const double *__restrict__ Fp, double rho,
+                  double2 *__restrict__ Mout, double2 *__restrict__ Gl)
+{
+    const int Vh = g.Vh;
+    const long t = blockIdx.x * (long)kGaugeThreads + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    const int i = (int)(t % Vh);
+    const int mp = (int)(t / Vh);
+    const int mu = mp >> 1, P = mp & 1;
+    int x[4];
+    coords_of(g, P, i, x);
+    Mat3<double> C, U, Q, E, D, W, S, iQ, F;
+    stout_C(g, L, x, mu, rho, C);
+    load_link_soa<double>(L, mu, P, i, Vh, U);
+    stout_Q(C, U, Q);
+    double h[8];
+    const double *hp = Fp + (size_t)(mp * 8) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = hp[(size_t)k * Vh];
+    herm_unpack(h, F);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) iQ.e[q] = {-Q.e[q].im, Q.e[q].re};
+    exp_iH_dev(Q, 1.0, E);
+    mat_mul(E, U, W);  // U'
+    // S = -i U'^dag F
+    Mat3<double> Wd = W;
+    mat_dag(Wd);
+    mat_mul(Wd, F, S);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) S.e[q] = {S.e[q].im, -S.e[q].re};
+    Mat3<double> US, E2;
+    mat_mul(U, S, US);
+    exp_frechet_dev(iQ, US, E2, D);
+    // L = (D - D^dag)/2 - Tr(D - D^dag)/6
+    Mat3<double> Lm;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+            Lm.e[a * 3 + b] = {0.5 * (D.e[a * 3 + b].re - D.e[b * 3 + a].re),
+                               0.5 * (D.e[a * 3 + b].im + D.e[b * 3 + a].im)};
+    const double tri = (Lm.e[0].im + Lm.e[4].im + Lm.e[8].im) / 3.0;
+    Lm.e[0].im -= tri;
+    Lm.e[4].im -= tri;
+    Lm.e[8].im -= tri;
+    // Gl = S E - C^dag L
+    Mat3<double> SE, CdL, Cd = C;
+    mat_mul(S, E, SE);
+    mat_dag(Cd);
+    mat_mul(Cd, Lm, CdL);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) SE.e[q] = {SE.e[q].re - CdL.e[q].re, SE.e[q].im - CdL.e[q].im};
+    store_link_soa(Gl, mu, P, i, Vh, SE);
+    // M = U^dag L
+    Mat3<double> Ud = U, M;
+    mat_dag(Ud);
+    mat_mul(Ud, Lm, M);
+    store_link_soa(Mout, mu, P, i, Vh, M);
+}
+
+// Second pass: each link (y, l) gathers the staple terms that carry M of the
+// links whose C contains it (rho times, for every mu != l and nu != l):
+//   U_mu(y+l) U_l(y+mu)^dag M_mu(y)            U_mu(y-mu+l)^dag U_l(y-mu)^dag M_mu(y-mu)^dag
+//   M_mu(y+l)^dag U_l(y+mu)^dag U_mu(y)^dag    M_mu(y+l-mu) U_l(y-mu)^dag U_mu(y-mu)
+//   U_nu(y-nu+l)^dag M_l(y-nu) U_nu(y-nu)      U_nu(y+l) M_l(y+nu) U_nu(y)^dag
+// adds the link's own terms Gl and writes the force on the link,
+//   F = traceless part of (i/2)(U G - G^dag U^dag), as 8 reals.
+__global__ void __launch_bounds__(kGaugeThreads)
+    k_stout_gather(LinkGeo g, const double2 *__restrict__ L, const double2 *__restrict__ M,
+                   const double2 *__restrict__ Gl, double rho, double *__restrict__ Fout)
+{
+    const int Vh = g.Vh;
+    const long t = blockIdx.x * (long)kGaugeThreads + threadIdx.x;
+    if (t >= 8L * Vh) return;
+    const int i = (int)(t % Vh);
+    const int mp = (int)(t / Vh);
+    const int l = mp >> 1, P = mp & 1;
+    int y[4];
+    coords_of(g, P, i, y);
+    Mat3<double> G, acc;
+    load_link_soa<double>(Gl, l, P, i, Vh, G);
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc.e[q] = {0.0, 0.0};
+    int el[4] = {0, 0, 0, 0};
+    el[l] = 1;
+#pragma unroll 1
+    for (int m = 0; m < 4; ++m) {
+        if (m == l) continue;
+        int em[4] = {0, 0, 0, 0};
+        em[m] = 1;
+        Mat3<double> a, b, c, t1, t2;
+        // U_m(y+l) U_l(y+m)^dag M_m(y)
+        link_at<double>(g, L, y, el[0], el[1], el[2], el[3], m, a);
+        link_at<double>(g, L, y, em[0], em[1], em[2], em[3], l, b);
+        mat_mul_dag(a, b, t1);
+        link_at<double>(g, M, y, 0, 0, 0, 0, m, c);
+        mat_mul(t1, c, t2);
+        mat_axpy(1.0, t2, acc);
+        // U_m(y-m+l)^dag U_l(y-m)^dag M_m(y-m)^dag = (M_m(y-m) U_l(y-m) U_m(y-m+l))^dag
+        link_at<double>(g, M, y, -em[0], -em[1], -em[2], -em[3], m, c);
+        link_at<double>(g, L, y, -em[0], -em[1], -em[2], -em[3], l, b);
+        mat_mul(c, b, t1);
+        link_at<double>(g, L, y, el[0] - em[0], el[1] - em[1], el[2] - em[2], el[3] - em[3], m, a);
+        mat_mul(t1, a, t2);
+        mat_dag(t2);
+        mat_axpy(1.0, t2, acc);
+        // M_m(y+l)^dag U_l(y+m)^dag U_m(y)^dag = (U_m(y) U_l(y+m) M_m(y+l))^dag
+        link_at<double>(g, L, y, 0, 0, 0, 0, m, a);
+        link_at<double>(g, L, y, em[0], em[1], em[2], em[3], l, b);
+        mat_mul(a, b, t1);
+        link_at<double>(g, M, y, el[0], el[1], el[2], el[3], m, c);
+        mat_mul(t1, c, t2);
+        mat_dag(t2);
+        mat_axpy(1.0, t2, acc);
+        // M_m(y+l-m) U_l(y-m)^dag U_m(y-m)
+        link_at<double>(g, M, y, el[0] - em[0], el[1] - em[1], el[2] - em[2], el[3] - em[3], m, c);
+        link_at<double>(g, L, y, -em[0], -em[1], -em[2], -em[3], l, b);
+        mat_mul_dag(c, b, t1);
+        link_at<double>(g, L, y, -em[0], -em[1], -em[2], -em[3], m, a);
+        mat_mul(t1, a, t2);
+        mat_axpy(1.0, t2, acc);
+        // (m plays nu) U_m(y-m+l)^dag M_l(y-m) U_m(y-m)
+        link_at<double>(g, L, y, el[0] - em[0], el[1] - em[1], el[2] - em[2], el[3] - em[3], m, a);
+        mat_dag(a);
+        link_at<double>(g, M, y, -em[0], -em[1], -em[2], -em[3], l, c);
+        mat_mul(a, c, t1);
+        link_at<double>(g, L, y, -em[0], -em[1], -em[2], -em[3], m, b);
+        mat_mul(t1, b, t2);
+        mat_axpy(1.0, t2, acc);
+        // U_m(y+l) M_l(y+m) U_m(y)^dag
+        link_at<double>(g, L, y, el[0], el[1], el[2], el[3], m, a);
+        link_at<double>(g, M, y, em[0], em[1], em[2], em[3], l, c);
+        mat_mul(a, c, t1);
+        link_at<double>(g, L, y, 0, 0, 0, 0, m, b);
+        mat_mul_dag(t1, b, t2);
+        mat_axpy(1.0, t2, acc);
+    }
+    mat_axpy(rho, acc, G);
+    Mat3<double> U, W;
+    load_link_soa<double>(L, l, P, i, Vh, U);
+    mat_mul(U, G, W);
+    // F = (i/2)(W - W^dag): re F_pq = -(Im W_pq + Im W_qp)/2, im F_pq = (Re W_pq - Re W_qp)/2
+    const double d0 = -W.e[0].im, d1 = -W.e[4].im, d2 = -W.e[8].im;
+    const double tr = (d0 + d1 + d2) / 3.0;
+    double f[8];
+    f[0] = d0 - tr;
+    f[1] = d1 - tr;
+    f[2] = -0.5 * (W.e[1].im + W.e[3].im);
+    f[3] = 0.5 * (W.e[1].re - W.e[3].re);
+    f[4] = -0.5 * (W.e[2].im + W.e[6].im);
+    f[5] = 0.5 * (W.e[2].re - W.e[6].re);
+    f[6] = -0.5 * (W.e[5].im + W.e[7].im);
+    f[7] = 0.5 * (W.e[5].re - W.e[7].re);
+    double *fo = Fout + (size_t)(mp * 8) * Vh + i;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) fo[(size_t)k * Vh] = f[k];
+}
+
+// y += a x over n doubles
+__global__ void k_daxpy(long n, double a, const double *__restrict__ x, double *__restrict__ y)
+{
+    const long t = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (t < n) y[t] = fma(a, x[t], y[t]);
+}
+
 static LinkGeo link_geo(const lqcd_ctx *c)
 {
     LinkGeo g;
@@ -1053,6 +1376,42 @@ static int prepare(lqcd_ctx *c, int prec)
     return mom_to_prec(c, prec);
 }
 
+// MD updates move the uploaded (thin) links; they are refused while the
+// links in use are stout-smeared.
+static int check_thin(const lqcd_ctx *c)
+{
+    if (c->stout_n) return fail(LQCD_ESTATE, "links are stout-smeared: call lqcd_stout_restore first");
+    return LQCD_OK;
+}
+
+// Force on the stout levels' thin links from the force F (8 reals per link,
+// mom layout) on the smeared links, in place: one local and one gather
+// pass per level, from level n-1 down to 0.
+static int stout_chain(lqcd_ctx *c, double *F, cudaStream_t s)
+{
+    const LinkGeo g = link_geo(c);
+    const size_t nl = 72 * c->Vh, nf = 64 * c->Vh;
+    int st;
+    if ((st = c->stout_M.ensure(nl * sizeof(double2))) || (st = c->stout_G.ensure(nl * sizeof(double2))) ||
+        (st = c->stout_F.ensure(2 * nf * sizeof(double))))
+        return st;
+    double *tmp = F == c->stout_F.as<double>() ? c->stout_F.as<double>() + nf : c->stout_F.as<double>();
+    double *fa = F, *fb = tmp;
+    const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
+    for (int k = c->stout_n - 1; k >= 0; --k) {
+        const double2 *Lk = c->stout_lv.as<double2>() + (size_t)k * nl;
+        k_stout_local<<<nb, kGaugeThreads, 0, s>>>(g, Lk, fa, c->stout_rho, c->stout_M.as<double2>(),
+                                                    c->stout_G.as<double2>());
+        k_stout_gather<<<nb, kGaugeThreads, 0, s>>>(g, Lk, c->stout_M.as<double2>(), c->stout_G.as<double2>(),
+                                                     c->stout_rho, fb);
+        c->launches += 2;
+        std::swap(fa, fb);
+    }
+    LQCD_CUDA(cudaGetLastError());
+    if (fa != F) LQCD_CUDA(cudaMemcpyAsync(F, fa, nf * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    return LQCD_OK;
+}
+
 }  // namespace lqcd
 
 using namespace lqcd;
@@ -1118,7 +1477,7 @@ int lqcd_mom_download(lqcd_ctx *c, double *H, size_t n)
 int lqcd_gauge_mom_update(lqcd_ctx *c, int prec, double beta, double eps)
 {
     int st;
-    if ((st = check_md(c, prec)) || (st = prepare(c, prec))) return st;
+    if ((st = check_md(c, prec)) || (st = check_thin(c)) || (st = prepare(c, prec))) return st;
     launch_mom_update(c, prec, beta, eps);
     LQCD_CUDA(cudaGetLastError());
     LQCD_CUDA(cudaStreamSynchronize(c->stream));
@@ -1128,7 +1487,7 @@ int lqcd_gauge_mom_update(lqcd_ctx *c, int prec, double beta, double eps)
 int lqcd_gauge_link_update(lqcd_ctx *c, int prec, double eps)
 {
     int st;
-    if ((st = check_md(c, prec)) || (st = prepare(c, prec))) return st;
+    if ((st = check_md(c, prec)) || (st = check_thin(c)) || (st = prepare(c, prec))) return st;
     launch_link_update(c, prec, eps);
     LQCD_CUDA(cudaGetLastError());
     LQCD_CUDA(cudaStreamSynchronize(c->stream));
@@ -1138,7 +1497,7 @@ int lqcd_gauge_link_update(lqcd_ctx *c, int prec, double eps)
 int lqcd_gauge_md_steps(lqcd_ctx *c, int prec, double beta, double eps, int n_steps)
 {
     int st;
-    if ((st = check_md(c, prec)) || (st = prepare(c, prec))) return st;
+    if ((st = check_md(c, prec)) || (st = check_thin(c)) || (st = prepare(c, prec))) return st;
     if (n_steps < 0) return fail(LQCD_EINVAL, "n_steps must be >= 0");
     for (int k = 0; k < n_steps; ++k) {
         launch_mom_update(c, prec, beta, eps);
@@ -1176,8 +1535,23 @@ int lqcd_fermion_force_update(lqcd_ctx *c, double mass, double a0, const double 
     FFCoef C;
     C.n = n_shift;
     for (int k = 0; k < kMaxShifts; ++k) C.a[k] = k < n_shift ? a[k] : 0.0;
-    k_fermion_force_update<<<nblocks(8L * (long)c->Vh, kGaugeThreads), kGaugeThreads, 0, s>>>(
-        c->g, c->lnk_nat.as<double2>(), x, y, C, c->mom64.as<double>(), eps);
+    const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
+    if (c->stout_n) {
+        // force on the smeared links (into a zeroed buffer: 0 - (-1) F), chained
+        // back to the thin links, then H -= eps F
+        const size_t nf = 64 * c->Vh;
+        if ((st = c->stout_F.ensure(2 * nf * sizeof(double)))) return st;
+        double *F = c->stout_F.as<double>();
+        LQCD_CUDA(cudaMemsetAsync(F, 0, nf * sizeof(double), s));
+        k_fermion_force_update<<<nb, kGaugeThreads, 0, s>>>(c->g, c->lnk_nat.as<double2>(), x, y, C, F, -1.0);
+        LQCD_CUDA(cudaGetLastError());
+        c->launches += 1;
+        if ((st = stout_chain(c, F, s))) return st;
+        k_daxpy<<<nblocks((long)nf, 256), 256, 0, s>>>((long)nf, -eps, F, c->mom64.as<double>());
+    } else {
+        k_fermion_force_update<<<nb, kGaugeThreads, 0, s>>>(c->g, c->lnk_nat.as<double2>(), x, y, C,
+                                                             c->mom64.as<double>(), eps);
+    }
     LQCD_CUDA(cudaGetLastError());
     c->launches += 1;
     c->mom_newest = LQCD_PREC_FP64;
@@ -1185,6 +1559,85 @@ int lqcd_fermion_force_update(lqcd_ctx *c, double mass, double a0, const double 
     if (action) *action = act;
     if (rs == LQCD_ENOCONV) set_error("solver did not reach tol within max_iter");
     return rs;
+}
+
+int lqcd_stout_smear(lqcd_ctx *c, double rho, int n_levels)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
+    if (c->stout_n) return fail(LQCD_ESTATE, "links are already stout-smeared: call lqcd_stout_restore first");
+    if (!(rho >= 0.0) || !std::isfinite(rho)) return fail(LQCD_EINVAL, "rho must be finite and >= 0");
+    if (n_levels < 1 || n_levels > 8) return fail(LQCD_EINVAL, "n_levels must be in 1..8");
+    int st;
+    if ((st = links_to_prec(c, LQCD_PREC_FP64_NATIVE))) return st;
+    const size_t nl = 72 * c->Vh;
+    if ((st = c->stout_lv.ensure((size_t)n_levels * nl * sizeof(double2)))) return st;
+    cudaStream_t s = c->stream;
+    const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
+    for (int k = 0; k < n_levels; ++k) {
+        double2 *lv = c->stout_lv.as<double2>() + (size_t)k * nl;
+        LQCD_CUDA(cudaMemcpyAsync(lv, c->lnk_nat.ptr, nl * sizeof(double2), cudaMemcpyDeviceToDevice, s));
+        k_stout_level<<<nb, kGaugeThreads, 0, s>>>(link_geo(c), lv, c->lnk_nat.as<double2>(), rho);
+        c->launches += 1;
+    }
+    LQCD_CUDA(cudaGetLastError());
+    c->stout_n = n_levels;
+    c->stout_rho = rho;
+    c->md_links_newest = LQCD_PREC_FP64;
+    c->links_derived_stale = true;
+    c->df_stale = true;
+    LQCD_CUDA(cudaStreamSynchronize(s));
+    return LQCD_OK;
+}
+
+int lqcd_stout_restore(lqcd_ctx *c)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    if (!c->stout_n) return LQCD_OK;
+    const size_t nl = 72 * c->Vh;
+    LQCD_CUDA(cudaMemcpyAsync(c->lnk_nat.ptr, c->stout_lv.ptr, nl * sizeof(double2), cudaMemcpyDeviceToDevice,
+                              c->stream));
+    c->stout_n = 0;
+    c->md_links_newest = LQCD_PREC_FP64;
+    c->links_derived_stale = true;
+    c->df_stale = true;
+    LQCD_CUDA(cudaStreamSynchronize(c->stream));
+    return LQCD_OK;
+}
+
+int lqcd_stout_force(lqcd_ctx *c, const double *F_smeared, double *F_thin, size_t n)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    if (!c->stout_n) return fail(LQCD_ESTATE, "links are not stout-smeared");
+    const size_t want = 4 * c->V * 18;
+    if (!F_smeared || !F_thin || n != want) return fail(LQCD_EINVAL, "forces: expected 4*V*18 doubles");
+    const size_t nf = 64 * c->Vh;
+    int st;
+    if ((st = c->stout_F.ensure(2 * nf * sizeof(double)))) return st;
+    DevBuf stage;
+    if ((st = stage.ensure(want * sizeof(double) + 16))) return st;
+    int *bad = (int *)((char *)stage.ptr + want * sizeof(double));
+    cudaStream_t s = c->stream;
+    double *F = c->stout_F.as<double>();
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(stage.ptr, F_smeared, want * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "force upload");
+    k_mom_from_canonical<<<nblocks(4L * (long)c->V, 256), 256, 0, s>>>(link_geo(c), stage.as<double2>(), F, nullptr,
+                                                                        bad, (long)c->V);
+    c->launches += 1;
+    int hbad = 0;
+    LQCD_CUDA(cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s));
+    LQCD_CUDA(cudaStreamSynchronize(s));
+    if (hbad) return fail(LQCD_EINVAL, "forces must be finite, Hermitian and traceless");
+    if ((st = stout_chain(c, F, s))) return st;
+    k_mom_to_canonical<double><<<nblocks(4L * (long)c->V, 256), 256, 0, s>>>(link_geo(c), F, stage.as<double2>(),
+                                                                            (long)c->V);
+    c->launches += 1;
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F_thin, stage.ptr, want * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "force download");
+    return LQCD_OK;
 }
 
 int lqcd_gauge_action(lqcd_ctx *c, int prec, double beta, double *S)

@@ -104,6 +104,11 @@ struct lqcd_ctx {
     // gauge molecular dynamics (gauge.cu): momenta as 8 reals per link, SoA [4][2][8][Vh]
     lqcd::DevBuf mom64, mom32;
     lqcd::DevBuf md_part;     // partials of the action / kinetic energy (+ the total)
+    lqcd::DevBuf stout_lv;    // stout levels 0 .. n-1 (level 0 = the thin links), IEEE SoA each; level n is lnk_nat
+    lqcd::DevBuf stout_M, stout_G;  // force chain scratch: U^dag L and the link's own gradient terms, per link
+    lqcd::DevBuf stout_F;     // two forces on the links, 8 reals each ([2][4][2][8][Vh] double)
+    int stout_n = 0;          // active stout levels (0: the links in use are the uploaded ones)
+    double stout_rho = 0.0;
     lqcd::DevBuf ff_y;        // D_oe x_i of the fermion force [n][3][Vh] double2
     int md_links_newest = 0;  // LQCD_PREC_FP64: lnk_nat holds the newest links; FP32: lnk_f18
     bool links_derived_stale = false;  // MD moved the links: derived formats need a rebuild

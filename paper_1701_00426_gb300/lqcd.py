@@ -50,6 +50,7 @@ EXPORTED = [
     "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy", "lqcd_serve_set_opts",
     "lqcd_mom_upload", "lqcd_mom_download", "lqcd_gauge_mom_update", "lqcd_gauge_link_update",
     "lqcd_gauge_md_steps", "lqcd_gauge_action", "lqcd_mom_energy", "lqcd_fermion_force_update",
+    "lqcd_stout_smear", "lqcd_stout_restore", "lqcd_stout_force",
 ]
 
 
@@ -154,6 +155,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_fermion_force_update": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int,
                                                      ctypes.c_double, vp, ctypes.c_double, dp,
                                                      ctypes.POINTER(lqcd_solve_info)]),
+        "lqcd_stout_smear": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
+        "lqcd_stout_restore": (ctypes.c_int, [vp]),
+        "lqcd_stout_force": (ctypes.c_int, [vp, vp, vp, ctypes.c_size_t]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -302,6 +306,21 @@ class Context:
                                                  sh.ctypes.data_as(dp), sh.size, float(tol), _ptr(pp), float(eps),
                                                  ctypes.byref(act), ctypes.byref(info)))
         return act.value, info.as_dict()
+
+    def stout_smear(self, rho: float, levels: int):
+        """Smear the links `levels` times (lqcd_stout_smear)."""
+        check(self.lib.lqcd_stout_smear(self.h, float(rho), int(levels)))
+
+    def stout_restore(self):
+        """Put the unsmeared links back (lqcd_stout_restore)."""
+        check(self.lib.lqcd_stout_restore(self.h))
+
+    def stout_force(self, F_smeared) -> np.ndarray:
+        """Force on the thin links from one on the smeared links, [4][V][3][3]."""
+        Fs = _c128(F_smeared, (4, self.V, 3, 3))
+        out = np.empty_like(Fs)
+        check(self.lib.lqcd_stout_force(self.h, _ptr(Fs), _ptr(out), Fs.size * 2))
+        return out
 
     def mom_energy(self, prec: int = 0) -> float:
         k = ctypes.c_double()
