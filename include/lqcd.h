@@ -207,7 +207,9 @@ int lqcd_deo_apply_ex(lqcd_ctx *ctx, int out_parity, int prec, int recon,
 /* Multi-right-hand-side D_eo/D_oe in FP32: each link is loaded once for all
  * n_rhs (1..16) fields.  Device layout of in/out: complex64 [3][Vh][n_rhs]
  * (colour-major, then site, right-hand side fastest).  recon 18 or 12.
- * Asynchronous on `stream`. */
+ * With in and out 16-byte aligned, the kernel may read and write two fields
+ * per access (the fields per thread are picked by timing on the first call);
+ * any alignment of complex64 is accepted.  Asynchronous on `stream`. */
 int lqcd_deo_apply_mrhs(lqcd_ctx *ctx, int out_parity, int n_rhs, int recon,
                         const void *in, void *out, void *stream);
 

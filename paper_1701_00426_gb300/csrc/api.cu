@@ -55,7 +55,7 @@ size_t ctx_device_bytes(const lqcd_ctx *c)
     const DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->lnk_dfs,
                          &c->err_word, &c->io_a, &c->io_b, &c->rat_x, &c->rat_part, &c->mom64,
                          &c->mom32, &c->md_part, &c->ff_y, &c->stout_lv, &c->stout_M, &c->stout_G,
-                         &c->stout_F, &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state,
+                         &c->stout_F, &c->host_b, &c->host_x, &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state,
                          &c->ws.stage};
     size_t s = 0;
     for (const DevBuf *p : b) s += p->bytes;
@@ -142,7 +142,7 @@ void lqcd_destroy(lqcd_ctx *c)
     c->graph.reset();
     DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->lnk_dfs, &c->err_word,
                    &c->io_a, &c->io_b, &c->rat_x, &c->rat_part, &c->mom64, &c->mom32, &c->md_part, &c->ff_y,
-                   &c->stout_lv, &c->stout_M, &c->stout_G, &c->stout_F,
+                   &c->stout_lv, &c->stout_M, &c->stout_G, &c->stout_F, &c->host_b, &c->host_x,
                    &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
     for (DevBuf *p : b) p->release();
     c->ws32.release();
@@ -220,7 +220,9 @@ int lqcd_mscg_solve(lqcd_ctx *c, double mass, const double *shifts, int n_shift,
     if (!b || !x || !shifts) return fail(LQCD_EINVAL, "NULL argument");
     if (n_shift < 1 || n_shift > LQCD_MAX_SHIFTS) return fail(LQCD_EINVAL, "n_shift must be in 1..32");
     const size_t n3 = 3 * c->Vh;
-    DevBuf db, dx;
+    // the device copies of b and x stay with the context (grown, never shrunk)
+    // so that repeated host calls allocate nothing
+    DevBuf &db = c->host_b, &dx = c->host_x;
     int st;
     if ((st = db.ensure(n3 * sizeof(double2))) || (st = dx.ensure((size_t)n_shift * n3 * sizeof(double2)))) return st;
     cudaStream_t s = c->stream;
@@ -232,8 +234,6 @@ int lqcd_mscg_solve(lqcd_ctx *c, double mass, const double *shifts, int n_shift,
         if (st2) st = st2;
         else if (e != cudaSuccess) st = cuda_fail(e, "lqcd_mscg_solve");
     }
-    db.release();
-    dx.release();
     if (info) info->secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     return st;
 }

@@ -109,6 +109,7 @@ struct lqcd_ctx {
     lqcd::DevBuf stout_F;     // two forces on the links, 8 reals each ([2][4][2][8][Vh] double)
     int stout_n = 0;          // active stout levels (0: the links in use are the uploaded ones)
     double stout_rho = 0.0;
+    lqcd::DevBuf host_b, host_x;  // device copies of b and x of the host multi-shift call
     lqcd::DevBuf ff_y;        // D_oe x_i of the fermion force [n][3][Vh] double2
     int md_links_newest = 0;  // LQCD_PREC_FP64: lnk_nat holds the newest links; FP32: lnk_f18
     bool links_derived_stale = false;  // MD moved the links: derived formats need a rebuild

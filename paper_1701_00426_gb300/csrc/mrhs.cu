@@ -65,28 +65,44 @@ __device__ __forceinline__ void mrhs_site(const MrhsArgs &A, const Stencil &S, i
             const int idx = dir == 0 ? f : b;
             const uint32_t ng = dir == 0 ? nf : nb;
             load_link_f32<LF>(A.links, mu, dir == 0 ? A.P : 1 - A.P, dir == 0 ? i : b, Vh, U);
+            // fields two at a time in one 16-byte load when R is even (the
+            // fields of a site are contiguous, so the G threads of a site
+            // read one contiguous run); per field the arithmetic is the same
+            constexpr int W = (R % 2 == 0) ? 2 : 1;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                float2 v[3];
+            for (int r = 0; r < R; r += W) {
+                float2 v[W][3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float2 t = __ldg(A.in + ((size_t)c * Vh + idx) * n + j0 + r);
-                    v[c] = make_float2(__uint_as_float(__float_as_uint(t.x) ^ ng), __uint_as_float(__float_as_uint(t.y) ^ ng));
+                    const float2 *src = A.in + ((size_t)c * Vh + idx) * n + j0 + r;
+                    if constexpr (W == 2) {
+                        const float4 t = __ldg(reinterpret_cast<const float4 *>(src));
+                        v[0][c] = make_float2(__uint_as_float(__float_as_uint(t.x) ^ ng),
+                                              __uint_as_float(__float_as_uint(t.y) ^ ng));
+                        v[1][c] = make_float2(__uint_as_float(__float_as_uint(t.z) ^ ng),
+                                              __uint_as_float(__float_as_uint(t.w) ^ ng));
+                    } else {
+                        const float2 t = __ldg(src);
+                        v[0][c] = make_float2(__uint_as_float(__float_as_uint(t.x) ^ ng),
+                                              __uint_as_float(__float_as_uint(t.y) ^ ng));
+                    }
                 }
 #pragma unroll
-                for (int a = 0; a < 3; ++a)
+                for (int q = 0; q < W; ++q)
 #pragma unroll
-                    for (int bb = 0; bb < 3; ++bb) {
-                        if (dir == 0) {
-                            const float2 u = U[a * 3 + bb];
-                            acc[r][a].x = __fmaf_rn(u.x, v[bb].x, __fmaf_rn(-u.y, v[bb].y, acc[r][a].x));
-                            acc[r][a].y = __fmaf_rn(u.x, v[bb].y, __fmaf_rn(u.y, v[bb].x, acc[r][a].y));
-                        } else {
-                            const float2 u = U[bb * 3 + a];
-                            acc[r][a].x = __fmaf_rn(u.x, v[bb].x, __fmaf_rn(u.y, v[bb].y, acc[r][a].x));
-                            acc[r][a].y = __fmaf_rn(u.x, v[bb].y, __fmaf_rn(-u.y, v[bb].x, acc[r][a].y));
+                    for (int a = 0; a < 3; ++a)
+#pragma unroll
+                        for (int bb = 0; bb < 3; ++bb) {
+                            if (dir == 0) {
+                                const float2 u = U[a * 3 + bb];
+                                acc[r + q][a].x = __fmaf_rn(u.x, v[q][bb].x, __fmaf_rn(-u.y, v[q][bb].y, acc[r + q][a].x));
+                                acc[r + q][a].y = __fmaf_rn(u.x, v[q][bb].y, __fmaf_rn(u.y, v[q][bb].x, acc[r + q][a].y));
+                            } else {
+                                const float2 u = U[bb * 3 + a];
+                                acc[r + q][a].x = __fmaf_rn(u.x, v[q][bb].x, __fmaf_rn(u.y, v[q][bb].y, acc[r + q][a].x));
+                                acc[r + q][a].y = __fmaf_rn(u.x, v[q][bb].y, __fmaf_rn(-u.y, v[q][bb].x, acc[r + q][a].y));
+                            }
                         }
-                    }
             }
         }
     }
@@ -113,10 +129,18 @@ __global__ void __launch_bounds__(kTile) k_deo_mrhs(const MrhsArgs A)
     float2 acc[R][3];
     mrhs_site<LF, R>(A, S, site, j0, acc);
 #pragma unroll
-    for (int r = 0; r < R; ++r)
+    for (int c = 0; c < 3; ++c) {
+        float2 *dst = A.out + ((size_t)c * A.g.Vh + site) * A.n + j0;
+        if constexpr (R % 2 == 0) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
-            A.out[((size_t)c * A.g.Vh + site) * A.n + j0 + r] = make_float2(0.5f * acc[r][c].x, 0.5f * acc[r][c].y);
+            for (int r = 0; r < R; r += 2)
+                *reinterpret_cast<float4 *>(dst + r) = make_float4(0.5f * acc[r][c].x, 0.5f * acc[r][c].y,
+                                                                   0.5f * acc[r + 1][c].x, 0.5f * acc[r + 1][c].y);
+        } else {
+#pragma unroll
+            for (int r = 0; r < R; ++r) dst[r] = make_float2(0.5f * acc[r][c].x, 0.5f * acc[r][c].y);
+        }
+    }
 }
 
 // Per-field deterministic block + tile reduction: vals[r] belongs to field
@@ -382,7 +406,9 @@ int deo_mrhs_launch(lqcd_ctx *c, int P, int n, int recon, const void *in, void *
     A.in = (const float2 *)in;
     A.out = (float2 *)out;
     const int lf = recon == 18 ? LF_F32_18 : LF_F32_12;
-    const int R = mrhs_pick_R(c, A, lf, s);
+    // an even R reads and writes two fields per 16-byte access
+    const bool al16 = ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0);
+    const int R = al16 ? mrhs_pick_R(c, A, lf, s) : 1;
     A.G = n / R;
     const unsigned nb = (unsigned)(((long)c->Vh * A.G + kTile - 1) / kTile);
     launch_deo_mrhs(A, lf, R, nb, s);

@@ -356,11 +356,20 @@ class Context:
                                            _dptr(out), _stream_ptr(stream)))
 
     # ------------------------------------------------------------- solvers
-    def mscg_solve(self, mass: float, shifts, tol: float, b: np.ndarray, allow_noconv: bool = False):
-        """Host call: returns (x [n_shift, Vh, 3], info dict)."""
+    def mscg_solve(self, mass: float, shifts, tol: float, b: np.ndarray, allow_noconv: bool = False,
+                   out: np.ndarray | None = None):
+        """Host call: returns (x [n_shift, Vh, 3], info dict).  `out`, a
+        C-contiguous complex128 array of that shape, receives x instead of a
+        new array (a reused buffer avoids first-touch page faults)."""
         sh = np.ascontiguousarray(shifts, dtype=np.float64)
         bb = _c128(b, (self.Vh, 3))
-        x = np.empty((sh.size, self.Vh, 3), np.complex128)
+        shape = (sh.size, self.Vh, 3)
+        if out is None:
+            x = np.empty(shape, np.complex128)
+        else:
+            if out.shape != shape or out.dtype != np.complex128 or not out.flags.c_contiguous:
+                raise ValueError(f"out must be a C-contiguous complex128 array of shape {shape}")
+            x = out
         info = lqcd_solve_info()
         st = self.lib.lqcd_mscg_solve(self.h, float(mass), sh.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                       sh.size, float(tol), _ptr(bb), _ptr(x), ctypes.byref(info))

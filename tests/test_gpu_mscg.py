@@ -120,6 +120,29 @@ def test_device_call_equals_host_call_and_is_deterministic(gpu):
     assert np.array_equal(x1, x3)
 
 
+def test_host_call_into_caller_buffer(gpu):
+    """out= receives the solution in place; host calls with more and then
+    fewer shifts reuse the context's device copies; a wrong buffer is refused."""
+    dims = (4, 6, 8, 10)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=5)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        ref, _ = c.mscg_solve(0.05, [1e-3, 0.1, 1.0], 1e-10, b)
+        out = np.full((3, c.Vh, 3), np.nan + 0j)
+        x, _ = c.mscg_solve(0.05, [1e-3, 0.1, 1.0], 1e-10, b, out=out)
+        assert x is out and np.array_equal(out, ref)
+        bytes_after = c.device_bytes()
+        one, _ = c.mscg_solve(0.05, [0.1], 1e-10, b)
+        assert c.device_bytes() == bytes_after
+        x, _ = c.mscg_solve(0.05, [1e-3, 0.1, 1.0], 1e-10, b, out=out)
+        assert np.array_equal(out, ref)
+        for bad in (np.zeros((2, c.Vh, 3), complex), np.zeros((3, c.Vh, 3), np.complex64),
+                    np.zeros((3, 3, c.Vh), complex).transpose(0, 2, 1)):
+            with pytest.raises(ValueError):
+                c.mscg_solve(0.05, [1e-3, 0.1, 1.0], 1e-10, b, out=bad)
+
+
 def test_free_field_closed_form(gpu):
     import pins
     dims = (4, 4, 6, 8)
