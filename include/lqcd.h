@@ -213,6 +213,20 @@ int lqcd_deo_apply_ex(lqcd_ctx *ctx, int out_parity, int prec, int recon,
 int lqcd_deo_apply_mrhs(lqcd_ctx *ctx, int out_parity, int n_rhs, int recon,
                         const void *in, void *out, void *stream);
 
+/* Batch layouts of lqcd_deo_apply_mrhs_layout. */
+#define LQCD_MRHS_SITE_MAJOR 0   /* complex64 [3][Vh][n_rhs]: the fields of a site contiguous */
+#define LQCD_MRHS_FIELD_MAJOR 1  /* complex64 [3][n_rhs][Vh]: the sites of a field contiguous */
+
+/* lqcd_deo_apply_mrhs with the batch layout chosen by the caller
+ * (LQCD_MRHS_SITE_MAJOR is lqcd_deo_apply_mrhs).  In the field-major layout
+ * neighbouring threads read neighbouring sites of one field, so every
+ * spinor access is a contiguous run across the warp; each thread still
+ * applies a link it loads once to several fields.  Same bits as the
+ * single-field operator in either layout.  LQCD_EINVAL for another layout
+ * value.  Asynchronous on `stream`. */
+int lqcd_deo_apply_mrhs_layout(lqcd_ctx *ctx, int out_parity, int n_rhs, int recon, int layout,
+                               const void *in, void *out, void *stream);
+
 /* ----------------------------------------------------------------- solver */
 
 /* Multi-shift CG for (A + shifts[i]) x_i = b, A = m^2 - D_eo D_oe on even

@@ -212,6 +212,13 @@ int lqcd_deo_apply_mrhs(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const
     return deo_mrhs_launch(c, out_parity, n_rhs, recon, in, out, stream ? (cudaStream_t)stream : c->stream);
 }
 
+int lqcd_deo_apply_mrhs_layout(lqcd_ctx *c, int out_parity, int n_rhs, int recon, int layout, const void *in,
+                               void *out, void *stream)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    return deo_mrhs_launch(c, out_parity, n_rhs, recon, in, out, stream ? (cudaStream_t)stream : c->stream, layout);
+}
+
 int lqcd_mscg_solve(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double *b,
                     double *x, lqcd_solve_info *info)
 {

@@ -209,7 +209,8 @@ int rational_apply_dev(lqcd_ctx *c, double mass, double a0, const double *a, con
                        cudaStream_t s_user);
 
 // mrhs.cu
-int deo_mrhs_launch(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const void *in, void *out, cudaStream_t s);
+int deo_mrhs_launch(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const void *in, void *out, cudaStream_t s,
+                    int layout = 0);
 int cg_solve_mrhs(lqcd_ctx *c, double mass, double sigma, int n_rhs, double tol, const double *b, double *x,
                   lqcd_solve_info *info);
 int mrhs_cg_core(lqcd_ctx *c, double mass, const double *sigma, int n, double tol, const double2 *b, int b_stride,

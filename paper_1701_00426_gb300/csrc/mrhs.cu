@@ -46,7 +46,17 @@ struct MrhsArgs {
     int ntiles;
 };
 
-template <int LF, int R>
+// Field (c, site, j) of a batch: site-major [3][Vh][n] (FM = false: the
+// fields of a site are contiguous) or field-major [3][n][Vh] (FM = true:
+// the sites of a field are contiguous, so consecutive threads read
+// consecutive sites).
+template <bool FM>
+__device__ __forceinline__ size_t mrhs_at(int c, int site, int j, int Vh, int n)
+{
+    return FM ? ((size_t)c * n + j) * Vh + site : ((size_t)c * Vh + site) * n + j;
+}
+
+template <int LF, int R, bool FM = false>
 __device__ __forceinline__ void mrhs_site(const MrhsArgs &A, const Stencil &S, int i, int j0, float2 (&acc)[R][3])
 {
     const int Vh = A.g.Vh, n = A.n;
@@ -68,13 +78,13 @@ __device__ __forceinline__ void mrhs_site(const MrhsArgs &A, const Stencil &S, i
             // fields two at a time in one 16-byte load when R is even (the
             // fields of a site are contiguous, so the G threads of a site
             // read one contiguous run); per field the arithmetic is the same
-            constexpr int W = (R % 2 == 0) ? 2 : 1;
+            constexpr int W = (R % 2 == 0 && !FM) ? 2 : 1;
 #pragma unroll
             for (int r = 0; r < R; r += W) {
                 float2 v[W][3];
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float2 *src = A.in + ((size_t)c * Vh + idx) * n + j0 + r;
+                    const float2 *src = A.in + mrhs_at<FM>(c, idx, j0 + r, Vh, n);
                     if constexpr (W == 2) {
                         const float4 t = __ldg(reinterpret_cast<const float4 *>(src));
                         v[0][c] = make_float2(__uint_as_float(__float_as_uint(t.x) ^ ng),
@@ -141,6 +151,25 @@ __global__ void __launch_bounds__(kTile) k_deo_mrhs(const MrhsArgs A)
             for (int r = 0; r < R; ++r) dst[r] = make_float2(0.5f * acc[r][c].x, 0.5f * acc[r][c].y);
         }
     }
+}
+
+// Plain multi-RHS D on field-major batches: block (x, y) takes 256
+// consecutive sites of field group y.
+template <int LF, int R>
+__global__ void __launch_bounds__(kTile) k_deo_mrhs_fm(const MrhsArgs A)
+{
+    const int site = blockIdx.x * kTile + threadIdx.x;
+    if (site >= A.g.Vh) return;
+    const int j0 = blockIdx.y * R;
+    Stencil S;
+    make_stencil(A.g, site, A.P, S);
+    float2 acc[R][3];
+    mrhs_site<LF, R, true>(A, S, site, j0, acc);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            A.out[mrhs_at<true>(c, site, j0 + r, A.g.Vh, A.n)] = make_float2(0.5f * acc[r][c].x, 0.5f * acc[r][c].y);
 }
 
 // Per-field deterministic block + tile reduction: vals[r] belongs to field
@@ -327,8 +356,26 @@ static void launch_deo_mrhs_R(const MrhsArgs &A, int R, unsigned nb, cudaStream_
     else k_deo_mrhs<LF, 1><<<nb, kTile, 0, s>>>(A);
 }
 
-static void launch_deo_mrhs(const MrhsArgs &A, int lf, int R, unsigned nb, cudaStream_t s)
+template <int LF>
+static void launch_deo_mrhs_fm_R(const MrhsArgs &A, int R, cudaStream_t s)
 {
+    const dim3 grid((unsigned)((A.g.Vh + kTile - 1) / kTile), (unsigned)(A.n / R));
+    if (R == 16) k_deo_mrhs_fm<LF, 16><<<grid, kTile, 0, s>>>(A);
+    else if (R == 8) k_deo_mrhs_fm<LF, 8><<<grid, kTile, 0, s>>>(A);
+    else if (R == 4) k_deo_mrhs_fm<LF, 4><<<grid, kTile, 0, s>>>(A);
+    else if (R == 2) k_deo_mrhs_fm<LF, 2><<<grid, kTile, 0, s>>>(A);
+    else k_deo_mrhs_fm<LF, 1><<<grid, kTile, 0, s>>>(A);
+}
+
+// layout: 0 site-major, 1 field-major
+static void launch_deo_mrhs(const MrhsArgs &A, int lf, int R, unsigned nb, cudaStream_t s, int layout = 0)
+{
+    if (layout == 1) {
+        if (lf == LF_F32_18) launch_deo_mrhs_fm_R<LF_F32_18>(A, R, s);
+        else if (lf == LF_F32_12) launch_deo_mrhs_fm_R<LF_F32_12>(A, R, s);
+        else launch_deo_mrhs_fm_R<LF_F16_12>(A, R, s);
+        return;
+    }
     if (lf == LF_F32_18) launch_deo_mrhs_R<LF_F32_18>(A, R, nb, s);
     else if (lf == LF_F32_12) launch_deo_mrhs_R<LF_F32_12>(A, R, nb, s);
     else launch_deo_mrhs_R<LF_F16_12>(A, R, nb, s);
@@ -350,10 +397,11 @@ static void launch_deo2_R(const MrhsArgs &A, int R, unsigned nb, cudaStream_t s)
 static std::mutex g_mr_mu;
 static std::map<std::string, int> g_mr_tune;
 
-static int mrhs_pick_R(lqcd_ctx *c, MrhsArgs A, int lf, cudaStream_t s)
+static int mrhs_pick_R(lqcd_ctx *c, MrhsArgs A, int lf, cudaStream_t s, int layout)
 {
     char key[96];
-    snprintf(key, sizeof key, "n%d lf%d %dx%dx%dx%d", A.n, lf, c->dims[0], c->dims[1], c->dims[2], c->dims[3]);
+    snprintf(key, sizeof key, "n%d lf%d L%d %dx%dx%dx%d", A.n, lf, layout, c->dims[0], c->dims[1], c->dims[2],
+             c->dims[3]);
     {
         std::lock_guard<std::mutex> lk(g_mr_mu);
         auto it = g_mr_tune.find(key);
@@ -370,9 +418,9 @@ static int mrhs_pick_R(lqcd_ctx *c, MrhsArgs A, int lf, cudaStream_t s)
         if (A.n % R) continue;
         A.G = A.n / R;
         const unsigned nb = (unsigned)(((long)c->Vh * A.G + kTile - 1) / kTile);
-        launch_deo_mrhs(A, lf, R, nb, s);  // warm
+        launch_deo_mrhs(A, lf, R, nb, s, layout);  // warm
         cudaEventRecord(e0, s);
-        for (int r = 0; r < 3; ++r) launch_deo_mrhs(A, lf, R, nb, s);
+        for (int r = 0; r < 3; ++r) launch_deo_mrhs(A, lf, R, nb, s, layout);
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float t = 0.f;
@@ -390,8 +438,9 @@ static int mrhs_pick_R(lqcd_ctx *c, MrhsArgs A, int lf, cudaStream_t s)
     return best_R;
 }
 
-int deo_mrhs_launch(lqcd_ctx *c, int P, int n, int recon, const void *in, void *out, cudaStream_t s)
+int deo_mrhs_launch(lqcd_ctx *c, int P, int n, int recon, const void *in, void *out, cudaStream_t s, int layout)
 {
+    if (layout != 0 && layout != 1) return fail(LQCD_EINVAL, "layout must be 0 (site-major) or 1 (field-major)");
     if (int lr = links_ready(c)) return lr;
     if (P != 0 && P != 1) return fail(LQCD_EINVAL, "out_parity must be 0 or 1");
     if (n < 1 || n > kMaxRhs) return fail(LQCD_EINVAL, "n_rhs must be in 1..16");
@@ -408,10 +457,10 @@ int deo_mrhs_launch(lqcd_ctx *c, int P, int n, int recon, const void *in, void *
     const int lf = recon == 18 ? LF_F32_18 : LF_F32_12;
     // an even R reads and writes two fields per 16-byte access
     const bool al16 = ((uintptr_t)in % 16 == 0) && ((uintptr_t)out % 16 == 0);
-    const int R = al16 ? mrhs_pick_R(c, A, lf, s) : 1;
+    const int R = (al16 || layout == 1) ? mrhs_pick_R(c, A, lf, s, layout) : 1;
     A.G = n / R;
     const unsigned nb = (unsigned)(((long)c->Vh * A.G + kTile - 1) / kTile);
-    launch_deo_mrhs(A, lf, R, nb, s);
+    launch_deo_mrhs(A, lf, R, nb, s, layout);
     LQCD_CUDA(cudaGetLastError());
     c->launches += 1;
     return LQCD_OK;

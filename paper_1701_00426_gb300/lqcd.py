@@ -50,7 +50,7 @@ EXPORTED = [
     "lqcd_serve_drain", "lqcd_serve_stats_get", "lqcd_serve_destroy", "lqcd_serve_set_opts",
     "lqcd_mom_upload", "lqcd_mom_download", "lqcd_gauge_mom_update", "lqcd_gauge_link_update",
     "lqcd_gauge_md_steps", "lqcd_gauge_action", "lqcd_mom_energy", "lqcd_fermion_force_update",
-    "lqcd_stout_smear", "lqcd_stout_restore", "lqcd_stout_force",
+    "lqcd_stout_smear", "lqcd_stout_restore", "lqcd_stout_force", "lqcd_deo_apply_mrhs_layout",
 ]
 
 
@@ -155,6 +155,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_fermion_force_update": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double, dp, dp, ctypes.c_int,
                                                      ctypes.c_double, vp, ctypes.c_double, dp,
                                                      ctypes.POINTER(lqcd_solve_info)]),
+        "lqcd_deo_apply_mrhs_layout": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                      vp, vp, vp]),
         "lqcd_stout_smear": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
         "lqcd_stout_restore": (ctypes.c_int, [vp]),
         "lqcd_stout_force": (ctypes.c_int, [vp, vp, vp, ctypes.c_size_t]),
@@ -351,9 +353,14 @@ class Context:
         check(self.lib.lqcd_deo_apply_ex(self.h, int(out_parity), int(prec), int(recon), _dptr(inp), _dptr(out),
                                          _stream_ptr(stream)))
 
-    def deo_apply_mrhs(self, out_parity: int, n_rhs: int, recon: int, inp, out, stream=None):
-        check(self.lib.lqcd_deo_apply_mrhs(self.h, int(out_parity), int(n_rhs), int(recon), _dptr(inp),
-                                           _dptr(out), _stream_ptr(stream)))
+    def deo_apply_mrhs(self, out_parity: int, n_rhs: int, recon: int, inp, out, stream=None, layout: int = 0):
+        """Multi-RHS D on device batches: layout 0 [3][Vh][n], 1 [3][n][Vh]."""
+        if layout == 0:
+            check(self.lib.lqcd_deo_apply_mrhs(self.h, int(out_parity), int(n_rhs), int(recon), _dptr(inp),
+                                               _dptr(out), _stream_ptr(stream)))
+        else:
+            check(self.lib.lqcd_deo_apply_mrhs_layout(self.h, int(out_parity), int(n_rhs), int(recon), int(layout),
+                                                      _dptr(inp), _dptr(out), _stream_ptr(stream)))
 
     # ------------------------------------------------------------- solvers
     def mscg_solve(self, mass: float, shifts, tol: float, b: np.ndarray, allow_noconv: bool = False,

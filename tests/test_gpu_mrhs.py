@@ -48,6 +48,29 @@ def test_mrhs_equals_single_rhs_bitwise(gpu, n, recon):
                 assert np.array_equal(got[j], gpu.from_device_spinor(os_)), f"field {j}"
 
 
+@pytest.mark.parametrize("n", [1, 3, 4, 16])
+@pytest.mark.parametrize("recon", [18, 12])
+def test_field_major_equals_site_major_bitwise(gpu, n, recon):
+    """The field-major layout [3][n][Vh] gives, field by field, the bits of
+    the site-major layout (and so of the single-field operator)."""
+    dims = (4, 6, 8, 10)
+    U = inputs.random_links(dims)
+    fields = [inputs.gaussian_field(dims, k=j) for j in range(n)]
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        for parity in (0, 1):
+            xs = batch_to_device(fields)                       # [3][Vh][n]
+            os_ = torch.empty_like(xs)
+            c.deo_apply_mrhs(parity, n, recon, xs, os_)
+            xf = xs.permute(0, 2, 1).contiguous()              # [3][n][Vh]
+            of = torch.empty_like(xf)
+            c.deo_apply_mrhs(parity, n, recon, xf, of, layout=1)
+            torch.cuda.synchronize()
+            assert torch.equal(of.permute(0, 2, 1), os_)
+        with pytest.raises(gpu.LqcdError):
+            c.deo_apply_mrhs(0, n, recon, xf, of, layout=2)
+
+
 @pytest.mark.parametrize("n", [4, 16])
 def test_mrhs_unaligned_buffers_equal_aligned(gpu, n):
     """in / out 8 bytes off a 16-byte boundary take the one-field-per-access
