@@ -55,6 +55,38 @@ def test_15_shifts_fp64(gpu, orc, dims):
     check_solution(orc, dims, U, 0.01, shifts, b, x, 1e-10, xref)
 
 
+def test_timed_workload_32_sampled_shifts(gpu, orc):
+    """The configuration bench.py times: 32^4 hot links (seed 1701), m = 0.01,
+    the 15 log-spaced shifts, tol 1e-10, staged FP64 kernels, through the
+    device call that the bench times.  The oracle recomputes the true
+    residual of the smallest, a middle and the largest shift from the
+    returned solutions.  The iteration count is within 5 % of the oracle's
+    own full-solve count (tests/golden/oracle_counts.json): the double-float
+    iteration rounds at about 2^-48, so the worst-conditioned shift (kappa
+    ~ 1.5e5) takes a few per cent more iterations than in IEEE FP64."""
+    import json
+    import os
+    dims = (32, 32, 32, 32)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=0)
+    shifts = inputs.log_shifts(15)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        bd = gpu.to_device_spinor(b)
+        xd = torch.empty((15, 3, c.Vh), dtype=torch.complex128, device="cuda")
+        info = c.mscg_solve_dev(0.01, shifts, 1e-10, bd, xd)
+        x = gpu.from_device_spinor(xd)
+    assert max(info["true_resid"][:15]) <= 1e-10
+    orc.set_threads(0)
+    for i in (0, 7, 14):
+        r = orc.true_residual(dims, U, 0.01, shifts[i], b, x[i])
+        assert r <= 1e-10, f"shift {shifts[i]}: oracle-recomputed true residual {r:.3e}"
+    golden = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_counts.json")
+    with open(golden) as f:
+        counts = json.load(f)["mscg_32x32x32x32_m0.01_15shifts_tol1e-10"]
+    assert abs(info["iters"] - counts["iters"]) <= 0.05 * counts["iters"]
+
+
 @pytest.mark.parametrize("prec,recon,fp64_until",
                          [(1, 18, 1e-4), (1, 12, 1e-4), (1, 12, 1e-2), (1, 18, 0.0), (1, 12, 0.0), (2, 12, 0.0)])
 def test_15_shifts_mixed_precision(gpu, orc, prec, recon, fp64_until):
