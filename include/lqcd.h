@@ -435,6 +435,16 @@ int lqcd_serve_stats_get(lqcd_server *srv, lqcd_serve_stats *stats);
 /* Stop the scheduler, free every resource.  Unpolled results are dropped. */
 void lqcd_serve_destroy(lqcd_server *srv);
 
+/* Failure-detection self-test of the bounded device waits.  Every wait of the
+ * staged kernels (a consumer for a stage of links, the producer for a free
+ * stage) gives up after a time limit, records the stall, and the call
+ * returns LQCD_ETIMEOUT with the context still usable.  This call runs one
+ * block of the staged layout whose stage is never filled, with the wait
+ * limited to limit_s seconds (0 < limit_s <= 10), and returns what such a
+ * stall returns: LQCD_ETIMEOUT.  No fault, no hang; the context stays
+ * usable.  Synchronous. */
+int lqcd_selftest_stage_wait(lqcd_ctx *ctx, double limit_s);
+
 /* ---------------------------------------------------------------- stout smearing
  * Stout smearing of the fermion links (Sec. 2.1: stout-improved staggered
  * action, Ref. Morningstar:2003gk; Sec. 2.2: a few stout levels).  One level

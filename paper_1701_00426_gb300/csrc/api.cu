@@ -212,6 +212,12 @@ int lqcd_deo_apply_mrhs(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const
     return deo_mrhs_launch(c, out_parity, n_rhs, recon, in, out, stream ? (cudaStream_t)stream : c->stream);
 }
 
+int lqcd_selftest_stage_wait(lqcd_ctx *c, double limit_s)
+{
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    return stage_wait_selftest(c, limit_s);
+}
+
 int lqcd_deo_apply_mrhs_layout(lqcd_ctx *c, int out_parity, int n_rhs, int recon, int layout, const void *in,
                                void *out, void *stream)
 {

@@ -465,6 +465,41 @@ __global__ void __launch_bounds__(kStagedThreads, kStagedMinBlocks)
 }
 
 
+// Self-test of the bounded stage wait.  One block of the staged layout whose
+// producer issues nothing: every consumer waits for stage 0, which no copy
+// ever fills, gives up after limit_ns (the wait the staged kernels use, with
+// a short limit), records the stall, and the block leaves through
+// ring_finish like a staged kernel.  *status = 1 when the waits gave up.
+__global__ void __launch_bounds__(kStagedThreads) k_stage_wait_selftest(uint64_t limit_ns, int *status)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    RingDF &R = *reinterpret_cast<RingDF *>(smem_raw);
+    ring_init(R);
+    if (threadIdx.x < kStagedConsumers && !mbar_wait(&R.full[0], 0u, limit_ns)) R.stalled = 1;
+    __syncthreads();
+    if (threadIdx.x == 0) *status = R.stalled;
+    ring_finish(R);
+}
+
+int stage_wait_selftest(lqcd_ctx *c, double limit_s)
+{
+    if (!(limit_s > 0.0 && limit_s <= 10.0)) return fail(LQCD_EINVAL, "limit must be in (0, 10] seconds");
+    LQCD_CUDA(cudaFuncSetAttribute(k_stage_wait_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)kRingDFBytes));
+    DevBuf st;
+    int rc;
+    if ((rc = st.ensure(sizeof(int)))) return rc;
+    LQCD_CUDA(cudaMemsetAsync(st.ptr, 0, sizeof(int), c->stream));
+    k_stage_wait_selftest<<<1, kStagedThreads, kRingDFBytes, c->stream>>>((uint64_t)(limit_s * 1e9), st.as<int>());
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += 1;
+    int h = 0;
+    LQCD_CUDA(cudaMemcpyAsync(&h, st.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LQCD_CUDA(cudaStreamSynchronize(c->stream));
+    if (h) return fail(LQCD_ETIMEOUT, "self-test: the bounded wait for an unfilled stage ran out");
+    return LQCD_OK;
+}
+
 // Residency of the staged stand-alone kernel per device (0: cannot run).
 static std::mutex g_staged_mu;
 static int g_staged_blocks[64];

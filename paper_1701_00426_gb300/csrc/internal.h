@@ -138,6 +138,7 @@ int upload_links(lqcd_ctx *c, const double *host, size_t n);
 // Staged kernels: shared-memory attribute and residency, once per device.
 // Returns true when they can run on the current device.
 bool staged_deo_ready();
+int stage_wait_selftest(lqcd_ctx *c, double limit_s);
 bool staged_solver_ready();
 bool staged_active(const lqcd_ctx *c);   // staged option on and the staged link stream built
 // LQCD_ESTATE before an upload; otherwise makes every link format current

@@ -51,6 +51,7 @@ EXPORTED = [
     "lqcd_mom_upload", "lqcd_mom_download", "lqcd_gauge_mom_update", "lqcd_gauge_link_update",
     "lqcd_gauge_md_steps", "lqcd_gauge_action", "lqcd_mom_energy", "lqcd_fermion_force_update",
     "lqcd_stout_smear", "lqcd_stout_restore", "lqcd_stout_force", "lqcd_deo_apply_mrhs_layout",
+    "lqcd_selftest_stage_wait",
 ]
 
 
@@ -157,6 +158,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                                      ctypes.POINTER(lqcd_solve_info)]),
         "lqcd_deo_apply_mrhs_layout": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                       vp, vp, vp]),
+        "lqcd_selftest_stage_wait": (ctypes.c_int, [vp, ctypes.c_double]),
         "lqcd_stout_smear": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
         "lqcd_stout_restore": (ctypes.c_int, [vp]),
         "lqcd_stout_force": (ctypes.c_int, [vp, vp, vp, ctypes.c_size_t]),
@@ -308,6 +310,11 @@ class Context:
                                                  sh.ctypes.data_as(dp), sh.size, float(tol), _ptr(pp), float(eps),
                                                  ctypes.byref(act), ctypes.byref(info)))
         return act.value, info.as_dict()
+
+    def selftest_stage_wait(self, limit_s: float = 0.05):
+        """Run the bounded-wait self-test (lqcd_selftest_stage_wait); raises
+        LqcdError with status LQCD_ETIMEOUT when the wait ran out as designed."""
+        check(self.lib.lqcd_selftest_stage_wait(self.h, float(limit_s)))
 
     def stout_smear(self, rho: float, levels: int):
         """Smear the links `levels` times (lqcd_stout_smear)."""

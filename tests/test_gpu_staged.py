@@ -137,3 +137,31 @@ def test_staged_packed_equals_per_thread_solo(gpu):
     for c in ctxs:
         c.close()
 
+
+
+def test_bounded_stage_wait_times_out_and_context_survives(gpu, orc):
+    """Failure detection without a fault: a staged block waits for a stage
+    that nothing fills; the bounded wait gives up after 50 ms, the call
+    returns LQCD_ETIMEOUT, and the same context then computes D_eo and a
+    solve correctly."""
+    import time
+    dims = (4, 6, 8, 10)
+    U = inputs.random_links(dims, seed=120)
+    x = inputs.gaussian_field(dims, k=120)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        for limit in (0.05, 0.2):
+            t0 = time.perf_counter()
+            with pytest.raises(gpu.LqcdError) as e:
+                c.selftest_stage_wait(limit)
+            dt = time.perf_counter() - t0
+            assert e.value.status == gpu.LQCD_ETIMEOUT
+            assert limit <= dt < limit + 5.0
+        with pytest.raises(gpu.LqcdError) as e:
+            c.selftest_stage_wait(0.0)
+        assert e.value.status == gpu.LQCD_EINVAL
+        y = c.deo_apply(0, x)
+        ref = orc.deo(dims, 0, U, x)
+        assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref)
+        xs, info = c.mscg_solve(0.05, [1e-3, 0.1], 1e-10, x)
+        assert max(info["true_resid"][:2]) <= 1e-10
