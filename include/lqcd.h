@@ -132,6 +132,13 @@ void lqcd_default_opts(lqcd_opts *opts);
 /* Last error message of the calling thread ("" if none). */
 const char *lqcd_last_error(void);
 
+/* Host-side fault injection for tests of the error paths: the k-th device
+ * allocation from now (k >= 1) fails as an out-of-memory cudaMalloc would,
+ * and the call that made it returns LQCD_ENOMEM; k <= 0 disarms.  Process
+ * wide.  A failed lqcd_links_upload leaves the context without links
+ * (LQCD_ESTATE until the next successful upload). */
+void lqcd_inject_alloc_failure(long k);
+
 /* ABI version (major*10000 + minor*100 + patch). */
 int lqcd_version(void);
 

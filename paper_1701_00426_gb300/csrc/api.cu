@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <atomic>
 #include <string>
 
 #include "internal.h"
@@ -27,11 +28,17 @@ int cuda_fail(cudaError_t e, const char *what)
     return e == cudaErrorMemoryAllocation ? LQCD_ENOMEM : LQCD_ECUDA;
 }
 
+// Host-side fault injection (lqcd_inject_alloc_failure): the k-th device
+// allocation from now fails as cudaMalloc would.
+static std::atomic<long> g_fail_alloc{0};
+
 int DevBuf::ensure(size_t n)
 {
     if (n <= bytes && ptr) return LQCD_OK;
     release();
     if (n == 0) return LQCD_OK;
+    if (g_fail_alloc.load() > 0 && g_fail_alloc.fetch_sub(1) == 1)
+        return fail(LQCD_ENOMEM, "injected failure of a " + std::to_string(n) + "-byte device allocation");
     cudaError_t e = cudaMalloc(&ptr, n);
     if (e != cudaSuccess) {
         ptr = nullptr;
@@ -97,6 +104,8 @@ void lqcd_default_opts(lqcd_opts *o)
 }
 
 const char *lqcd_last_error(void) { return g_err.c_str(); }
+
+void lqcd_inject_alloc_failure(long k) { g_fail_alloc.store(k > 0 ? k : 0); }
 
 int lqcd_version(void) { return 100; }
 

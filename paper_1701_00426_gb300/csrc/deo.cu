@@ -179,6 +179,9 @@ int upload_links(lqcd_ctx *c, const double *host, size_t n)
     if (n != want) return fail(LQCD_EINVAL, "links: expected 4*V*18 = " + std::to_string(want) + " doubles, got " + std::to_string(n));
     const size_t Vh = c->Vh;
     int st;
+    // until this upload completes the context has no usable links: a failure
+    // below (allocation, copy, invalid entries) leaves it in that state
+    c->links_ok = false;
     if ((st = c->lnk_nat.ensure(72 * Vh * sizeof(double2)))) return st;
     if ((st = c->lnk_df.ensure(72 * Vh * sizeof(float4)))) return st;
     if ((st = c->lnk_f18.ensure(72 * Vh * sizeof(float2)))) return st;

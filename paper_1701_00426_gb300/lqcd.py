@@ -51,7 +51,7 @@ EXPORTED = [
     "lqcd_mom_upload", "lqcd_mom_download", "lqcd_gauge_mom_update", "lqcd_gauge_link_update",
     "lqcd_gauge_md_steps", "lqcd_gauge_action", "lqcd_mom_energy", "lqcd_fermion_force_update",
     "lqcd_stout_smear", "lqcd_stout_restore", "lqcd_stout_force", "lqcd_deo_apply_mrhs_layout",
-    "lqcd_selftest_stage_wait",
+    "lqcd_selftest_stage_wait", "lqcd_inject_alloc_failure",
 ]
 
 
@@ -159,6 +159,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_deo_apply_mrhs_layout": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                       vp, vp, vp]),
         "lqcd_selftest_stage_wait": (ctypes.c_int, [vp, ctypes.c_double]),
+        "lqcd_inject_alloc_failure": (None, [ctypes.c_long]),
         "lqcd_stout_smear": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
         "lqcd_stout_restore": (ctypes.c_int, [vp]),
         "lqcd_stout_force": (ctypes.c_int, [vp, vp, vp, ctypes.c_size_t]),
@@ -545,3 +546,9 @@ class Server:
         st = lqcd_serve_stats()
         check(self.lib.lqcd_serve_stats_get(self.h, ctypes.byref(st)))
         return st.as_dict()
+
+
+def inject_alloc_failure(k: int):
+    """The k-th device allocation from now fails with LQCD_ENOMEM (k <= 0
+    disarms); see lqcd_inject_alloc_failure."""
+    load().lqcd_inject_alloc_failure(int(k))

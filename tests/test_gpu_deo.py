@@ -215,3 +215,30 @@ def test_every_tuned_fp64_variant_matches_oracle(gpu, tmp_path, code):
     res = json.loads(r.stdout.strip().splitlines()[-1])
     for k, (n, m) in res.items():
         assert n <= FP64_TOL and m <= FP64_TOL, f"variant {code} case {k}: {n:.2e} {m:.2e}"
+
+
+def test_injected_allocation_failure_leaves_context_usable(gpu, orc):
+    """Host-side fault injection: a device allocation made to fail inside
+    lqcd_links_upload returns LQCD_ENOMEM and leaves the context without
+    links (LQCD_ESTATE, no kernel runs); the next upload succeeds and D_eo
+    matches the oracle.  Covered for the first upload (link storage) and a
+    re-upload (the staging buffer)."""
+    dims = (4, 6, 8, 10)
+    U = inputs.random_links(dims, seed=130)
+    x = inputs.gaussian_field(dims, k=130)
+    ref = orc.deo(dims, 0, U, x)
+    with gpu.Context(dims) as c:
+        try:
+            for attempt in range(2):
+                gpu.inject_alloc_failure(1)
+                with pytest.raises(gpu.LqcdError) as e:
+                    c.links_upload(U)
+                assert e.value.status == gpu.LQCD_ENOMEM and "injected" in str(e.value)
+                with pytest.raises(gpu.LqcdError) as e:
+                    c.deo_apply(0, x)
+                assert e.value.status == gpu.LQCD_ESTATE
+                c.links_upload(U)
+                y = c.deo_apply(0, x)
+                assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref)
+        finally:
+            gpu.inject_alloc_failure(0)
