@@ -46,7 +46,7 @@ COUNTS_KEY = "mscg_32x32x32x32_m0.01_15shifts_tol1e-10"
 # with the even sites (links stream from HBM at both sizes, spinors hit L2), so
 # a launch at V/2 sites moves bytes_per_site * V/2.  Reported only while the
 # kernel sources still hash to the captured version.
-K2_TRAFFIC = {"bytes_per_site": 1257.9, "src_sha256_16": "ec50f1e5a9e4a84e",
+K2_TRAFFIC = {"bytes_per_site": 1257.9, "src_sha256_16": "5954b1e13b6f073a",
               "sources": ["solver_kernels.cuh", "stencil_staged.cuh", "bulk.cuh", "deo_core.cuh", "common.cuh", "iteration.h"]}
 
 

@@ -139,6 +139,15 @@ const char *lqcd_last_error(void);
  * (LQCD_ESTATE until the next successful upload). */
 void lqcd_inject_alloc_failure(long k);
 
+/* Bounds-checked builds (liblqcd_checked.so, compiled with
+ * -DLQCD_CHECK_BOUNDS): every neighbour and link index a kernel computes is
+ * compared with its array extent; an index out of range is replaced by an
+ * in-range one and recorded.  This call synchronises the device, writes the
+ * OR of the recorded error bits since the last call to *word (0: no index
+ * was ever out of range) and clears them.  In the default build it writes 0
+ * and returns LQCD_ESTATE. */
+int lqcd_bounds_errors(unsigned *word);
+
 /* ABI version (major*10000 + minor*100 + patch). */
 int lqcd_version(void);
 

@@ -17,6 +17,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblqcd.so")
+# The bounds-checked variant (every neighbour index compared with its extent,
+# errors recorded in device words read by lqcd_bounds_errors), for tests.
+CHECKED_BUILD = os.path.join(HERE, "_build_checked")
+CHECKED_LIB = os.path.join(HERE, "liblqcd_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 UNITS = ["api.cu", "deo.cu", "solver.cu", "mrhs.cu", "serve.cu", "noalloc.cu", "rational.cu", "gauge.cu"]
@@ -43,12 +47,12 @@ def _headers_mtime() -> float:
     return m
 
 
-def _compile(unit: str, hdr_mtime: float, verbose: bool) -> str:
+def _compile(unit: str, hdr_mtime: float, verbose: bool, bdir: str = BUILD, defs=()) -> str:
     src = os.path.join(CSRC, unit)
-    obj = os.path.join(BUILD, unit.replace(".cu", ".o"))
+    obj = os.path.join(bdir, unit.replace(".cu", ".o"))
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_mtime):
         return obj
-    cmd = [nvcc(), *ARCH, *FLAGS, *EXTRA, "-c", src, "-o", obj]
+    cmd = [nvcc(), *ARCH, *FLAGS, *EXTRA, *defs, "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -59,25 +63,28 @@ def _compile(unit: str, hdr_mtime: float, verbose: bool) -> str:
     return obj
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile every unit (parallel) and link liblqcd.so; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    """Compile every unit (parallel) and link liblqcd.so; returns its path.
+    checked: the bounds-checked variant liblqcd_checked.so instead."""
+    bdir, lib = (CHECKED_BUILD, CHECKED_LIB) if checked else (BUILD, LIB)
+    defs = ("-DLQCD_CHECK_BOUNDS",) if checked else ()
+    os.makedirs(bdir, exist_ok=True)
     if force:
-        for f in os.listdir(BUILD):
+        for f in os.listdir(bdir):
             if f.endswith(".o"):
-                os.remove(os.path.join(BUILD, f))
+                os.remove(os.path.join(bdir, f))
     hm = _headers_mtime()
     with ThreadPoolExecutor(max_workers=len(UNITS)) as ex:
-        objs = list(ex.map(lambda u: _compile(u, hm, verbose), UNITS))
+        objs = list(ex.map(lambda u: _compile(u, hm, verbose, bdir, defs), UNITS))
     newest = max(os.path.getmtime(o) for o in objs)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
-        tmp = f"{LIB}.{os.getpid()}.tmp"
+    if not os.path.exists(lib) or os.path.getmtime(lib) < newest:
+        tmp = f"{lib}.{os.getpid()}.tmp"
         cmd = [nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

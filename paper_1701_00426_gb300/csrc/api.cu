@@ -7,6 +7,7 @@
 #include <cstring>
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "internal.h"
 
@@ -27,6 +28,17 @@ int cuda_fail(cudaError_t e, const char *what)
     g_err = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
     return e == cudaErrorMemoryAllocation ? LQCD_ENOMEM : LQCD_ECUDA;
 }
+
+#ifdef LQCD_CHECK_BOUNDS
+// Readers of the translation units' bounds error words (bounds-checked builds).
+static std::vector<BoundsReader> &bounds_readers()
+{
+    static std::vector<BoundsReader> r;
+    return r;
+}
+
+void register_bounds_reader(BoundsReader f) { bounds_readers().push_back(f); }
+#endif
 
 // Host-side fault injection (lqcd_inject_alloc_failure): the k-th device
 // allocation from now fails as cudaMalloc would.
@@ -107,6 +119,21 @@ const char *lqcd_last_error(void) { return g_err.c_str(); }
 
 void lqcd_inject_alloc_failure(long k) { g_fail_alloc.store(k > 0 ? k : 0); }
 
+int lqcd_bounds_errors(unsigned *word)
+{
+    if (!word) return fail(LQCD_EINVAL, "NULL argument");
+#ifdef LQCD_CHECK_BOUNDS
+    cudaDeviceSynchronize();
+    unsigned w = 0;
+    for (BoundsReader f : bounds_readers()) w |= f();
+    *word = w;
+    return LQCD_OK;
+#else
+    *word = 0;
+    return fail(LQCD_ESTATE, "library built without LQCD_CHECK_BOUNDS");
+#endif
+}
+
 int lqcd_version(void) { return 100; }
 
 int lqcd_create(const int dims[4], const lqcd_opts *opts, lqcd_ctx **out)
@@ -175,6 +202,7 @@ size_t lqcd_device_bytes(const lqcd_ctx *c) { return c ? ctx_device_bytes(c) : 0
 
 int lqcd_links_upload(lqcd_ctx *c, const double *links, size_t n)
 {
+    NvtxRange nvtx_("lqcd_links_upload");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     c->graph.reset();
     return upload_links(c, links, n);
@@ -188,6 +216,7 @@ int lqcd_links_download(lqcd_ctx *c, double *links, size_t n)
 
 int lqcd_deo_apply(lqcd_ctx *c, int out_parity, const void *in, void *out, int where, void *stream)
 {
+    NvtxRange nvtx_("lqcd_deo_apply");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     if (where == 1) return deo_launch(c, out_parity, LQCD_PREC_FP64, 18, in, out, (cudaStream_t)stream ? (cudaStream_t)stream : c->stream);
     if (where != 0) return fail(LQCD_EINVAL, "where must be 0 (host) or 1 (device)");
@@ -211,12 +240,14 @@ int lqcd_deo_apply(lqcd_ctx *c, int out_parity, const void *in, void *out, int w
 
 int lqcd_deo_apply_ex(lqcd_ctx *c, int out_parity, int prec, int recon, const void *in, void *out, void *stream)
 {
+    NvtxRange nvtx_("lqcd_deo_apply_ex");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     return deo_launch(c, out_parity, prec, recon, in, out, stream ? (cudaStream_t)stream : c->stream);
 }
 
 int lqcd_deo_apply_mrhs(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const void *in, void *out, void *stream)
 {
+    NvtxRange nvtx_("lqcd_deo_apply_mrhs");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     return deo_mrhs_launch(c, out_parity, n_rhs, recon, in, out, stream ? (cudaStream_t)stream : c->stream);
 }
@@ -230,6 +261,7 @@ int lqcd_selftest_stage_wait(lqcd_ctx *c, double limit_s)
 int lqcd_deo_apply_mrhs_layout(lqcd_ctx *c, int out_parity, int n_rhs, int recon, int layout, const void *in,
                                void *out, void *stream)
 {
+    NvtxRange nvtx_("lqcd_deo_apply_mrhs_layout");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     return deo_mrhs_launch(c, out_parity, n_rhs, recon, in, out, stream ? (cudaStream_t)stream : c->stream, layout);
 }
@@ -237,6 +269,7 @@ int lqcd_deo_apply_mrhs_layout(lqcd_ctx *c, int out_parity, int n_rhs, int recon
 int lqcd_mscg_solve(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const double *b,
                     double *x, lqcd_solve_info *info)
 {
+    NvtxRange nvtx_("lqcd_mscg_solve");
     const auto t0 = std::chrono::steady_clock::now();
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     if (!b || !x || !shifts) return fail(LQCD_EINVAL, "NULL argument");
@@ -263,6 +296,7 @@ int lqcd_mscg_solve(lqcd_ctx *c, double mass, const double *shifts, int n_shift,
 int lqcd_mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_shift, double tol, const void *b,
                         void *x, lqcd_solve_info *info, void *stream)
 {
+    NvtxRange nvtx_("lqcd_mscg_solve_dev");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     return mscg_solve_dev(c, mass, shifts, n_shift, tol, (const double2 *)b, (double2 *)x, info, (cudaStream_t)stream);
 }
@@ -277,6 +311,7 @@ int lqcd_profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n
 int lqcd_cg_solve_mrhs(lqcd_ctx *c, double mass, double sigma, int n_rhs, double tol, const double *b, double *x,
                        lqcd_solve_info *info)
 {
+    NvtxRange nvtx_("lqcd_cg_solve_mrhs");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     return cg_solve_mrhs(c, mass, sigma, n_rhs, tol, b, x, info);
 }
@@ -285,6 +320,7 @@ int lqcd_mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, con
                            const int *n_shift, const double *tol, const double *const *b, double *const *x,
                            lqcd_solve_info *info)
 {
+    NvtxRange nvtx_("lqcd_mscg_solve_packed");
     if (!ctxs || n < 1 || n > kMaxJobs || !mass || !shifts || !n_shift || !tol || !b || !x)
         return fail(LQCD_EINVAL, "bad packed-solve arguments");
     return mscg_solve_packed(ctxs, n, mass, shifts, n_shift, tol, b, x, info);

@@ -105,6 +105,48 @@ __host__ __device__ __forceinline__ void make_stencil(const Geom &g, int i, int 
     S.i = i;
 }
 
+// ------------------------------------------------------------------ bounds-checked builds
+// Built with -DLQCD_CHECK_BOUNDS, every neighbour index a kernel computes
+// (hop, the gauge kernels' site_of, the staged link stream's tile offsets)
+// is compared with its array extent before it is used.  An index out of
+// range is replaced by 0, an element in range, and bit 0 of the
+// translation unit's error word is set; lqcd_bounds_errors() reads and
+// clears the words.  Nothing traps, so the kernel runs to completion and
+// the context stays usable.  In the default build the check compiles to
+// nothing.
+#ifdef LQCD_CHECK_BOUNDS
+static __device__ unsigned int g_lqcd_bounds_err;
+#endif
+
+__host__ __device__ __forceinline__ int bound_index(int idx, int n)
+{
+#if defined(LQCD_CHECK_BOUNDS) && defined(__CUDA_ARCH__)
+    if ((unsigned)idx < (unsigned)n) return idx;
+    atomicOr(&g_lqcd_bounds_err, 1u);
+    return 0;
+#else
+    (void)n;
+    return idx;
+#endif
+}
+
+#ifdef LQCD_CHECK_BOUNDS
+// Host side: each translation unit registers a reader of its own word.
+using BoundsReader = unsigned (*)();
+void register_bounds_reader(BoundsReader f);  // api.cu
+static unsigned read_bounds_word()
+{
+    unsigned v = 0, z = 0;
+    if (cudaMemcpyFromSymbol(&v, g_lqcd_bounds_err, sizeof v) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_lqcd_bounds_err, &z, sizeof z) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return v;
+}
+static const int g_lqcd_bounds_registered = (register_bounds_reader(read_bounds_word), 0);
+#endif
+
 // Hop mu of site S: half indices of n+mu (fwd) and n-mu (bwd) and the sign
 // masks (0 or 0x80000000) of their contributions.  The forward hop adds
 // +s_mu(n) U_mu(n) psi(n+mu), the backward hop -s_mu(n-mu) U_mu(n-mu)^dag
@@ -117,8 +159,8 @@ __host__ __device__ __forceinline__ void hop(const Geom &g, const Stencil &S, in
     if (mu == 0) {
         const int xf = (S.x0 + 1 == g.N[0]) ? 0 : S.x0 + 1;
         const int xb = (S.x0 == 0) ? g.N[0] - 1 : S.x0 - 1;
-        fwd = S.rest + (xf >> 1);
-        bwd = S.rest + (xb >> 1);
+        fwd = bound_index(S.rest + (xf >> 1), g.Vh);
+        bwd = bound_index(S.rest + (xb >> 1), g.Vh);
         neg_f = 0u;
         neg_b = 1u << 31;
         return;
@@ -126,8 +168,8 @@ __host__ __device__ __forceinline__ void hop(const Geom &g, const Stencil &S, in
     const int x = mu == 1 ? S.x1 : (mu == 2 ? S.x2 : S.x3);
     const int n = g.N[mu];
     const int st = mu == 1 ? g.s1 : (mu == 2 ? g.s2 : g.s3);
-    fwd = (x == n - 1) ? S.i - (n - 1) * st : S.i + st;
-    bwd = (x == 0) ? S.i + (n - 1) * st : S.i - st;
+    fwd = bound_index((x == n - 1) ? S.i - (n - 1) * st : S.i + st, g.Vh);
+    bwd = bound_index((x == 0) ? S.i + (n - 1) * st : S.i - st, g.Vh);
     const int esum = mu == 1 ? S.x0 : (mu == 2 ? S.x0 + S.x1 : S.x0 + S.x1 + S.x2);
     uint32_t e = (uint32_t)(esum & 1);
     const uint32_t tf = (mu == 3 && x == n - 1) ? 1u : 0u;

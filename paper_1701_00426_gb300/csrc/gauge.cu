@@ -104,7 +104,7 @@ __device__ __forceinline__ void site_of(const LinkGeo &g, const int (&x)[4], int
     const int y0 = wrap(x[0] + d0, g.N[0]), y1 = wrap(x[1] + d1, g.N[1]);
     const int y2 = wrap(x[2] + d2, g.N[2]), y3 = wrap(x[3] + d3, g.N[3]);
     par = (y0 + y1 + y2 + y3) & 1;
-    idx = (y0 + g.N[0] * (y1 + g.N[1] * (y2 + g.N[2] * y3))) >> 1;
+    idx = bound_index((y0 + g.N[0] * (y1 + g.N[1] * (y2 + g.N[2] * y3))) >> 1, g.Vh);
 }
 
 template <class T>
@@ -1476,6 +1476,7 @@ int lqcd_mom_download(lqcd_ctx *c, double *H, size_t n)
 
 int lqcd_gauge_mom_update(lqcd_ctx *c, int prec, double beta, double eps)
 {
+    NvtxRange nvtx_("lqcd_gauge_mom_update");
     int st;
     if ((st = check_md(c, prec)) || (st = check_thin(c)) || (st = prepare(c, prec))) return st;
     launch_mom_update(c, prec, beta, eps);
@@ -1486,6 +1487,7 @@ int lqcd_gauge_mom_update(lqcd_ctx *c, int prec, double beta, double eps)
 
 int lqcd_gauge_link_update(lqcd_ctx *c, int prec, double eps)
 {
+    NvtxRange nvtx_("lqcd_gauge_link_update");
     int st;
     if ((st = check_md(c, prec)) || (st = check_thin(c)) || (st = prepare(c, prec))) return st;
     launch_link_update(c, prec, eps);
@@ -1496,6 +1498,7 @@ int lqcd_gauge_link_update(lqcd_ctx *c, int prec, double eps)
 
 int lqcd_gauge_md_steps(lqcd_ctx *c, int prec, double beta, double eps, int n_steps)
 {
+    NvtxRange nvtx_("lqcd_gauge_md_steps");
     int st;
     if ((st = check_md(c, prec)) || (st = check_thin(c)) || (st = prepare(c, prec))) return st;
     if (n_steps < 0) return fail(LQCD_EINVAL, "n_steps must be >= 0");
@@ -1511,6 +1514,7 @@ int lqcd_gauge_md_steps(lqcd_ctx *c, int prec, double beta, double eps, int n_st
 int lqcd_fermion_force_update(lqcd_ctx *c, double mass, double a0, const double *a, const double *shifts, int n_shift,
                               double tol, const double *phi, double eps, double *action, lqcd_solve_info *info)
 {
+    NvtxRange nvtx_("lqcd_fermion_force_update");
     int st;
     if ((st = check_md(c, LQCD_PREC_FP64))) return st;
     if (!phi || !a || !shifts) return fail(LQCD_EINVAL, "NULL argument");
@@ -1563,6 +1567,7 @@ int lqcd_fermion_force_update(lqcd_ctx *c, double mass, double a0, const double 
 
 int lqcd_stout_smear(lqcd_ctx *c, double rho, int n_levels)
 {
+    NvtxRange nvtx_("lqcd_stout_smear");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
     if (c->stout_n) return fail(LQCD_ESTATE, "links are already stout-smeared: call lqcd_stout_restore first");
@@ -1607,6 +1612,7 @@ int lqcd_stout_restore(lqcd_ctx *c)
 
 int lqcd_stout_force(lqcd_ctx *c, const double *F_smeared, double *F_thin, size_t n)
 {
+    NvtxRange nvtx_("lqcd_stout_force");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     if (!c->stout_n) return fail(LQCD_ESTATE, "links are not stout-smeared");
     const size_t want = 4 * c->V * 18;
@@ -1642,6 +1648,7 @@ int lqcd_stout_force(lqcd_ctx *c, const double *F_smeared, double *F_thin, size_
 
 int lqcd_gauge_action(lqcd_ctx *c, int prec, double beta, double *S)
 {
+    NvtxRange nvtx_("lqcd_gauge_action");
     if (!c || !S) return fail(LQCD_EINVAL, "NULL argument");
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
     if (prec != LQCD_PREC_FP64 && prec != LQCD_PREC_FP32 && prec != LQCD_PREC_FP64_NATIVE)

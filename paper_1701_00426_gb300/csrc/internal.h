@@ -9,12 +9,24 @@
 #include <vector>
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "../../include/lqcd.h"
 #include "common.cuh"
 #include "iteration.h"
 
 namespace lqcd {
+
+// NVTX range over a library call (header-only NVTX v3: a no-op unless a
+// profiler is attached), so that ncu --nvtx filters and timelines can name
+// the calls.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 
 // ------------------------------------------------------------------ errors
 void set_error(const std::string &msg);

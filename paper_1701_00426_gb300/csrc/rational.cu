@@ -119,6 +119,7 @@ extern "C" {
 int lqcd_rational_apply_dev(lqcd_ctx *c, double mass, double a0, const double *a, const double *shifts, int n_shift,
                             double tol, const void *b, void *y, double *action, lqcd_solve_info *info, void *stream)
 {
+    NvtxRange nvtx_("lqcd_rational_apply_dev");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     return rational_apply_dev(c, mass, a0, a, shifts, n_shift, tol, (const double2 *)b, (double2 *)y, action, info,
                               (cudaStream_t)stream);
@@ -127,6 +128,7 @@ int lqcd_rational_apply_dev(lqcd_ctx *c, double mass, double a0, const double *a
 int lqcd_rational_apply(lqcd_ctx *c, double mass, double a0, const double *a, const double *shifts, int n_shift,
                         double tol, const double *b, double *y, double *action, lqcd_solve_info *info)
 {
+    NvtxRange nvtx_("lqcd_rational_apply");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
     if (!b || !y) return fail(LQCD_EINVAL, "NULL argument");
     const size_t bytes = 3 * c->Vh * sizeof(double2);

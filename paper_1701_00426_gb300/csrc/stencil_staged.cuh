@@ -61,7 +61,7 @@ __host__ __device__ __forceinline__ size_t staged_df_elems(int ntiles)
 
 __device__ __forceinline__ const float4 *staged_tile_base(const float4 *links_st, int P, int ntiles, int tile)
 {
-    return links_st + (size_t)(P * ntiles + tile) * 8 * kDFStageElems;
+    return links_st + (size_t)(bound_index(P, 2) * ntiles + bound_index(tile, ntiles)) * 8 * kDFStageElems;
 }
 
 // barrier of the 256 consumer threads only (named barrier 1)

@@ -51,7 +51,7 @@ EXPORTED = [
     "lqcd_mom_upload", "lqcd_mom_download", "lqcd_gauge_mom_update", "lqcd_gauge_link_update",
     "lqcd_gauge_md_steps", "lqcd_gauge_action", "lqcd_mom_energy", "lqcd_fermion_force_update",
     "lqcd_stout_smear", "lqcd_stout_restore", "lqcd_stout_force", "lqcd_deo_apply_mrhs_layout",
-    "lqcd_selftest_stage_wait", "lqcd_inject_alloc_failure",
+    "lqcd_selftest_stage_wait", "lqcd_inject_alloc_failure", "lqcd_bounds_errors",
 ]
 
 
@@ -160,6 +160,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                                       vp, vp, vp]),
         "lqcd_selftest_stage_wait": (ctypes.c_int, [vp, ctypes.c_double]),
         "lqcd_inject_alloc_failure": (None, [ctypes.c_long]),
+        "lqcd_bounds_errors": (ctypes.c_int, [ctypes.POINTER(ctypes.c_uint)]),
         "lqcd_stout_smear": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
         "lqcd_stout_restore": (ctypes.c_int, [vp]),
         "lqcd_stout_force": (ctypes.c_int, [vp, vp, vp, ctypes.c_size_t]),
@@ -552,3 +553,11 @@ def inject_alloc_failure(k: int):
     """The k-th device allocation from now fails with LQCD_ENOMEM (k <= 0
     disarms); see lqcd_inject_alloc_failure."""
     load().lqcd_inject_alloc_failure(int(k))
+
+
+def bounds_errors() -> int:
+    """Error bits recorded by a bounds-checked library since the last call
+    (lqcd_bounds_errors); LqcdError(LQCD_ESTATE) for the default build."""
+    w = ctypes.c_uint()
+    check(load().lqcd_bounds_errors(ctypes.byref(w)))
+    return w.value
