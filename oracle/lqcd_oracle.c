@@ -22,7 +22,7 @@
  *     together using one matrix-vector product per iteration thanks to the
  *     shift invariance of the Krylov space.
  *
- * Readings where the paper is silent (each also listed in the design doc):
+ * Readings where the paper is silent:
  *   - D carries the factor 1/2:  (D psi)(n) = 1/2 sum_mu [ s_mu(n) U_mu(n)
  *     psi(n+mu) - s_mu(n-mu) U_mu(n-mu)^dag psi(n-mu) ].
  *   - Staggered phases eta_0 = 1, eta_mu = (-1)^(x_0+...+x_{mu-1}); time is
