@@ -200,7 +200,12 @@ double oracle_true_residual(const int N[4], const cplx *links, double mass,
 {
     const long n = volume(N) / 2 * 3;
     cplx *ax = malloc(sizeof(cplx) * n), *tmp = malloc(sizeof(cplx) * n);
+#if ORACLE_MUTANT == 21
+    /* planted: the shift is left out of the residual's operator */
+    oracle_apply_A(N, links, mass, 0.0, x, ax, tmp);
+#else
     oracle_apply_A(N, links, mass, sigma, x, ax, tmp);
+#endif
     double rr = 0;
     for (long i = 0; i < n; ++i) {
         cplx d = ax[i] - b[i];
@@ -209,7 +214,12 @@ double oracle_true_residual(const int N[4], const cplx *links, double mass,
     double bb = oracle_norm2(n, b);
     free(ax);
     free(tmp);
+#if ORACLE_MUTANT == 20
+    /* planted: divided by ||b||^2 instead of ||b|| */
+    return bb > 0 ? sqrt(rr) / bb : sqrt(rr);
+#else
     return bb > 0 ? sqrt(rr / bb) : sqrt(rr);
+#endif
 }
 
 /* ------------------------------------------------------------------------ */
@@ -795,8 +805,18 @@ static void stout_C(const int N[4], const cplx *links, const int x[4], int mu, d
         const int up[3] = {1, 1, -1}, dn[3] = {-1, 1, 1};
         path_product(N, links, x, 3, dir, up, P);
         for (int i = 0; i < 9; ++i) C[i] += rho * P[i];
+#if ORACLE_MUTANT == 22
+        /* planted: the lower staples are left out */
+        (void)dn;
+#else
         path_product(N, links, x, 3, dir, dn, P);
+#if ORACLE_MUTANT == 23
+        /* planted: the lower staples are added without the weight rho */
+        for (int i = 0; i < 9; ++i) C[i] += P[i];
+#else
         for (int i = 0; i < 9; ++i) C[i] += rho * P[i];
+#endif
+#endif
     }
 }
 

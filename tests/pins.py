@@ -212,6 +212,81 @@ def pin_hermitian_positive(orc, dims, mass=MASS) -> tuple[bool, str]:
     return ok, f"hermiticity {herm:.2e}, lowest eigenvalue {ev[0]:.3e}"
 
 
+def numpy_deo_matrix(dims, U, out_parity) -> np.ndarray:
+    """D_eo (out_parity 0) or D_oe (out_parity 1) as a dense (3 Vh, 3 Vh)
+    matrix, assembled here from Eq. (diracblock) without the oracle: rows are
+    the output sites of one parity and columns the input sites of the other,
+    both in rank order (Eq. lexicographic_eo), with the staggered sign
+    eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}) and -1 on the time links of the
+    last time slice."""
+    coords = list(sites(dims))
+    lex_of = {x: n for n, x in enumerate(coords)}
+    rank = {}
+    count = [0, 0]
+    for x in coords:
+        p = sum(x) % 2
+        rank[x] = count[p]
+        count[p] += 1
+    Vh = len(coords) // 2
+
+    def sign(x, mu):
+        s = -1.0 if sum(x[:mu]) % 2 else 1.0
+        if mu == 3 and x[3] == dims[3] - 1:
+            s = -s
+        return s
+
+    D = np.zeros((3 * Vh, 3 * Vh), np.complex128)
+    for x in coords:
+        if sum(x) % 2 != out_parity:
+            continue
+        i = rank[x]
+        for mu in range(4):
+            xf = list(x); xf[mu] = (xf[mu] + 1) % dims[mu]; xf = tuple(xf)
+            xb = list(x); xb[mu] = (xb[mu] - 1) % dims[mu]; xb = tuple(xb)
+            jf, jb = rank[xf], rank[xb]
+            D[3 * i:3 * i + 3, 3 * jf:3 * jf + 3] += 0.5 * sign(x, mu) * U[mu, lex_of[x]]
+            D[3 * i:3 * i + 3, 3 * jb:3 * jb + 3] -= 0.5 * sign(xb, mu) * U[mu, lex_of[xb]].conj().T
+    return D
+
+
+def numpy_A(dims, U, mass, sigma=0.0) -> np.ndarray:
+    """m^2 + sigma - D_eo D_oe (Eq. lineqeo) from numpy_deo_matrix."""
+    Deo, Doe = numpy_deo_matrix(dims, U, 0), numpy_deo_matrix(dims, U, 1)
+    return (mass * mass + sigma) * np.eye(Deo.shape[0]) - Deo @ Doe
+
+
+def pin_A_numpy_assembly(orc, dims, mass=MASS, sigma=0.37, seed=57) -> tuple[bool, str]:
+    """The oracle's matrix-free A + sigma, column by column, equals the
+    matrix assembled here from Eq. (diracblock) and Eq. (lineqeo)."""
+    U = inputs.random_links(dims, seed=seed)
+    ref = numpy_A(dims, U, mass, sigma)
+    got = dense_A(orc, dims, U, mass, sigma)
+    e = float(np.abs(got - ref).max() / np.abs(ref).max())
+    return e <= 1e-14, f"max |A_oracle - A_numpy| / max |A| = {e:.2e}"
+
+
+def pin_true_residual(orc, dims, mass=MASS, seed=58) -> tuple[bool, str]:
+    """oracle_true_residual = ||(A + sigma) x - b|| / ||b|| with A assembled in
+    numpy and x = the LAPACK solution perturbed by a relative 1e-3, so the
+    expected value is of order 1e-3, not zero; shifts 0, 0.37 and 25."""
+    U = inputs.random_links(dims, seed=seed)
+    Vh = int(np.prod(dims)) // 2
+    rng = np.random.default_rng(seed + 1)
+    b = (rng.standard_normal((Vh, 3)) + 1j * rng.standard_normal((Vh, 3))) * 3.0
+    worst, vals = 0.0, []
+    for sigma in (0.0, 0.37, 25.0):
+        A = numpy_A(dims, U, mass, sigma)
+        xs = np.linalg.solve(A, b.ravel())
+        noise = rng.standard_normal(xs.shape) + 1j * rng.standard_normal(xs.shape)
+        x = (xs + 1e-3 * np.linalg.norm(xs) / np.linalg.norm(noise) * noise).reshape(Vh, 3)
+        expect = np.linalg.norm(A @ x.ravel() - b.ravel()) / np.linalg.norm(b)
+        got = orc.true_residual(dims, U, mass, sigma, b, x)
+        vals.append(expect)
+        worst = max(worst, abs(got - expect) / expect)
+    ok = worst <= 1e-12 and min(vals) > 1e-5
+    return ok, f"max relative defect {worst:.2e} over residuals {['%.2e' % v for v in vals]}"
+
+
 # ---------------------------------------------------------------- solvers
 def pin_mscg_vs_lapack(orc, dims, shifts, mass=MASS, tol=1e-10) -> tuple[bool, str]:
     U = inputs.random_links(dims, seed=44)
@@ -496,6 +571,57 @@ def pin_stout_smooths(orc, dims=(4, 4, 4, 4), seed=98) -> tuple[bool, str]:
     return s[0] > s[1] > s[2], f"Wilson action at rho = 0, 0.01, 0.02: {s}"
 
 
+def pin_stout_single_link(orc, dims=(4, 4, 4, 4), rho=0.11, nu0=1, y=(1, 2, 0, 3), seed=101) -> tuple[bool, str]:
+    """One stout level of a field that is the identity on every link but one,
+    U_nu0(y) = W in SU(3), worked out by hand from the definition of C, Omega
+    and Q (each staple product is the identity unless it passes through W):
+      link (y, nu0):                   C = 6 rho 1 (six staples, none holds W);
+      links (y, mu), mu != nu0:        the upper staple in nu0 is W;
+      links (y - mu, mu):              the upper staple in nu0 ends in W^dag;
+      links (y + nu0, mu):             the lower staple in nu0 starts with W^dag;
+      links (y + nu0 - mu, mu):        the lower staple in nu0 ends in W;
+      links (y - mu, nu0):             the upper staple in mu has W in the middle;
+      links (y + mu, nu0):             the lower staple in mu has W in the middle;
+    then C = rho (S + 5 1) with S that staple, Omega = C U^dag, and every other
+    link has C = 6 rho 1, so Q = 0 and the link stays the identity: 19 links
+    move.
+    Expected U' = expm(iQ) U with scipy; compared link by link."""
+    import scipy.linalg
+    V = int(np.prod(dims))
+    coords = list(sites(dims))
+    lex_of = {x: n for n, x in enumerate(coords)}
+    W = inputs.random_links((2, 2, 2, 2), seed=seed)[0, 0]
+    U = inputs.unit_links(dims).copy()
+    U[nu0, lex_of[y]] = W
+
+    def step(x, mu, d):
+        z = list(x); z[mu] = (z[mu] + d) % dims[mu]; return tuple(z)
+
+    eye = np.eye(3)
+    C = np.empty((4, V, 3, 3), complex)
+    C[:] = 6.0 * rho * eye
+    C[nu0, lex_of[y]] = 6.0 * rho * eye
+    for mu in range(4):
+        if mu == nu0:
+            continue
+        for x, S in ((y, W), (step(y, mu, -1), W.conj().T), (step(y, nu0, 1), W.conj().T),
+                     (step(step(y, nu0, 1), mu, -1), W)):
+            C[mu, lex_of[x]] = rho * (S + 5.0 * eye)
+        for x in (step(y, mu, -1), step(y, mu, 1)):
+            C[nu0, lex_of[x]] = rho * (W + 5.0 * eye)
+    expect = np.empty_like(U)
+    for mu in range(4):
+        for n in range(V):
+            Om = C[mu, n] @ U[mu, n].conj().T
+            T = Om.conj().T - Om
+            Q = 0.5j * T - (1j / 6.0) * np.trace(T) * eye
+            expect[mu, n] = scipy.linalg.expm(1j * Q) @ U[mu, n]
+    got = orc.stout_smear(dims, U, rho, 1)
+    e = float(np.abs(got - expect).max())
+    moved = int(np.sum(np.abs(expect - U).reshape(4 * V, 9).max(axis=1) > 1e-12))
+    return e <= 1e-13 and moved == 19, f"max defect {e:.2e}, links moved {moved} (expected 19)"
+
+
 def plaq(dims, U, mu, nu):
     """P_{mu nu}(x) for every site by plain enumeration."""
     coords = list(sites(dims))
@@ -568,6 +694,10 @@ BATTERY = [
     ("gauge force = derivative of the action 4^4", pin_force_is_derivative),
     ("MD energy conservation O(dt^2) 4^4", pin_md_energy),
     ("fermion force = derivative of the rational action 4^4", pin_fermion_force_is_derivative),
+    ("A vs numpy assembly 4x4x2x6", lambda o: pin_A_numpy_assembly(o, (4, 4, 2, 6))),
+    ("true residual vs numpy A 2^4", lambda o: pin_true_residual(o, (2, 2, 2, 2))),
+    ("true residual vs numpy A 4^4", lambda o: pin_true_residual(o, (4, 4, 4, 4))),
+    ("stout: one non-trivial link by hand 4^4", pin_stout_single_link),
     ("stout: rho=0, SU(3), gauge covariance 4x4x4x6", pin_stout_basic),
     ("stout smearing lowers the Wilson action 4^4", pin_stout_smooths),
     ("stout force chain = derivative 4^4", pin_stout_force_is_derivative),

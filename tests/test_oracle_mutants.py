@@ -25,6 +25,10 @@ MUTANTS = {
     17: "fermion force without the staggered sign",
     18: "stout links move with exp(-iQ)",
     19: "stout force: C^dag L term with the wrong sign",
+    20: "true residual divided by ||b||^2",
+    21: "true residual without the shift",
+    22: "stout: lower staples left out",
+    23: "stout: lower staples without the weight rho",
 }
 
 

@@ -233,3 +233,22 @@ def test_stout_force_chain_is_derivative(orc, dims):
 def test_stout_fermion_force_is_derivative(orc):
     ok, msg = pins.pin_stout_fermion_force(orc)
     assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 2, 6), (2, 2, 2, 2)])
+def test_oracle_A_equals_numpy_assembly(orc, dims):
+    ok, msg = pins.pin_A_numpy_assembly(orc, dims)
+    assert ok, msg
+
+
+@pytest.mark.parametrize("dims", [(2, 2, 2, 2), (4, 4, 4, 4)])
+def test_true_residual_against_numpy_assembled_A(orc, dims):
+    """The checker behind every solve test: perturbed solutions, so the
+    residual is of order 1e-3, at shifts 0, 0.37 and 25."""
+    ok, msg = pins.pin_true_residual(orc, dims)
+    assert ok, msg
+
+
+def test_stout_single_nontrivial_link_by_hand(orc):
+    ok, msg = pins.pin_stout_single_link(orc)
+    assert ok, msg
