@@ -37,6 +37,11 @@
  *   - Every call returns an lqcd_status; nothing throws across this ABI.  On
  *     failure lqcd_last_error() describes the cause (thread-local string).
  *   - A context is not thread-safe: one thread at a time per context.
+ *   - A context lives on the device that was current at lqcd_create.  Every
+ *     call that takes a context makes that device current for the call and
+ *     restores the calling thread's current device before it returns, so a
+ *     context may be driven from any thread.  The contexts of one packed
+ *     solve must share a device.
  */
 #ifndef LQCD_H
 #define LQCD_H
@@ -205,12 +210,13 @@ int lqcd_deo_apply(lqcd_ctx *ctx, int out_parity, const void *in, void *out,
  * complex128 = 18.9 MB), which every device that loads the library holds
  * until the process exits.  in / out: host canonical spinors ([Vh][3]
  * complex128), as for lqcd_deo_apply.  Lattices with V/2 > 131072 sites are
- * rejected with LQCD_EINVAL.  The first call on a device looks up the
- * array's device address (with that device current); make that first call
- * before capturing work on any stream.  Every call uses the same array and
- * leaves its contents behind, so calls that overlap on the GPU (from
- * several threads, contexts or streams at once) race.  Synchronous, on the
- * context's stream. */
+ * rejected with LQCD_EINVAL.  The first call in a CUDA context of a device
+ * looks up the array's device address (with the context's device current)
+ * and keeps it with that CUDA context's identifier; after a device reset the
+ * next call looks it up again.  Make the first call before capturing work on
+ * any stream.  Every call uses the same array and leaves its contents
+ * behind, so calls that overlap on the GPU (from several threads, contexts
+ * or streams at once) race.  Synchronous, on the context's stream. */
 int lqcd_deo_apply_host_noalloc(lqcd_ctx *ctx, int out_parity, const double *in, double *out);
 
 /* Same operator in a chosen arithmetic on device spinors (asynchronous):

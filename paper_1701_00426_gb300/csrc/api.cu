@@ -174,6 +174,7 @@ int lqcd_create(const int dims[4], const lqcd_opts *opts, lqcd_ctx **out)
 void lqcd_destroy(lqcd_ctx *c)
 {
     if (!c) return;
+    DeviceGuard device_guard(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     c->graph.reset();
     DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->lnk_dfs, &c->err_word,
@@ -192,6 +193,7 @@ void lqcd_destroy(lqcd_ctx *c)
 int lqcd_set_opts(lqcd_ctx *c, const lqcd_opts *o)
 {
     if (!c || !o) return fail(LQCD_EINVAL, "NULL argument");
+    LQCD_ON_DEVICE(c->device);
     int st = validate_opts(o);
     if (st) return st;
     c->opts = *o;
@@ -204,6 +206,7 @@ int lqcd_links_upload(lqcd_ctx *c, const double *links, size_t n)
 {
     NvtxRange nvtx_("lqcd_links_upload");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     c->graph.reset();
     return upload_links(c, links, n);
 }
@@ -211,6 +214,7 @@ int lqcd_links_upload(lqcd_ctx *c, const double *links, size_t n)
 int lqcd_links_download(lqcd_ctx *c, double *links, size_t n)
 {
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     return download_links(c, links, n);
 }
 
@@ -218,6 +222,7 @@ int lqcd_deo_apply(lqcd_ctx *c, int out_parity, const void *in, void *out, int w
 {
     NvtxRange nvtx_("lqcd_deo_apply");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     if (where == 1) return deo_launch(c, out_parity, LQCD_PREC_FP64, 18, in, out, (cudaStream_t)stream ? (cudaStream_t)stream : c->stream);
     if (where != 0) return fail(LQCD_EINVAL, "where must be 0 (host) or 1 (device)");
     if (!in || !out) return fail(LQCD_EINVAL, "NULL spinor pointer");
@@ -242,6 +247,7 @@ int lqcd_deo_apply_ex(lqcd_ctx *c, int out_parity, int prec, int recon, const vo
 {
     NvtxRange nvtx_("lqcd_deo_apply_ex");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     return deo_launch(c, out_parity, prec, recon, in, out, stream ? (cudaStream_t)stream : c->stream);
 }
 
@@ -249,12 +255,14 @@ int lqcd_deo_apply_mrhs(lqcd_ctx *c, int out_parity, int n_rhs, int recon, const
 {
     NvtxRange nvtx_("lqcd_deo_apply_mrhs");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     return deo_mrhs_launch(c, out_parity, n_rhs, recon, in, out, stream ? (cudaStream_t)stream : c->stream);
 }
 
 int lqcd_selftest_stage_wait(lqcd_ctx *c, double limit_s)
 {
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     return stage_wait_selftest(c, limit_s);
 }
 
@@ -263,6 +271,7 @@ int lqcd_deo_apply_mrhs_layout(lqcd_ctx *c, int out_parity, int n_rhs, int recon
 {
     NvtxRange nvtx_("lqcd_deo_apply_mrhs_layout");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     return deo_mrhs_launch(c, out_parity, n_rhs, recon, in, out, stream ? (cudaStream_t)stream : c->stream, layout);
 }
 
@@ -272,6 +281,7 @@ int lqcd_mscg_solve(lqcd_ctx *c, double mass, const double *shifts, int n_shift,
     NvtxRange nvtx_("lqcd_mscg_solve");
     const auto t0 = std::chrono::steady_clock::now();
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     if (!b || !x || !shifts) return fail(LQCD_EINVAL, "NULL argument");
     if (n_shift < 1 || n_shift > LQCD_MAX_SHIFTS) return fail(LQCD_EINVAL, "n_shift must be in 1..32");
     const size_t n3 = 3 * c->Vh;
@@ -298,6 +308,7 @@ int lqcd_mscg_solve_dev(lqcd_ctx *c, double mass, const double *shifts, int n_sh
 {
     NvtxRange nvtx_("lqcd_mscg_solve_dev");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     return mscg_solve_dev(c, mass, shifts, n_shift, tol, (const double2 *)b, (double2 *)x, info, (cudaStream_t)stream);
 }
 
@@ -305,6 +316,7 @@ int lqcd_profile_iteration(lqcd_ctx *c, double mass, const double *shifts, int n
                            int iters, double ms_out[4], double *n_active_avg)
 {
     if (!c || !ms_out || !n_active_avg) return fail(LQCD_EINVAL, "NULL argument");
+    LQCD_ON_DEVICE(c->device);
     return profile_iteration(c, mass, shifts, n_shift, tol, (const double2 *)b, iters, ms_out, n_active_avg);
 }
 
@@ -313,6 +325,7 @@ int lqcd_cg_solve_mrhs(lqcd_ctx *c, double mass, double sigma, int n_rhs, double
 {
     NvtxRange nvtx_("lqcd_cg_solve_mrhs");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     return cg_solve_mrhs(c, mass, sigma, n_rhs, tol, b, x, info);
 }
 
@@ -323,6 +336,12 @@ int lqcd_mscg_solve_packed(lqcd_ctx *const *ctxs, int n, const double *mass, con
     NvtxRange nvtx_("lqcd_mscg_solve_packed");
     if (!ctxs || n < 1 || n > kMaxJobs || !mass || !shifts || !n_shift || !tol || !b || !x)
         return fail(LQCD_EINVAL, "bad packed-solve arguments");
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return fail(LQCD_EINVAL, "NULL context in a packed solve");
+        if (ctxs[i]->device != ctxs[0]->device)
+            return fail(LQCD_EINVAL, "the contexts of a packed solve must live on one device");
+    }
+    LQCD_ON_DEVICE(ctxs[0]->device);
     return mscg_solve_packed(ctxs, n, mass, shifts, n_shift, tol, b, x, info);
 }
 

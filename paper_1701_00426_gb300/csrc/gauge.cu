@@ -1324,6 +1324,7 @@ static int mom_to_prec(lqcd_ctx *c, int prec)
 static int check_md(lqcd_ctx *c, int prec)
 {
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
     if (!c->mom64.ptr) return fail(LQCD_ESTATE, "no momenta uploaded");
     if (prec != LQCD_PREC_FP64 && prec != LQCD_PREC_FP32 && prec != LQCD_PREC_FP64_NATIVE)
@@ -1421,6 +1422,7 @@ extern "C" {
 int lqcd_mom_upload(lqcd_ctx *c, const double *H, size_t n)
 {
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     const size_t want = 4 * c->V * 18;
     if (!H || n != want) return fail(LQCD_EINVAL, "momenta: expected 4*V*18 doubles");
     int st;
@@ -1454,6 +1456,7 @@ int lqcd_mom_upload(lqcd_ctx *c, const double *H, size_t n)
 int lqcd_mom_download(lqcd_ctx *c, double *H, size_t n)
 {
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     const size_t want = 4 * c->V * 18;
     if (!H || n != want) return fail(LQCD_EINVAL, "momenta: expected 4*V*18 doubles");
     if (!c->mom64.ptr) return fail(LQCD_ESTATE, "no momenta uploaded");
@@ -1477,6 +1480,8 @@ int lqcd_mom_download(lqcd_ctx *c, double *H, size_t n)
 int lqcd_gauge_mom_update(lqcd_ctx *c, int prec, double beta, double eps)
 {
     NvtxRange nvtx_("lqcd_gauge_mom_update");
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     int st;
     if ((st = check_md(c, prec)) || (st = check_thin(c)) || (st = prepare(c, prec))) return st;
     launch_mom_update(c, prec, beta, eps);
@@ -1488,6 +1493,8 @@ int lqcd_gauge_mom_update(lqcd_ctx *c, int prec, double beta, double eps)
 int lqcd_gauge_link_update(lqcd_ctx *c, int prec, double eps)
 {
     NvtxRange nvtx_("lqcd_gauge_link_update");
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     int st;
     if ((st = check_md(c, prec)) || (st = check_thin(c)) || (st = prepare(c, prec))) return st;
     launch_link_update(c, prec, eps);
@@ -1499,6 +1506,8 @@ int lqcd_gauge_link_update(lqcd_ctx *c, int prec, double eps)
 int lqcd_gauge_md_steps(lqcd_ctx *c, int prec, double beta, double eps, int n_steps)
 {
     NvtxRange nvtx_("lqcd_gauge_md_steps");
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     int st;
     if ((st = check_md(c, prec)) || (st = check_thin(c)) || (st = prepare(c, prec))) return st;
     if (n_steps < 0) return fail(LQCD_EINVAL, "n_steps must be >= 0");
@@ -1515,6 +1524,8 @@ int lqcd_fermion_force_update(lqcd_ctx *c, double mass, double a0, const double 
                               double tol, const double *phi, double eps, double *action, lqcd_solve_info *info)
 {
     NvtxRange nvtx_("lqcd_fermion_force_update");
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     int st;
     if ((st = check_md(c, LQCD_PREC_FP64))) return st;
     if (!phi || !a || !shifts) return fail(LQCD_EINVAL, "NULL argument");
@@ -1569,6 +1580,7 @@ int lqcd_stout_smear(lqcd_ctx *c, double rho, int n_levels)
 {
     NvtxRange nvtx_("lqcd_stout_smear");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
     if (c->stout_n) return fail(LQCD_ESTATE, "links are already stout-smeared: call lqcd_stout_restore first");
     if (!(rho >= 0.0) || !std::isfinite(rho)) return fail(LQCD_EINVAL, "rho must be finite and >= 0");
@@ -1598,6 +1610,7 @@ int lqcd_stout_smear(lqcd_ctx *c, double rho, int n_levels)
 int lqcd_stout_restore(lqcd_ctx *c)
 {
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     if (!c->stout_n) return LQCD_OK;
     const size_t nl = 72 * c->Vh;
     LQCD_CUDA(cudaMemcpyAsync(c->lnk_nat.ptr, c->stout_lv.ptr, nl * sizeof(double2), cudaMemcpyDeviceToDevice,
@@ -1614,6 +1627,7 @@ int lqcd_stout_force(lqcd_ctx *c, const double *F_smeared, double *F_thin, size_
 {
     NvtxRange nvtx_("lqcd_stout_force");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     if (!c->stout_n) return fail(LQCD_ESTATE, "links are not stout-smeared");
     const size_t want = 4 * c->V * 18;
     if (!F_smeared || !F_thin || n != want) return fail(LQCD_EINVAL, "forces: expected 4*V*18 doubles");
@@ -1650,6 +1664,7 @@ int lqcd_gauge_action(lqcd_ctx *c, int prec, double beta, double *S)
 {
     NvtxRange nvtx_("lqcd_gauge_action");
     if (!c || !S) return fail(LQCD_EINVAL, "NULL argument");
+    LQCD_ON_DEVICE(c->device);
     if (!c->links_ok) return fail(LQCD_ESTATE, "no links uploaded");
     if (prec != LQCD_PREC_FP64 && prec != LQCD_PREC_FP32 && prec != LQCD_PREC_FP64_NATIVE)
         return fail(LQCD_EINVAL, "precision must be FP64, FP64_NATIVE or FP32");
@@ -1676,6 +1691,8 @@ int lqcd_mom_energy(lqcd_ctx *c, int prec, double *K)
 {
     int st;
     if (!K) return fail(LQCD_EINVAL, "NULL argument");
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     if ((st = check_md(c, prec)) || (st = mom_to_prec(c, prec))) return st;
     const unsigned nb = nblocks(8L * (long)c->Vh, kGaugeThreads);
     if ((st = c->md_part.ensure(((size_t)nb + 1) * sizeof(double)))) return st;

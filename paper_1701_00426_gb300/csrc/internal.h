@@ -28,6 +28,43 @@ struct NvtxRange {
 };
 
 
+// Makes `dev` the calling thread's current device for the lifetime of the
+// guard and restores the previous one afterwards, so that a context created on
+// one device is driven on that device whichever device the calling thread has
+// current.  ok is false when the switch failed.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev)
+    {
+        int cur = -1;
+        if (cudaGetDevice(&cur) != cudaSuccess) {
+            cudaGetLastError();
+            cur = -1;
+        }
+        if (cur == dev) return;
+        if (cudaSetDevice(dev) != cudaSuccess) {
+            cudaGetLastError();
+            ok = false;
+            return;
+        }
+        prev = cur;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceGuard(const DeviceGuard &) = delete;
+    DeviceGuard &operator=(const DeviceGuard &) = delete;
+};
+
+// Every C entry point that receives a context (or a server) opens one of
+// these right after its NULL check.
+#define LQCD_ON_DEVICE(dev)                                                               \
+    ::lqcd::DeviceGuard lqcd_device_guard_(dev);                                          \
+    if (!lqcd_device_guard_.ok)                                                           \
+        return ::lqcd::fail(LQCD_ECUDA, "cannot make the context's device current")
+
 // ------------------------------------------------------------------ errors
 void set_error(const std::string &msg);
 int fail(int status, const std::string &msg);  // sets the message, returns status

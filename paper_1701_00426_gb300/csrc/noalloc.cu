@@ -12,9 +12,14 @@
 // Host code cannot use the array's name as a device address: on the host it
 // names a stand-in object, and a kernel handed it would fault or, where the
 // GPU can reach host memory, use the wrong memory.  The device address is
-// therefore looked up once per device with cudaGetSymbolAddress, with that
-// device current, on the first call made on that device.
+// therefore looked up with cudaGetSymbolAddress, with the context's device
+// current, on the first call made in a CUDA context of that device, and kept
+// with that context's identifier.  A device reset replaces the context (and
+// may move the array); the next call sees the new identifier and looks the
+// address up again.
 #include <mutex>
+
+#include <cuda.h>  // driver API types only; the two functions are resolved at run time
 
 #include "internal.h"
 
@@ -28,23 +33,63 @@ constexpr size_t kNoAllocRegion = 3 * (size_t)kNoAllocMaxVh;  // double2 element
 
 static __device__ __align__(256) double2 g_noalloc_stage[3 * kNoAllocRegion];
 
-static std::mutex g_noalloc_mu;
-static double2 *g_noalloc_ptr[64];  // device address per device ordinal (set up on first use)
+using PfnStreamGetCtx = CUresult (*)(CUstream, CUcontext *);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long *);
 
-// Device address of the staging array on the current device.
-static int noalloc_stage(double2 **out)
+// Identifier of the CUDA context that owns stream s; 0 when the driver does
+// not tell (then the address is looked up on every call).
+static unsigned long long stream_context_id(cudaStream_t s)
 {
-    int dev = 0;
-    LQCD_CUDA(cudaGetDevice(&dev));
+    static PfnStreamGetCtx get_ctx = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuStreamGetCtx", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_ctx = (PfnStreamGetCtx)p;
+        p = nullptr;
+        q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = (PfnCtxGetId)p;
+        cudaGetLastError();
+    });
+    if (!get_ctx || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (get_ctx((CUstream)s, &ctx) != CUDA_SUCCESS || !ctx) return 0;
+    if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+static std::mutex g_noalloc_mu;
+struct NoAllocAddr {
+    unsigned long long ctx_id = 0;
+    double2 *ptr = nullptr;
+};
+static NoAllocAddr g_noalloc_addr[64];  // per device ordinal, set up on first use in a context
+
+// Device address of the staging array for context c (its device is current).
+static int noalloc_stage(const lqcd_ctx *c, double2 **out)
+{
+    const int dev = c->device;
     if (dev < 0 || dev >= 64) return fail(LQCD_EINVAL, "device ordinal out of range");
+    const unsigned long long id = stream_context_id(c->stream);
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    NoAllocAddr &a = g_noalloc_addr[dev];
+    if (!a.ptr || id == 0 || a.ctx_id != id) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation staging array");
-        g_noalloc_ptr[dev] = (double2 *)p;
+        if (e != cudaSuccess) {
+            a = NoAllocAddr{};
+            return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation staging array");
+        }
+        a.ptr = (double2 *)p;
+        a.ctx_id = id;
     }
-    *out = g_noalloc_ptr[dev];
+    *out = a.ptr;
     return LQCD_OK;
 }
 
@@ -55,6 +100,7 @@ using namespace lqcd;
 extern "C" int lqcd_deo_apply_host_noalloc(lqcd_ctx *c, int out_parity, const double *in, double *out)
 {
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     if (!in || !out) return fail(LQCD_EINVAL, "NULL host buffer");
     if (out_parity != 0 && out_parity != 1) return fail(LQCD_EINVAL, "out_parity must be 0 or 1");
     if (int lr = links_ready(c)) return lr;
@@ -63,7 +109,7 @@ extern "C" int lqcd_deo_apply_host_noalloc(lqcd_ctx *c, int out_parity, const do
                                      std::to_string(c->Vh) + " exceeds its fixed staging of " +
                                      std::to_string(kNoAllocMaxVh) + " sites");
     double2 *stage = nullptr;
-    int st = noalloc_stage(&stage);
+    int st = noalloc_stage(c, &stage);
     if (st) return st;
     // Every element read below is written earlier in the same call, so the
     // contents left by a previous call need no clearing.

@@ -121,6 +121,7 @@ int lqcd_rational_apply_dev(lqcd_ctx *c, double mass, double a0, const double *a
 {
     NvtxRange nvtx_("lqcd_rational_apply_dev");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     return rational_apply_dev(c, mass, a0, a, shifts, n_shift, tol, (const double2 *)b, (double2 *)y, action, info,
                               (cudaStream_t)stream);
 }
@@ -130,6 +131,7 @@ int lqcd_rational_apply(lqcd_ctx *c, double mass, double a0, const double *a, co
 {
     NvtxRange nvtx_("lqcd_rational_apply");
     if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
     if (!b || !y) return fail(LQCD_EINVAL, "NULL argument");
     const size_t bytes = 3 * c->Vh * sizeof(double2);
     DevBuf db, dy;

@@ -356,6 +356,7 @@ int lqcd_serve_register_field(lqcd_server *s, const int dims[4], const double *l
                               int *field_id)
 {
     if (!s || !dims || !links || !field_id) return fail(LQCD_EINVAL, "NULL argument");
+    LQCD_ON_DEVICE(s->device);
     lqcd_ctx *c = nullptr;
     lqcd_opts o;
     {
@@ -512,6 +513,7 @@ int lqcd_serve_stats_get(lqcd_server *s, lqcd_serve_stats *o)
 void lqcd_serve_destroy(lqcd_server *s)
 {
     if (!s) return;
+    DeviceGuard device_guard(s->device);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         s->stop = true;

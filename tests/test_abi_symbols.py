@@ -173,3 +173,45 @@ int main() {
                        capture_output=True)
         r = subprocess.run([exe], capture_output=True, text=True)
         assert r.returncode == 0, r.stdout
+
+
+def _entry_bodies():
+    """(name, body) of every extern "C" definition under csrc/ whose first
+    parameter is a context or a server."""
+    csrc = os.path.join(ROOT, "paper_1701_00426_gb300", "csrc")
+    out = []
+    for f in sorted(os.listdir(csrc)):
+        if not f.endswith(".cu"):
+            continue
+        src = open(os.path.join(csrc, f)).read()
+        for m in re.finditer(r"^(?:extern \"C\" )?(?:int|void) (lqcd_[a-z_]+)\((lqcd_ctx|lqcd_server|lqcd_ctx \*const) \*", src, re.M):
+            start = src.index("{", m.end())
+            depth, i = 0, start
+            while True:
+                depth += {"{": 1, "}": -1}.get(src[i], 0)
+                i += 1
+                if depth == 0:
+                    break
+            out.append((m.group(1), src[start:i]))
+    return out
+
+
+# Server calls that only touch host state (queues, counters, copies of
+# finished results); their device work runs on the server's own thread, which
+# makes the server's device current when it starts.
+HOST_ONLY_SERVER_CALLS = {"lqcd_serve_submit", "lqcd_serve_set_opts", "lqcd_serve_poll",
+                          "lqcd_serve_drain", "lqcd_serve_stats_get"}
+
+
+def test_every_context_call_runs_on_the_context_device():
+    """Each C entry point that takes a context switches to the context's
+    device for the call (and back), so a thread whose current device differs
+    cannot launch on the wrong GPU."""
+    bodies = _entry_bodies()
+    names = {n for n, _ in bodies}
+    assert {"lqcd_deo_apply", "lqcd_mscg_solve", "lqcd_deo_apply_host_noalloc",
+            "lqcd_stout_force", "lqcd_rational_apply", "lqcd_serve_register_field"} <= names
+    for name, body in bodies:
+        if name in HOST_ONLY_SERVER_CALLS:
+            continue
+        assert "LQCD_ON_DEVICE(" in body or "DeviceGuard device_guard(" in body, name

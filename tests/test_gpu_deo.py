@@ -242,3 +242,32 @@ def test_injected_allocation_failure_leaves_context_usable(gpu, orc):
                 assert np.linalg.norm(y - ref) <= 1e-13 * np.linalg.norm(ref)
         finally:
             gpu.inject_alloc_failure(0)
+
+
+@pytest.mark.gpu
+def test_calls_from_a_thread_that_never_set_a_device(gpu, orc):
+    """Every call switches to the context's device itself: a context made on
+    the main thread is driven from a fresh thread whose current device was
+    never set, with the same results."""
+    import threading
+    dims = (4, 6, 8, 10)
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=5)
+    ref = orc.deo(dims, 0, U, x)
+    out = {}
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+
+        def work():
+            try:
+                out["deo"] = c.deo_apply(0, x)
+                out["noalloc"] = c.deo_apply_host_noalloc(0, x)
+            except Exception as exc:  # reported on the main thread
+                out["error"] = exc
+
+        t = threading.Thread(target=work)
+        t.start()
+        t.join()
+    assert "error" not in out, out.get("error")
+    for k in ("deo", "noalloc"):
+        assert np.linalg.norm(out[k] - ref) / np.linalg.norm(ref) <= 1e-13

@@ -45,6 +45,33 @@ def test_noalloc_matches_allocating_entry_point_twice(gpu, dims):
         assert _rel(again, c.deo_apply(0, x1)) <= TOL
 
 
+def test_noalloc_makes_no_device_allocation(gpu):
+    """With the library's allocation-failure injector armed for the very next
+    device allocation, the no-allocation call still succeeds (it reaches no
+    allocation), while the allocating host-buffer call fails with
+    LQCD_ENOMEM."""
+    lib = gpu.load()
+    dims = (4, 6, 8, 10)
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=3)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        ref = c.deo_apply(0, x)
+        st, _ = _call_noalloc(lib, c, 0, x)   # first call on this context: address set-up
+        assert st == gpu.LQCD_OK, lib.lqcd_last_error()
+        try:
+            lib.lqcd_inject_alloc_failure(1)
+            st, got = _call_noalloc(lib, c, 0, x)
+            assert st == gpu.LQCD_OK, lib.lqcd_last_error()
+            assert _rel(got, ref) <= TOL
+            a = np.ascontiguousarray(x)
+            out = np.empty_like(a)
+            st = lib.lqcd_deo_apply(c.h, 0, a.ctypes.data, out.ctypes.data, 0, None)
+            assert st == gpu.LQCD_ENOMEM   # the armed failure was still waiting
+        finally:
+            lib.lqcd_inject_alloc_failure(0)
+
+
 def test_noalloc_rejects_lattices_above_its_fixed_size(gpu):
     lib = gpu.load()
     dims = (24, 24, 24, 24)  # V/2 = 165888 > 131072
