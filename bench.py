@@ -677,7 +677,8 @@ def deo_sweep(lqcd, inputs, torch, flush, hbm_peak, sizes):
     shape), median and best of reps with L2 flushed before each (L2Flush);
     fractions of the measured copy bandwidth and of the 7.9 TB/s nominal."""
     out = {}
-    variants = [("fp64", 0, 18, torch.complex128, 1248.0), ("fp64_native_dfma", 3, 18, torch.complex128, 1248.0),
+    variants = [("fp64", 0, 18, torch.complex128, 1248.0), ("fp64_12r", 0, 12, torch.complex128, 864.0),
+                ("fp64_native_dfma", 3, 18, torch.complex128, 1248.0), ("fp32_18r", 1, 18, torch.complex64, 624.0),
                 ("fp32_12r", 1, 12, torch.complex64, 432.0), ("fp16_12r", 2, 12, torch.complex64, 240.0)]
     for L in sizes:
         dims = (L,) * 4

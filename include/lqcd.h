@@ -220,7 +220,11 @@ int lqcd_deo_apply(lqcd_ctx *ctx, int out_parity, const void *in, void *out,
 int lqcd_deo_apply_host_noalloc(lqcd_ctx *ctx, int out_parity, const double *in, double *out);
 
 /* Same operator in a chosen arithmetic on device spinors (asynchronous):
- *   prec LQCD_PREC_FP64, LQCD_PREC_FP64_NATIVE: complex128 spinors, recon 18;
+ *   prec LQCD_PREC_FP64: complex128 spinors, recon 18 or 12 (12: the first
+ *     two rows of each link are streamed, 96 of 144 bytes, and the third row
+ *     is rebuilt in double-float arithmetic, Sec. 2.3; within 1e-13 for
+ *     SU(3) links);
+ *   prec LQCD_PREC_FP64_NATIVE: complex128 spinors, recon 18;
  *   prec LQCD_PREC_FP32: complex64 spinors, recon 18 or 12;
  *   prec LQCD_PREC_FP16: complex64 spinors, FP16 links, recon 12. */
 int lqcd_deo_apply_ex(lqcd_ctx *ctx, int out_parity, int prec, int recon,

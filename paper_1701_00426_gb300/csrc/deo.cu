@@ -296,8 +296,10 @@ int soa_to_host(lqcd_ctx *c, const double2 *dev_soa, double *host, int nf, cudaS
 
 // ------------------------------------------------------------------ stand-alone D_eo
 // FP64 result from df64 arithmetic; IEEE complex128 spinors in and out.
-__global__ void __launch_bounds__(kTile, 2)
-    k_deo_df_ieee(Geom g, const float4 *__restrict__ L, const double2 *__restrict__ in, double2 *__restrict__ out, int P)
+// RECON 12 streams the first two rows of every link and rebuilds the third.
+template <int RECON>
+__device__ __forceinline__ void deo_df_ieee_site(const Geom &g, const float4 *__restrict__ L,
+                                                 const double2 *__restrict__ in, double2 *__restrict__ out, int P)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.Vh) return;
@@ -305,7 +307,7 @@ __global__ void __launch_bounds__(kTile, 2)
     make_stencil(g, i, P, S);
     float2 res[6];
     bool bad = false;
-    deo_site_df<SF_IEEE>(g, L, in, S, i, P, g.Vh, res, bad);
+    deo_site_df<SF_IEEE, RECON>(g, L, in, S, i, P, g.Vh, res, bad);
     double2 o[3];
     if (bad) {
         deo_site_native_from_df(g, L, in, S, i, P, g.Vh, o);
@@ -315,6 +317,19 @@ __global__ void __launch_bounds__(kTile, 2)
     }
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
+}
+
+__global__ void __launch_bounds__(kTile, 2)
+    k_deo_df_ieee(Geom g, const float4 *__restrict__ L, const double2 *__restrict__ in, double2 *__restrict__ out, int P)
+{
+    deo_df_ieee_site<18>(g, L, in, out, P);
+}
+
+__global__ void __launch_bounds__(kTile, 2)
+    k_deo_df12_ieee(Geom g, const float4 *__restrict__ L, const double2 *__restrict__ in, double2 *__restrict__ out,
+                    int P)
+{
+    deo_df_ieee_site<12>(g, L, in, out, P);
 }
 
 // Same operator with SPLIT threads per site (adjacent lanes): thread `part`
@@ -410,6 +425,7 @@ __global__ void __launch_bounds__(kTile)
 }
 
 // Stand-alone D_eo, consumers.
+template <int RECON>
 __device__ __forceinline__ void deo_staged_consume(const Geom &g, RingDF &R, const float4 *__restrict__ L,
                                                    const double2 *__restrict__ in, double2 *__restrict__ out, int P,
                                                    int ntiles, int *err)
@@ -424,7 +440,7 @@ __device__ __forceinline__ void deo_staged_consume(const Geom &g, RingDF &R, con
         make_stencil(g, live ? i : 0, P, S);
         float2 res[6];
         bool bad = false;
-        deo_site_df_staged<SF_IEEE>(R, q, dead, g, in, S, Vh, res, bad);
+        deo_site_df_staged<SF_IEEE, RECON>(R, q, dead, g, in, S, Vh, res, bad);
         if (!live) continue;
         double2 o[3];
         if (bad) {
@@ -443,6 +459,9 @@ __device__ __forceinline__ void deo_staged_consume(const Geom &g, RingDF &R, con
 // (stencil_staged.cuh): IEEE complex128 spinors in and out, double-float
 // arithmetic, the native FP64 fallback for inputs outside the df64 window.
 // Persistent: gridDim.x <= resident blocks; err bit 0/1 records a stall.
+// RECON 12 copies the first two rows of every hop's stage and rebuilds the
+// third row in the consumers.
+template <int RECON>
 __global__ void __launch_bounds__(kStagedThreads, kStagedMinBlocks)
     k_deo_df_ieee_staged(Geom g, const float4 *__restrict__ Lst, const float4 *__restrict__ L,
                          const double2 *__restrict__ in, double2 *__restrict__ out, int P, int ntiles, int *err)
@@ -453,7 +472,7 @@ __global__ void __launch_bounds__(kStagedThreads, kStagedMinBlocks)
     if (threadIdx.x >= kStagedConsumers) {
         if (threadIdx.x == kStagedConsumers) {
             int tile = blockIdx.x;
-            const bool ok = ring_produce(R, [&](const float4 *&base) -> bool {
+            const bool ok = ring_produce<RECON>(R, [&](const float4 *&base) -> bool {
                 if (tile >= ntiles) return false;
                 base = staged_tile_base(Lst, P, ntiles, tile);
                 tile += gridDim.x;
@@ -462,7 +481,7 @@ __global__ void __launch_bounds__(kStagedThreads, kStagedMinBlocks)
             if (!ok) atomicOr(err, 2);
         }
     } else {
-        deo_staged_consume(g, R, L, in, out, P, ntiles, err);
+        deo_staged_consume<RECON>(g, R, L, in, out, P, ntiles, err);
     }
     ring_finish(R);
 }
@@ -516,12 +535,17 @@ bool staged_deo_ready()
     if (!g_staged_done[dev]) {
         g_staged_done[dev] = true;
         int occ = 0, nsm = 0;
-        if (cudaFuncSetAttribute(k_deo_df_ieee_staged, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        int occ12 = 0;
+        if (cudaFuncSetAttribute(k_deo_df_ieee_staged<18>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kRingDFBytes) == cudaSuccess &&
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deo_df_ieee_staged, kStagedThreads,
+            cudaFuncSetAttribute(k_deo_df_ieee_staged<12>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kRingDFBytes) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_deo_df_ieee_staged<18>, kStagedThreads,
+                                                          kRingDFBytes) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ12, k_deo_df_ieee_staged<12>, kStagedThreads,
                                                           kRingDFBytes) == cudaSuccess &&
             cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess)
-            g_staged_blocks[dev] = occ * nsm;
+            g_staged_blocks[dev] = std::min(occ, occ12) * nsm;
         cudaGetLastError();  // a refusal above only disables the staged path
     }
     return g_staged_blocks[dev] > 0;
@@ -664,18 +688,34 @@ int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *ou
     int st = LQCD_OK;
     switch (prec) {
     case LQCD_PREC_FP64: {
-        if (recon != 18) return fail(LQCD_EINVAL, "FP64 D_eo uses 18-real links");
-        static const int cand[8] = {64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256,
-                                    3072 + kStagedThreads};
+        if (recon != 18 && recon != 12) return fail(LQCD_EINVAL, "recon must be 18 or 12");
         const float4 *L = c->lnk_df.as<float4>();
         const bool staged = staged_active(c);
         const int ntiles = (int)((c->Vh + kTile - 1) / kTile);
         const int sgrid = std::min(ntiles, staged_deo_blocks(c->device));
+        if (recon == 12) {
+            // 12-real links: the first two rows of the df64 arrays (96 of 144
+            // bytes per link) and the third row rebuilt, per thread or staged
+            static const int cand12[4] = {64, 128, 256, 3072 + kStagedThreads};
+            st = tuned_launch(c, 5, s, [&](int code) {
+                int kind = code >> 10, bs = code & 1023;
+                if (kind == 3 && (!staged || sgrid < 1)) kind = 0, bs = kTile;
+                if (kind == 3)
+                    k_deo_df_ieee_staged<12><<<(unsigned)sgrid, kStagedThreads, kRingDFBytes, s>>>(
+                        g, c->lnk_dfs.as<float4>(), L, (const double2 *)in, (double2 *)out, P, ntiles,
+                        c->err_word.as<int>());
+                else
+                    k_deo_df12_ieee<<<nb(bs), bs, 0, s>>>(g, L, (const double2 *)in, (double2 *)out, P);
+            }, staged ? 4 : 3, cand12);
+            break;
+        }
+        static const int cand[8] = {64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256,
+                                    3072 + kStagedThreads};
         st = tuned_launch(c, 0, s, [&](int code) {
             int kind = code >> 10, bs = code & 1023;
             if (kind == 3 && (!staged || sgrid < 1)) kind = 0, bs = kTile;  // staged stream not built
             if (kind == 3)
-                k_deo_df_ieee_staged<<<(unsigned)sgrid, kStagedThreads, kRingDFBytes, s>>>(
+                k_deo_df_ieee_staged<18><<<(unsigned)sgrid, kStagedThreads, kRingDFBytes, s>>>(
                     g, c->lnk_dfs.as<float4>(), L, (const double2 *)in, (double2 *)out, P, ntiles,
                     c->err_word.as<int>());
             else if (kind == 0)

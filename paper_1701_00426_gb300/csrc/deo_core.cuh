@@ -84,17 +84,73 @@ __device__ __forceinline__ void load_spinor_df(const void *in, int idx, int Vh, 
     }
 }
 
+// a0 b0 + a1 b1 + a2 b2 + a3 b3 for df64 factors (hi, lo), returned as a
+// normalised df64 pair.  The products of the high parts are split exactly
+// (two_prod) and their rounded values summed with two_sum; the product
+// errors, the sum errors and the mixed high-low products (relative 2^-24 of
+// a product) are added together in FP32 and once to the sum at the end.
+// Low-low products (relative 2^-48) are dropped.
+__device__ __forceinline__ float2 df_dot4(float2 a0, float2 b0, float2 a1, float2 b1, float2 a2, float2 b2,
+                                          float2 a3, float2 b3)
+{
+    float p0, e0, p1, e1, p2, e2, p3, e3;
+    two_prod(a0.x, b0.x, p0, e0);
+    two_prod(a1.x, b1.x, p1, e1);
+    two_prod(a2.x, b2.x, p2, e2);
+    two_prod(a3.x, b3.x, p3, e3);
+    e0 = __fmaf_rn(a0.x, b0.y, __fmaf_rn(a0.y, b0.x, e0));
+    e1 = __fmaf_rn(a1.x, b1.y, __fmaf_rn(a1.y, b1.x, e1));
+    e2 = __fmaf_rn(a2.x, b2.y, __fmaf_rn(a2.y, b2.x, e2));
+    e3 = __fmaf_rn(a3.x, b3.y, __fmaf_rn(a3.y, b3.x, e3));
+    float s, t0, t1, t2;
+    two_sum(p0, p1, s, t0);
+    two_sum(s, p2, s, t1);
+    two_sum(s, p3, s, t2);
+    const float err = __fadd_rn(__fadd_rn(__fadd_rn(t0, t1), t2), __fadd_rn(__fadd_rn(e0, e1), __fadd_rn(e2, e3)));
+    float h, l;
+    two_sum(s, err, h, l);
+    return make_float2(h, l);
+}
+
+// Third row of an SU(3) link from its first two (Sec. 2.3, 12 reals per
+// link): r2 = conj(r0 x r1), component k = conj(a_i b_j - a_j b_i) with
+// (i, j) = (k+1, k+2) mod 3, a = r0, b = r1, in df64 (components are
+// (re_h, re_l, im_h, im_l)).  Exact for an SU(3) matrix up to the df64
+// rounding of each component (a few 2^-48 of the largest entry).
+__device__ __forceinline__ void reconstruct_row2_df(float4 (&U)[9])
+{
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int i = (k + 1) % 3, j = (k + 2) % 3;
+        const float4 a_i = U[i], a_j = U[j], b_i = U[3 + i], b_j = U[3 + j];
+        const float2 air = make_float2(a_i.x, a_i.y), aii = make_float2(a_i.z, a_i.w);
+        const float2 ajr = make_float2(a_j.x, a_j.y), aji = make_float2(a_j.z, a_j.w);
+        const float2 bir = make_float2(b_i.x, b_i.y), bii = make_float2(b_i.z, b_i.w);
+        const float2 bjr = make_float2(b_j.x, b_j.y), bji = make_float2(b_j.z, b_j.w);
+        // re(a_i b_j - a_j b_i) = air bjr - aii bji - ajr bir + aji bii
+        const float2 re = df_dot4(air, bjr, df_neg(aii), bji, df_neg(ajr), bir, aji, bii);
+        // im(a_i b_j - a_j b_i) = air bji + aii bjr - ajr bii - aji bir
+        const float2 im = df_dot4(air, bji, aii, bjr, df_neg(ajr), bii, df_neg(aji), bir);
+        U[6 + k] = make_float4(re.x, re.y, -im.x, -im.y);
+    }
+}
+
+// RECON 18: all nine components streamed; RECON 12: the first two rows
+// (components 0..5 of the same arrays, 96 of the 144 bytes) streamed and
+// the third row rebuilt.
+template <int RECON = 18>
 __device__ __forceinline__ void load_link_df(const float4 *L, int mu, int par, int idx, int Vh, float4 (&U)[9])
 {
     const float4 *p = L + link_base(mu, par, 9, Vh) + idx;
     const uint64_t pol = l2_evict_first_policy();
 #pragma unroll
-    for (int c = 0; c < 9; ++c) U[c] = ldg4_stream(p + (size_t)c * Vh, pol);
+    for (int c = 0; c < (RECON == 12 ? 6 : 9); ++c) U[c] = ldg4_stream(p + (size_t)c * Vh, pol);
+    if (RECON == 12) reconstruct_row2_df(U);
 }
 
 // D applied at one site in df64.  Returns the six (re, im) x colour results
 // as normalised df64 pairs, already multiplied by 1/2.
-template <int SF>
+template <int SF, int RECON = 18>
 __device__ __forceinline__ void deo_site_df(const Geom &g, const float4 *L, const void *in, const Stencil &S, int i,
                                             int P, int Vh, float2 (&res)[6], bool &bad)
 {
@@ -108,10 +164,10 @@ __device__ __forceinline__ void deo_site_df(const Geom &g, const float4 *L, cons
         hop(g, S, mu, f, b, nf, nb);
         float4 U[9], v[3];
         float ch[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        load_link_df(L, mu, P, i, Vh, U);
+        load_link_df<RECON>(L, mu, P, i, Vh, U);
         load_spinor_df<SF>(in, f, Vh, nf, v, bad);
         hop_fwd_df(acc, ch, U, v);
-        load_link_df(L, mu, 1 - P, b, Vh, U);
+        load_link_df<RECON>(L, mu, 1 - P, b, Vh, U);
         load_spinor_df<SF>(in, b, Vh, nb, v, bad);
         hop_bwd_df(acc, ch, U, v);
 #pragma unroll

@@ -99,10 +99,19 @@ __device__ __forceinline__ void ring_finish(RingDF &R)
         }
 }
 
+// Bytes of one hop's stage: all nine link components (RECON 18), or the
+// first two rows, components 0..5, which lead each hop block of the stream
+// (RECON 12: 24 KB, the third row is rebuilt by the consumers).
+template <int RECON>
+__host__ __device__ constexpr uint32_t staged_stage_bytes()
+{
+    return (RECON == 12 ? 6u : 9u) * (uint32_t)kTile * (uint32_t)sizeof(float4);
+}
+
 // Producer (one lane).  next(base) yields the tile bases of this block in
 // the order the consumers walk them, and false at the end.  Returns false if
 // a wait for a free stage ran out.
-template <class Next>
+template <int RECON = 18, class Next>
 __device__ __forceinline__ bool ring_produce(RingDF &R, Next next)
 {
     const uint64_t pol = bulk_evict_first_policy();
@@ -117,8 +126,8 @@ __device__ __forceinline__ bool ring_produce(RingDF &R, Next next)
                 ok = false;
                 break;
             }
-            mbar_arrive_expect_tx(&R.full[s], kDFStageBytes);
-            bulk_g2s(&R.U[s][0][0], base + (size_t)h * kDFStageElems, kDFStageBytes, &R.full[s], pol);
+            mbar_arrive_expect_tx(&R.full[s], staged_stage_bytes<RECON>());
+            bulk_g2s(&R.U[s][0][0], base + (size_t)h * kDFStageElems, staged_stage_bytes<RECON>(), &R.full[s], pol);
         }
     }
     // every copy issued must have landed before the block may exit
@@ -156,7 +165,7 @@ __device__ __forceinline__ void ring_release(RingDF &R, int s)
 // deo_site_df.  q is the block's running stage counter (8 stages per tile).
 // Every consumer thread calls this once per tile (i is any valid site for
 // threads beyond V/2; their result is discarded).
-template <int SF>
+template <int SF, int RECON = 18>
 __device__ __forceinline__ void deo_site_df_staged(RingDF &R, uint32_t &q, bool &dead, const Geom &g, const void *in,
                                                    const Stencil &S, int Vh, float2 (&res)[6], bool &bad)
 {
@@ -180,7 +189,8 @@ __device__ __forceinline__ void deo_site_df_staged(RingDF &R, uint32_t &q, bool 
         load_spinor_df<SF>(in, b, Vh, nb, vb, bad);
         int s = ring_acquire(R, q++, dead);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) U[c] = R.U[s][c][t];
+        for (int c = 0; c < (RECON == 12 ? 6 : 9); ++c) U[c] = R.U[s][c][t];
+        if (RECON == 12) reconstruct_row2_df(U);
         hop_fwd_df(acc, ch, U, vf);
         ring_release(R, s);
         if (mu < 3) {
@@ -189,7 +199,8 @@ __device__ __forceinline__ void deo_site_df_staged(RingDF &R, uint32_t &q, bool 
         }
         s = ring_acquire(R, q++, dead);
 #pragma unroll
-        for (int c = 0; c < 9; ++c) U[c] = R.U[s][c][t];
+        for (int c = 0; c < (RECON == 12 ? 6 : 9); ++c) U[c] = R.U[s][c][t];
+        if (RECON == 12) reconstruct_row2_df(U);
         hop_bwd_df(acc, ch, U, vb);
         ring_release(R, s);
 #pragma unroll

@@ -217,6 +217,93 @@ def test_every_tuned_fp64_variant_matches_oracle(gpu, tmp_path, code):
         assert n <= FP64_TOL and m <= FP64_TOL, f"variant {code} case {k}: {n:.2e} {m:.2e}"
 
 
+def deo12(gpu, c, parity, x):
+    """FP64 D_eo with 12-real links (first two rows streamed, third rebuilt)."""
+    xin = gpu.to_device_spinor(x)
+    out = torch.empty_like(xin)
+    c.deo_apply_ex(parity, gpu.PREC_FP64, 12, xin, out)
+    torch.cuda.synchronize()
+    return gpu.from_device_spinor(out)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+def test_deo_fp64_12real_matches_oracle(gpu, orc, dims):
+    """Sec. 2.3 third-row reconstruction in double-float arithmetic: the same
+    1e-13 bar as the 18-real operator (the links are SU(3) to rounding)."""
+    U = inputs.random_links(dims)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        for parity in (0, 1):
+            x = inputs.gaussian_field(dims, k=20 + parity)
+            check_fp64(deo12(gpu, c, parity, x), orc.deo(dims, parity, U, x))
+
+
+@pytest.mark.parametrize("scale", [1e-80, 1e90])
+def test_deo_fp64_12real_extreme_magnitudes(gpu, orc, scale):
+    dims = (4, 4, 4, 6)
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=9) * scale
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        check_fp64(deo12(gpu, c, 0, x), orc.deo(dims, 0, U, x))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("dims", [(32, 32, 32, 32), (24, 24, 24, 24)])
+def test_deo_fp64_12real_full_size_matches_oracle(gpu, orc, dims):
+    U = inputs.random_links(dims)
+    x = inputs.gaussian_field(dims, k=0)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        got = deo12(gpu, c, 1, x)
+    check_fp64(got, orc.deo(dims, 1, U, x))
+
+
+FORCE12_SCRIPT = r'''
+import sys, json, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1701_00426_gb300 import inputs, lqcd
+from oracle import oracle
+orc = oracle()
+out = {}
+for dims in [(4, 6, 8, 10), (8, 8, 8, 8), (2, 2, 2, 2)]:
+    U = inputs.random_links(dims)
+    with lqcd.Context(dims) as c:
+        c.links_upload(U)
+        for parity in (0, 1):
+            x = inputs.gaussian_field(dims, k=3 + parity)
+            ref = orc.deo(dims, parity, U, x)
+            xin = lqcd.to_device_spinor(x)
+            o = torch.empty_like(xin)
+            c.deo_apply_ex(parity, lqcd.PREC_FP64, 12, xin, o)
+            torch.cuda.synchronize()
+            d = np.abs(lqcd.from_device_spinor(o) - ref)
+            out[f"{dims}{parity}"] = [float(np.linalg.norm(d) / np.linalg.norm(ref)), float(d.max() / np.abs(ref).max())]
+print(json.dumps(out))
+'''
+
+
+@pytest.mark.parametrize("code", [64, 128, 256, 3072 + 288])
+def test_every_tuned_fp64_12real_variant_matches_oracle(gpu, tmp_path, code):
+    """Per-thread blocks of 64/128/256 and the staged kernel, forced."""
+    import json
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cache = tmp_path / "tune.txt"
+    lines = [f"deo2 v5 {d[0]}x{d[1]}x{d[2]}x{d[3]} {code}" for d in [(4, 6, 8, 10), (8, 8, 8, 8), (2, 2, 2, 2)]]
+    cache.write_text("\n".join(lines) + "\n")
+    script = tmp_path / "force12.py"
+    script.write_text(FORCE12_SCRIPT)
+    env = dict(os.environ, LQCD_TUNE_CACHE=str(cache))
+    r = subprocess.run([sys.executable, str(script), root], env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    for k, (n, m) in res.items():
+        assert n <= FP64_TOL and m <= FP64_TOL, f"variant {code} case {k}: {n:.2e} {m:.2e}"
+
+
 def test_injected_allocation_failure_leaves_context_usable(gpu, orc):
     """Host-side fault injection: a device allocation made to fail inside
     lqcd_links_upload returns LQCD_ENOMEM and leaves the context without
