@@ -506,6 +506,64 @@ int lqcd_stout_restore(lqcd_ctx *ctx);
  * (i/2)(U G - G^dag U^dag).  LQCD_ESTATE when not smeared.  Synchronous. */
 int lqcd_stout_force(lqcd_ctx *ctx, const double *F_smeared, double *F_thin, size_t n_doubles);
 
+/* ------------------------------------------------- domain decomposition
+ * The lattice split into slabs of time slices over ranks, one context per
+ * rank (the distribution over several GPUs that Sec. 6 names as the next
+ * step).  Rank r of `world` owns global time slices [t0, t0 + nt), nt =
+ * N3 / world (even, >= 2), t0 = r nt.  Its context holds an extended slab of
+ * nt + 4 slices (two ghost slices on each side); a rank's field is a device
+ * spinor of that slab ([3][Vh_ext] complex128, Vh_ext = N0 N1 N2 (nt + 4) / 2)
+ * whose owned sites are the half-index range [lo, hi) = [2 h, (2 + nt) h),
+ * h = N0 N1 N2 / 2, in the global half-index order of those slices.  The
+ * hops of the owned sites read one ghost slice on each side, [lo - h, lo)
+ * and [hi, hi + h): the top owned slice of rank r - 1 and the bottom owned
+ * slice of rank r + 1 (periodic in the rank). */
+
+/* Shard context of rank `rank` of `world` for the global N0 x N1 x N2 x N3
+ * lattice, on the current device.  LQCD_EINVAL unless N3 / world is even and
+ * >= 2.  A shard context is an ordinary context of its extended slab for
+ * every other call (which then treats the slab as a periodic lattice of its
+ * own); the calls below are the sharded operations. */
+int lqcd_shard_create(const int dims[4], int world, int rank, const lqcd_opts *opts, lqcd_ctx **ctx);
+
+/* info[0..5] = t0, nt, Vh_ext, h, lo, hi (see above).  LQCD_EINVAL for a
+ * context that is not a shard. */
+int lqcd_shard_geometry(const lqcd_ctx *ctx, long info[6]);
+
+/* Upload the links of the rank's extended slab from the GLOBAL canonical
+ * field (4*V*18 doubles, V the global volume; copied, periodic in time);
+ * the time links of global slice N3 - 1 carry the antiperiodic sign.
+ * Synchronous. */
+int lqcd_shard_links_upload(lqcd_ctx *ctx, const double *links, size_t n_doubles);
+
+/* out = D_eo in (out_parity 0) or D_oe in (out_parity 1) at the rank's owned
+ * sites, in FP64 (double-float arithmetic, as lqcd_deo_apply), from a device
+ * spinor `in` of the extended slab whose ghost slices hold the neighbours'
+ * faces (lqcd_shard_exchange, or the caller's own transport).  Only the
+ * owned sites of `out` are written.  Asynchronous on `stream` (NULL = the
+ * context's stream). */
+int lqcd_shard_deo_apply(lqcd_ctx *ctx, int out_parity, const void *in, void *out, void *stream);
+
+/* Fill the ghost slices of every rank's field when all `world` ranks live in
+ * this process: ctxs[r] is rank r (n == world), fields[r] its device spinor
+ * of the extended slab.  Each face is one 2-D device copy (three colour rows)
+ * into the receiving rank's own memory, ordered after all work queued so far
+ * on every rank's stream and before any work queued after the call.
+ * Contexts on different devices are allowed (peer copies). */
+int lqcd_shard_exchange(lqcd_ctx *const *ctxs, int n, void *const *fields);
+
+/* CG for (A + sigma) x = b, A = m^2 - D_eo D_oe (Eq. lineqeo), with the
+ * sharded operator over the n = world ranks ctxs[0..n-1] of this process:
+ * two face exchanges per iteration, and the FP64 reductions summed per rank
+ * in a fixed block order, then over ranks in rank order, so that every rank
+ * uses the same scalars.  b, x: GLOBAL host canonical even spinors ([Vh][3]
+ * complex128); each rank reads and writes its owned slices.  Iterates to
+ * tol / 2 and accepts an FP64 true residual <= tol (recomputed with the
+ * sharded operator; up to three restarts).  info (may be NULL): iterations
+ * and true_resid[0].  Synchronous.  LQCD_ENOCONV at opts.max_iter. */
+int lqcd_shard_cg_solve(lqcd_ctx *const *ctxs, int n, double mass, double sigma, double tol, const double *b,
+                        double *x, lqcd_solve_info *info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,7 @@ CHECKED_BUILD = os.path.join(HERE, "_build_checked")
 CHECKED_LIB = os.path.join(HERE, "liblqcd_checked.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-UNITS = ["api.cu", "deo.cu", "solver.cu", "mrhs.cu", "serve.cu", "noalloc.cu", "rational.cu", "gauge.cu"]
+UNITS = ["api.cu", "deo.cu", "solver.cu", "mrhs.cu", "serve.cu", "noalloc.cu", "rational.cu", "gauge.cu", "shard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", INCLUDE, "-I", CSRC]

@@ -75,7 +75,7 @@ size_t ctx_device_bytes(const lqcd_ctx *c)
                          &c->err_word, &c->io_a, &c->io_b, &c->rat_x, &c->rat_part, &c->mom64,
                          &c->mom32, &c->md_part, &c->ff_y, &c->stout_lv, &c->stout_M, &c->stout_G,
                          &c->stout_F, &c->host_b, &c->host_x, &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state,
-                         &c->ws.stage};
+                         &c->ws.stage, &c->shard_ws};
     size_t s = 0;
     for (const DevBuf *p : b) s += p->bytes;
     s += c->ws32.bytes();
@@ -180,7 +180,8 @@ void lqcd_destroy(lqcd_ctx *c)
     DevBuf *b[] = {&c->lnk_df, &c->lnk_nat, &c->lnk_f18, &c->lnk_f12, &c->lnk_h12, &c->lnk_dfs, &c->err_word,
                    &c->io_a, &c->io_b, &c->rat_x, &c->rat_part, &c->mom64, &c->mom32, &c->md_part, &c->ff_y,
                    &c->stout_lv, &c->stout_M, &c->stout_G, &c->stout_F, &c->host_b, &c->host_x,
-                   &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage};
+                   &c->ws.vec, &c->ws.ieee, &c->ws.part, &c->ws.tickets, &c->ws.state, &c->ws.stage,
+                   &c->shard_ws};
     for (DevBuf *p : b) p->release();
     c->ws32.release();
     for (Workspace &w : c->ref_ws) w.release();

@@ -171,6 +171,10 @@ struct lqcd_ctx {
     int *h_pinned = nullptr;  // pinned host words for halt/iteration polling
     double *h_pinned_d = nullptr;
     uint64_t launches = 0;    // library kernels launched on behalf of this context
+    // t-slab shard of a global lattice (shard.cu); shard_world = 0: not a shard
+    int shard_world = 0, shard_rank = 0, shard_t0 = 0, shard_nt = 0;
+    int gdims[4] = {0, 0, 0, 0};  // global lattice of a shard (dims is its extended slab)
+    lqcd::DevBuf shard_ws;        // sharded CG vectors and partial sums
 };
 
 namespace lqcd {

@@ -52,6 +52,8 @@ EXPORTED = [
     "lqcd_gauge_md_steps", "lqcd_gauge_action", "lqcd_mom_energy", "lqcd_fermion_force_update",
     "lqcd_stout_smear", "lqcd_stout_restore", "lqcd_stout_force", "lqcd_deo_apply_mrhs_layout",
     "lqcd_selftest_stage_wait", "lqcd_inject_alloc_failure", "lqcd_bounds_errors",
+    "lqcd_shard_create", "lqcd_shard_geometry", "lqcd_shard_links_upload", "lqcd_shard_deo_apply",
+    "lqcd_shard_exchange", "lqcd_shard_cg_solve",
 ]
 
 
@@ -164,6 +166,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_stout_smear": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
         "lqcd_stout_restore": (ctypes.c_int, [vp]),
         "lqcd_stout_force": (ctypes.c_int, [vp, vp, vp, ctypes.c_size_t]),
+        "lqcd_shard_create": (ctypes.c_int, [ip, ctypes.c_int, ctypes.c_int, ctypes.POINTER(lqcd_opts),
+                                             ctypes.POINTER(vp)]),
+        "lqcd_shard_geometry": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_long)]),
+        "lqcd_shard_links_upload": (ctypes.c_int, [vp, vp, sz]),
+        "lqcd_shard_deo_apply": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp]),
+        "lqcd_shard_exchange": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(vp)]),
+        "lqcd_shard_cg_solve": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                               ctypes.c_double, vp, vp, ctypes.POINTER(lqcd_solve_info)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -474,6 +484,87 @@ def mscg_solve_packed(ctxs, masses, shifts_list, tols, bs):
     infos = (lqcd_solve_info * n)()
     check(lib.lqcd_mscg_solve_packed(hs, n, ms, shp, ns, ts, bp, xp, infos))
     return x_arr, [i.as_dict() for i in infos]
+
+
+class ShardWorld:
+    """All ranks of a t-slab decomposition of one lattice in this process,
+    one shard context per rank (wraps lqcd_shard_*)."""
+
+    def __init__(self, dims, world: int, opts: lqcd_opts | None = None, **kw):
+        self.lib = load()
+        self.dims = tuple(int(d) for d in dims)
+        self.world = int(world)
+        self.Vh = int(np.prod(self.dims)) // 2
+        o = opts if opts is not None else default_opts(**kw)
+        self.h = []
+        for r in range(self.world):
+            h = ctypes.c_void_p()
+            st = self.lib.lqcd_shard_create((ctypes.c_int * 4)(*self.dims), self.world, r, ctypes.byref(o),
+                                            ctypes.byref(h))
+            if st != LQCD_OK:
+                self.close()
+                check(st)
+            self.h.append(h)
+        info = (ctypes.c_long * 6)()
+        check(self.lib.lqcd_shard_geometry(self.h[0], info))
+        self.t0_step, self.nt, self.vh_ext, self.face, self.lo, self.hi = (int(v) for v in info)
+
+    def close(self):
+        for h in getattr(self, "h", []):
+            if h:
+                self.lib.lqcd_destroy(h)
+        self.h = []
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def links_upload(self, links: np.ndarray):
+        a = _c128(links, (4, self.Vh * 2, 3, 3))
+        for h in self.h:
+            check(self.lib.lqcd_shard_links_upload(h, _ptr(a), a.size * 2))
+
+    def scatter(self, field: np.ndarray, device="cuda"):
+        """Global canonical half field [Vh, 3] -> per-rank device spinors of
+        the extended slabs (owned slices filled, ghost slices zero)."""
+        import torch
+        out = []
+        for r in range(self.world):
+            ext = np.zeros((self.vh_ext, 3), np.complex128)
+            ext[self.lo:self.hi] = field[r * (self.hi - self.lo):(r + 1) * (self.hi - self.lo)]
+            out.append(to_device_spinor(ext, device=device))
+        torch.cuda.synchronize()
+        return out
+
+    def gather(self, fields) -> np.ndarray:
+        """Owned slices of the per-rank device spinors -> global [Vh, 3]."""
+        return np.concatenate([from_device_spinor(f)[self.lo:self.hi] for f in fields])
+
+    def exchange(self, fields):
+        hs = (ctypes.c_void_p * self.world)(*self.h)
+        fp = (ctypes.c_void_p * self.world)(*[_dptr(f) for f in fields])
+        check(self.lib.lqcd_shard_exchange(hs, self.world, fp))
+
+    def deo_apply(self, out_parity: int, fields_in, fields_out):
+        for h, a, b in zip(self.h, fields_in, fields_out):
+            check(self.lib.lqcd_shard_deo_apply(h, int(out_parity), _dptr(a), _dptr(b), None))
+
+    def cg_solve(self, mass: float, sigma: float, tol: float, b: np.ndarray):
+        bb = _c128(b, (self.Vh, 3))
+        x = np.zeros_like(bb)
+        info = lqcd_solve_info()
+        hs = (ctypes.c_void_p * self.world)(*self.h)
+        check(self.lib.lqcd_shard_cg_solve(hs, self.world, float(mass), float(sigma), float(tol), _ptr(bb),
+                                           _ptr(x), ctypes.byref(info)))
+        return x, info.as_dict()
 
 
 class Server:
