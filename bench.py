@@ -375,7 +375,8 @@ def packed_bench(lqcd, inputs):
             "bitwise_equal_to_separate": same, "max_true_resid": max(max(i["true_resid"]) for i in infos)}
 
 
-def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 30, mixed=False, sequential=True):
+def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 30, mixed=False, sequential=True,
+                  sides=(8, 16, 24, 32)):
     """Poisson stream of multi-shift requests over resident 8^4/16^4/24^4/32^4
     fields (1..16 shifts log-spaced in [1e-5, 1e2], tol 1e-8 or 1e-10,
     m = 0.01) under an HBM budget.  A burst run (all requests at t = 0)
@@ -385,11 +386,11 @@ def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 3
     to 3e-4, FP64 reliable updates).  sequential: also time the same requests
     solved one after another by the plain FP64 solver (device-resident
     sources, no host copies)."""
-    sizes = [(8,) * 4, (16,) * 4, (24,) * 4, (32,) * 4]
+    sizes = [(L,) * 4 for L in sides]
     rng = np.random.default_rng(inputs.ARRIVAL_SEED)
     reqs = []
     for k in range(n_req):
-        f = int(rng.integers(0, 4))
+        f = int(rng.integers(0, len(sizes)))
         ns = int(rng.integers(1, 17))
         tol = [1e-8, 1e-10][int(rng.integers(0, 2))]
         reqs.append((f, ns, tol, k))
@@ -398,13 +399,14 @@ def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 3
         if mixed:
             srv.set_opts(prec=1, recon=12, fp64_until=3e-4)
         fids = [srv.register_field(d, inputs.random_links(d)) for d in sizes]
-        srcs = {f: inputs.gaussian_field(sizes[f], k=100 + f) for f in range(4)}
+        srcs = {f: inputs.gaussian_field(sizes[f], k=100 + f) for f in range(len(sizes))}
+        res["fields"] = [f"{d[0]}^4" for d in sizes]
 
         def run(arrivals):
             """Submit at the given offsets; returns (wall, latencies, peak bytes, peak slots, worst residual)."""
             t0 = time.perf_counter()
             pend, lat = [], []
-            peak_b = peak_s = 0
+            peak_b = peak_s = peak_q = 0
             worst = 0.0
             i = 0
             while i < len(reqs) or pend:
@@ -427,15 +429,16 @@ def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 3
                 st = srv.stats()
                 peak_b = max(peak_b, st["hbm_in_use"])
                 peak_s = max(peak_s, st["active_slots"])
+                peak_q = max(peak_q, st["queued"])
                 time.sleep(0.0005)
-            return time.perf_counter() - t0, np.array(lat), peak_b, peak_s, worst
+            return time.perf_counter() - t0, np.array(lat), peak_b, peak_s, peak_q, worst
 
-        def summary(wall, lat, peak_b, peak_s, worst):
+        def summary(wall, lat, peak_b, peak_s, peak_q, worst):
             return {"solves_per_s": round(len(reqs) / wall, 3), "wall_s": round(wall, 2),
                     "p50_latency_s": round(float(np.percentile(lat, 50)), 4),
                     "p99_latency_s": round(float(np.percentile(lat, 99)), 4),
                     "peak_admitted_bytes": int(peak_b), "peak_active_slots": int(peak_s),
-                    "max_true_resid_over_tol": round(worst, 3)}
+                    "peak_queued": int(peak_q), "max_true_resid_over_tol": round(worst, 3)}
 
         out = run(np.zeros(len(reqs)))
         cap = len(reqs) / out[0]
@@ -457,7 +460,7 @@ def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 3
         c.links_upload(inputs.random_links(d))
         ctxs.append(c)
         bds.append(lqcd.to_device_spinor(inputs.gaussian_field(d, k=100 + f)))
-    for f in range(4):  # graphs and workspaces
+    for f in range(len(sizes)):  # graphs and workspaces
         ctxs[f].mscg_solve_dev(MASS, inputs.log_shifts(16), 1e-10, bds[f],
                                torch.empty((16, 3, ctxs[f].Vh), dtype=torch.complex128, device="cuda"))
     torch.cuda.synchronize()
@@ -482,21 +485,30 @@ def rel_diff_per_shift(x, xref):
     return float((d / n).max())
 
 
-def mixed_48_bench(lqcd, inputs, torch):
-    """Mixed precision on 48^4 (same mass and shifts): FP32 12-real links with an FP64
-    phase to 3e-4 and FP64 reliable updates, against the FP64 solver on the same lattice."""
+def mixed_48_bench(lqcd, inputs, torch, with_oracle=False):
+    """Mixed precision on 48^4 (same mass and shifts): FP32 12-real links with an
+    FP64 phase to 3e-4, and FP16 12-real links, both with FP64 reliable updates
+    and per-shift refinement, against the FP64 solver on the same lattice.  The
+    oracle recomputes the true residual of the smallest, a middle and the largest
+    shift of every result.  with_oracle: one full FP64 oracle solve (all host
+    cores, minutes) gives every shift's error of every result against it."""
     dims = (48, 48, 48, 48)
     U = inputs.random_links(dims)
     b = inputs.gaussian_field(dims, k=0)
     shifts = inputs.log_shifts(N_SHIFT)
     ctx = lqcd.Context(dims)
     ctx.links_upload(U)
-    del U
     bd = lqcd.to_device_spinor(b)
     xd = torch.empty((N_SHIFT, 3, ctx.Vh), dtype=torch.complex128, device="cuda")
     out = {"lattice": list(dims)}
+    from oracle import oracle
+    orc = oracle()
+    orc.set_threads(0)
+    sample = (0, 7, N_SHIFT - 1)
+    results = {}
     x64 = None
-    for name, kw in [("fp64", dict(prec=0, recon=18)), ("fp32_12r", dict(prec=1, recon=12, fp64_until=3e-4))]:
+    for name, kw in [("fp64", dict(prec=0, recon=18)), ("fp32_12r", dict(prec=1, recon=12, fp64_until=3e-4)),
+                     ("fp16_12r", dict(prec=2, recon=12, fp64_until=0.0))]:
         ctx.set_opts(**kw)
         ctx.mscg_solve_dev(MASS, shifts, TOL, bd, xd)  # warm-up (graph capture, workspaces)
         torch.cuda.synchronize()
@@ -511,9 +523,40 @@ def mixed_48_bench(lqcd, inputs, torch):
             x64 = xd.clone()
         else:
             out[name]["max_rel_diff_vs_fp64_solution"] = rel_diff_per_shift(xd, x64)
-    out["speedup_fp32_vs_fp64"] = round(out["fp64"]["s"] / out["fp32_12r"]["s"], 3)
+        out[name]["oracle_true_resid_sampled"] = {
+            f"{shifts[i]:.3g}": orc.true_residual(dims, U, MASS, shifts[i], b, lqcd.from_device_spinor(xd[i]))
+            for i in sample}
+        if with_oracle:
+            results[name] = lqcd.from_device_spinor(xd)
+    for name in ("fp32_12r", "fp16_12r"):
+        out[f"speedup_{name}_vs_fp64"] = round(out["fp64"]["s"] / out[name]["s"], 3)
+    if with_oracle:
+        t0 = time.perf_counter()
+        xo, oinfo = orc.mscg(dims, U, MASS, shifts, b, TOL)
+        out["oracle_solve"] = {"s": round(time.perf_counter() - t0, 1), "iters": oinfo["iters"],
+                               "threads": orc.set_threads(0), "status": oinfo["status"]}
+        for name, x in results.items():
+            out[name]["rel_err_vs_oracle_per_shift"] = [
+                float(np.linalg.norm(x[i] - xo[i]) / np.linalg.norm(xo[i])) for i in range(N_SHIFT)]
+            out[name]["bound_2_kappa_tol"] = [2 * (MASS ** 2 + sg + 16) / (MASS ** 2 + sg) * TOL for sg in shifts]
     out["note"] = "second of two solves of each kind (the first captures graphs and allocates workspaces)"
     ctx.close()
+    return out
+
+
+def fma_rates_bench(lqcd, sweep):
+    """Measured FP64 / FP32 FMA issue rates and the native-FP64 D_eo against
+    the FP64 one: 288 DFMA + 54 DMUL per output site (8 half-hops of a 3x3
+    complex mat-vec, the hop signs and the 1/2)."""
+    r = lqcd.measure_fma_rates()
+    out = {k: round(v / 1e12, 4) for k, v in r.items()}
+    out["unit"] = "T FMA/s"
+    for L, v in sweep.items():
+        nat = v.get("fp64_native_dfma")
+        if nat:
+            ops = (288 + 54) / (nat["ns_per_site"] * 1e-9)
+            out[f"native_fp64_deo_{L}"] = {"T_fp64_op_per_s": round(ops / 1e12, 4),
+                                           "frac_of_measured_fp64_rate": round(ops / r["fp64_fma_per_s"], 3)}
     return out
 
 
@@ -706,7 +749,10 @@ def deo_sweep(lqcd, inputs, torch, flush, hbm_peak, sizes):
                     ts.append(e0.elapsed_time(e1))
                 med = float(np.median(ts))
                 gbs = bps * c.Vh / (med * 1e-3) / 1e9
+                code = c.deo_tuned_config(prec, recon)
                 res[name] = {"ns_per_site": round(med * 1e6 / c.Vh, 4),
+                             "tuned": {"kind": ["per-thread", "2 threads/site", "4 threads/site", "staged",
+                                                "8 threads/site"][code >> 10], "threads": code & 1023},
                              "best_ns_per_site": round(min(ts) * 1e6 / c.Vh, 4), "GB_s": round(gbs, 1),
                              "frac_hbm": round(gbs / hbm_peak, 3), "frac_nominal_7900": round(gbs / 7900.0, 3),
                              "bytes_per_site": bps}
@@ -733,6 +779,24 @@ def run_ours(args, rank, world, local):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "unit": "ns/site", "config": {"only_md": True},
                               "gauge_md": gauge_md_bench(lqcd, inputs, L=args.lattice)}), flush=True)
+        return
+    if args.only_serving:
+        if rank == 0:
+            b = int(args.serving_budget_gb * (1 << 30))
+            n = args.serving_requests
+            out = {"serving": serving_bench(lqcd, inputs, n_req=n, budget=b),
+                   "serving_mixed": serving_bench(lqcd, inputs, n_req=n, loads=(0.8,), budget=b, mixed=True,
+                                                  sequential=False),
+                   "serving_2gb": serving_bench(lqcd, inputs, n_req=n, loads=(0.95,), budget=2 << 30,
+                                                sequential=False, sides=(8, 16, 24))}
+            print(json.dumps({"metric": METRIC, "unit": "solves/s", "config": {"only_serving": True}, **out}),
+                  flush=True)
+        return
+    if args.only_mixed_48:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": "solves/s", "config": {"only_mixed_48": True},
+                              "mixed_48": mixed_48_bench(lqcd, inputs, torch, with_oracle=args.with_oracle_48)}),
+                  flush=True)
         return
     if args.only_deo:
         if rank == 0:
@@ -860,14 +924,17 @@ def run_ours(args, rank, world, local):
                      ("gauge_md", lambda: gauge_md_bench(lqcd, inputs)),
                      ("fermion_force", lambda: fermion_force_bench(lqcd, inputs)),
                      ("stout", lambda: stout_bench(lqcd, inputs)),
-                     ("mixed_48", lambda: mixed_48_bench(lqcd, inputs, torch)),
+                     ("mixed_48", lambda: mixed_48_bench(lqcd, inputs, torch, with_oracle=args.with_oracle_48)),
+                     ("fma_rates", lambda: fma_rates_bench(lqcd, sweep)),
                      ("batched", lambda: batched_bench(lqcd, inputs, torch, hbm_peak)),
                      ("packed", lambda: packed_bench(lqcd, inputs)),
                      ("serving", lambda: serving_bench(lqcd, inputs, n_req=args.serving_requests,
                                                        budget=int(args.serving_budget_gb * (1 << 30)))),
                      ("serving_mixed", lambda: serving_bench(lqcd, inputs, n_req=args.serving_requests, loads=(0.8,),
                                                              budget=int(args.serving_budget_gb * (1 << 30)),
-                                                             mixed=True, sequential=False))]:
+                                                             mixed=True, sequential=False)),
+                     ("serving_2gb", lambda: serving_bench(lqcd, inputs, n_req=args.serving_requests, loads=(0.95,),
+                                                           budget=2 << 30, sequential=False, sides=(8, 16, 24)))]:
         if name in args.skip:
             continue
         try:
@@ -918,14 +985,20 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--sweep", type=int, nargs="*", default=[16, 24, 32, 48])
     ap.add_argument("--lattice", type=int, default=32, help="side of the solve lattice (default 32)")
-    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: rational gauge_md fermion_force stout mixed_48 batched packed serving "
-                         "serving_mixed")
+    ap.add_argument("--skip", nargs="*", default=[], help="extra sections to skip: rational gauge_md fermion_force stout mixed_48 fma_rates batched "
+                         "packed serving serving_mixed serving_2gb")
     ap.add_argument("--only-solve", action="store_true",
                     help="time the solves only (no e2e, profile, mixed, sweep, CPU legs); for ncu launch lists")
     ap.add_argument("--only-md", action="store_true",
                     help="only the gauge MD step timing at --lattice (for profiling)")
     ap.add_argument("--only-deo", action="store_true",
                     help="run the D_eo sweep only (sizes from --sweep); for ncu captures of the stencil")
+    ap.add_argument("--with-oracle-48", action="store_true",
+                    help="mixed_48 section: also one full FP64 oracle solve on 48^4 (minutes on the host cores) "
+                         "for every shift's error of the GPU results")
+    ap.add_argument("--only-mixed-48", action="store_true", help="run the 48^4 mixed-precision section only")
+    ap.add_argument("--only-serving", action="store_true",
+                    help="run the serving sections only (FP64 with the sequential baseline, mixed, tight 2 GB)")
     ap.add_argument("--serving-requests", type=int, default=40, help="requests per serving run (default 40)")
     ap.add_argument("--serving-budget-gb", type=float, default=16.0, help="HBM budget of the serving runs")
     ap.add_argument("--solve-prec", choices=["fp64", "fp32"], default="fp64",

@@ -153,6 +153,13 @@ void lqcd_inject_alloc_failure(long k);
  * and returns LQCD_ESTATE. */
 int lqcd_bounds_errors(unsigned *word);
 
+/* Measured FMA issue rates of the current device, for rooflines of the
+ * arithmetic-bound kernels: every thread of 8 blocks per SM runs 8
+ * independent FMA chains (a = a m + c); *fp64_fma_per_s and *fp32_fma_per_s
+ * receive the best of five timed launches (CUDA events), in FMA per second
+ * (one FMA = 2 flop).  Synchronous, on the default stream. */
+int lqcd_measure_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s);
+
 /* ABI version (major*10000 + minor*100 + patch). */
 int lqcd_version(void);
 
@@ -229,6 +236,15 @@ int lqcd_deo_apply_host_noalloc(lqcd_ctx *ctx, int out_parity, const double *in,
  *   prec LQCD_PREC_FP16: complex64 spinors, FP16 links, recon 12. */
 int lqcd_deo_apply_ex(lqcd_ctx *ctx, int out_parity, int prec, int recon,
                       const void *in, void *out, void *stream);
+
+/* Launch configuration the autotuner chose for lqcd_deo_apply_ex(prec,
+ * recon) on this context's lattice (the first such call times the candidates,
+ * each after emptying L2, and keeps the fastest for the process): *code =
+ * kind * 1024 + threads per block, kind 0 = one thread per site, 1 / 2 / 4 =
+ * 2 / 4 / 8 threads per site (the directions, or for 8 the half-hops, split
+ * over adjacent lanes), 3 = the staged persistent FP64 kernel; 0 before the
+ * first call.  LQCD_EINVAL for a (prec, recon) pair without a kernel. */
+int lqcd_deo_tuned_config(const lqcd_ctx *ctx, int prec, int recon, int *code);
 
 /* Multi-right-hand-side D_eo/D_oe in FP32: each link is loaded once for all
  * n_rhs (1..16) fields.  Device layout of in/out: complex64 [3][Vh][n_rhs]

@@ -1,6 +1,7 @@
 // api.cu -- the extern "C" entry points declared in include/lqcd.h:
 // argument validation, context life cycle, error reporting; the work is
 // done by deo.cu, solver.cu, mrhs.cu and serve.cu.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -96,11 +97,68 @@ int validate_opts(const lqcd_opts *o)
     return LQCD_OK;
 }
 
+// Issue-rate probe: every thread runs 8 independent FMA chains of K steps,
+// a = a * m + c, so the pipe never waits for a result; the sum is stored only
+// when it takes a value it never takes (kept so the chains are not removed).
+template <class T>
+__global__ void __launch_bounds__(256) k_fma_rate(int K, T m, T c, T *sink)
+{
+    T a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = (T)(threadIdx.x + k) * (T)1e-3;
+#pragma unroll 8
+    for (int it = 0; it < K; ++it)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) a[k] = fma(a[k], m, c);
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s += a[k];
+    if (s == (T)-1.2345) *sink = s;
+}
+
+template <class T>
+static int fma_rate(double *out)
+{
+    int dev = 0, nsm = 0;
+    LQCD_CUDA(cudaGetDevice(&dev));
+    LQCD_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    DevBuf sink;
+    if (int st = sink.ensure(sizeof(double))) return st;
+    const unsigned blocks = (unsigned)nsm * 8;
+    const int K = 2048;
+    cudaEvent_t e0, e1;
+    LQCD_CUDA(cudaEventCreate(&e0));
+    LQCD_CUDA(cudaEventCreate(&e1));
+    k_fma_rate<T><<<blocks, 256>>>(K, (T)0.999, (T)1e-3, sink.as<T>());  // warm
+    float best = 1e30f;
+    for (int r = 0; r < 5; ++r) {
+        cudaEventRecord(e0);
+        k_fma_rate<T><<<blocks, 256>>>(K, (T)0.999, (T)1e-3, sink.as<T>());
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    LQCD_CUDA(cudaGetLastError());
+    *out = (double)blocks * 256.0 * 8.0 * K / (best * 1e-3);
+    return LQCD_OK;
+}
+
 }  // namespace lqcd
 
 using namespace lqcd;
 
 extern "C" {
+
+int lqcd_measure_fma_rates(double *fp64_fma_per_s, double *fp32_fma_per_s)
+{
+    if (!fp64_fma_per_s || !fp32_fma_per_s) return fail(LQCD_EINVAL, "NULL argument");
+    if (int st = fma_rate<double>(fp64_fma_per_s)) return st;
+    return fma_rate<float>(fp32_fma_per_s);
+}
 
 void lqcd_default_opts(lqcd_opts *o)
 {

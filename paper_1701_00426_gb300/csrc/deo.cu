@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(kTile, 2)
 }
 
 // Same operator with SPLIT threads per site (adjacent lanes): thread `part`
-// takes directions mu in [part*4/SPLIT, (part+1)*4/SPLIT), the partial
+// takes directions mu in [part*4/SPLIT, (part+1)*4/SPLIT) (SPLIT 8: one
+// half-hop, direction part/2, forward for even part), the partial
 // double-float sums are merged across the lanes by a fixed xor butterfly
 // (two_sum is exact and symmetric, so every lane ends with the same value)
 // and the first lane writes.  Shortens the per-thread chain of dependent
@@ -356,21 +357,43 @@ __global__ void __launch_bounds__(kTile)
     for (int k = 0; k < 6; ++k) acc_zero(acc[k]);
     bool bad = false;
     const int Vh = g.Vh;
-#pragma unroll 1
-    for (int mu = part * (4 / SPLIT); mu < (part + 1) * (4 / SPLIT); ++mu) {
+    if (SPLIT == 8) {
+        // one half-hop per lane: lane part takes direction part / 2, forward
+        // (even part) or backward (odd part); all its loads are independent
+        const int mu = part >> 1;
         int f, b;
         uint32_t nf, nb;
         hop(g, S, mu, f, b, nf, nb);
         float4 U[9], v[3];
         float ch[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        load_link_df(L, mu, P, i, Vh, U);
-        load_spinor_df<SF_IEEE>(in, f, Vh, nf, v, bad);
-        hop_fwd_df(acc, ch, U, v);
-        load_link_df(L, mu, 1 - P, b, Vh, U);
-        load_spinor_df<SF_IEEE>(in, b, Vh, nb, v, bad);
-        hop_bwd_df(acc, ch, U, v);
+        if ((part & 1) == 0) {
+            load_link_df(L, mu, P, i, Vh, U);
+            load_spinor_df<SF_IEEE>(in, f, Vh, nf, v, bad);
+            hop_fwd_df(acc, ch, U, v);
+        } else {
+            load_link_df(L, mu, 1 - P, b, Vh, U);
+            load_spinor_df<SF_IEEE>(in, b, Vh, nb, v, bad);
+            hop_bwd_df(acc, ch, U, v);
+        }
 #pragma unroll
         for (int k = 0; k < 6; ++k) acc_flush(acc[k], ch[k]);
+    } else {
+#pragma unroll 1
+        for (int mu = part * (4 / SPLIT); mu < (part + 1) * (4 / SPLIT); ++mu) {
+            int f, b;
+            uint32_t nf, nb;
+            hop(g, S, mu, f, b, nf, nb);
+            float4 U[9], v[3];
+            float ch[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            load_link_df(L, mu, P, i, Vh, U);
+            load_spinor_df<SF_IEEE>(in, f, Vh, nf, v, bad);
+            hop_fwd_df(acc, ch, U, v);
+            load_link_df(L, mu, 1 - P, b, Vh, U);
+            load_spinor_df<SF_IEEE>(in, b, Vh, nb, v, bad);
+            hop_bwd_df(acc, ch, U, v);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc_flush(acc[k], ch[k]);
+        }
     }
 #pragma unroll
     for (int o = 1; o < SPLIT; o <<= 1)
@@ -574,8 +597,8 @@ int deo_check_stall(lqcd_ctx *c)
 // ------------------------------------------------------------------ autotuner
 // Threads per block of the stand-alone D_eo kernels, chosen per (variant,
 // lattice) by timing 64, 128 and 256 on the first call (CUDA events on the
-// call's stream; D_eo does not depend on the block size, so the tuning runs
-// produce the right output).  Cached for the process and, when the
+// call's stream, L2 emptied before each timed launch; D_eo does not depend
+// on the block size, so the tuning runs produce the right output).  Cached for the process and, when the
 // environment variable LQCD_TUNE_CACHE names a file, across processes.
 // During stream capture the default (256) is used without tuning.
 static std::mutex g_tune_mu;
@@ -620,8 +643,27 @@ static void tune_save(const std::string &key, int bs)
     fclose(fp);
 }
 
+// Reads n float4 of buf (grid-stride) and keeps nothing: run between two
+// timed launches of the tuner it replaces every line of L2 with clean lines
+// of buf, so the next launch starts with cold links and spinors, as a
+// stand-alone application does.  (The store is never taken: the XOR of the
+// buffer's zero bytes is zero.)
+__global__ void k_l2_evict_read(const float4 *__restrict__ buf, size_t n, unsigned *sink)
+{
+    unsigned x = 0;
+    for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
+        const float4 v = __ldcg(buf + k);
+        x ^= __float_as_uint(v.x) ^ __float_as_uint(v.y) ^ __float_as_uint(v.z) ^ __float_as_uint(v.w);
+    }
+    if (x == 0x9E3779B9u) *sink = x;
+}
+
+// Scratch of the tuner's L2 eviction: twice the L2 size, zero-filled.
+constexpr size_t kEvictBytes = 256ull << 20;
+
 // Candidates are encoded as kind * 1024 + threads per block; kind selects a
-// kernel variant (0: one thread per site, 1/2: 2/4 threads per site).
+// kernel variant (0: one thread per site, 1/2/4: 2/4/8 threads per site,
+// 3: the staged persistent kernel).
 template <class Launch>
 static int tuned_launch(lqcd_ctx *c, int variant, cudaStream_t s, Launch launch, int ncand = 3,
                         const int *cands = nullptr)
@@ -644,14 +686,34 @@ static int tuned_launch(lqcd_ctx *c, int variant, cudaStream_t s, Launch launch,
         cudaEvent_t e0, e1;
         LQCD_CUDA(cudaEventCreate(&e0));
         LQCD_CUDA(cudaEventCreate(&e1));
+        // each timed launch starts with L2 emptied of the operator's data (a
+        // stand-alone application streams cold links); without the scratch
+        // buffer (allocation refused) the launches run back to back
+        DevBuf evict;
+        unsigned *sink = nullptr;
+        if (evict.ensure(kEvictBytes + 16) == LQCD_OK &&
+            cudaMemsetAsync(evict.ptr, 0, kEvictBytes + 16, s) == cudaSuccess)
+            sink = (unsigned *)((char *)evict.ptr + kEvictBytes);
+        else
+            set_error("");
+        cudaGetLastError();
         for (int k = 0; k < ncand; ++k) {
             launch(cand[k]);  // warm
             float t = 0.f;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < 3; ++r) launch(cand[k]);
-            cudaEventRecord(e1, s);
-            cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&t, e0, e1);
+            for (int r = 0; r < 3; ++r) {
+                if (sink) {
+                    k_l2_evict_read<<<1216, 256, 0, s>>>((const float4 *)evict.ptr, kEvictBytes / sizeof(float4),
+                                                         sink);
+                    c->launches += 1;
+                }
+                float tr = 0.f;
+                cudaEventRecord(e0, s);
+                launch(cand[k]);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&tr, e0, e1);
+                t += tr;
+            }
             c->launches += 4;
             if (t < best) {
                 best = t;
@@ -660,6 +722,7 @@ static int tuned_launch(lqcd_ctx *c, int variant, cudaStream_t s, Launch launch,
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        evict.release();
         LQCD_CUDA(cudaGetLastError());
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = bs;
@@ -675,6 +738,16 @@ int deo_tuned_block(const lqcd_ctx *c, int variant)
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key(c, variant));
     return it == g_tune.end() ? 0 : it->second;
+}
+
+// Tuner variant of a (prec, recon) pair of the stand-alone D_eo (-1: none).
+static int deo_variant(int prec, int recon)
+{
+    if (prec == LQCD_PREC_FP64) return recon == 12 ? 5 : (recon == 18 ? 0 : -1);
+    if (prec == LQCD_PREC_FP64_NATIVE) return recon == 18 ? 1 : -1;
+    if (prec == LQCD_PREC_FP32) return recon == 18 ? 2 : (recon == 12 ? 3 : -1);
+    if (prec == LQCD_PREC_FP16) return recon == 12 ? 4 : -1;
+    return -1;
 }
 
 int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *out, cudaStream_t s)
@@ -709,8 +782,8 @@ int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *ou
             }, staged ? 4 : 3, cand12);
             break;
         }
-        static const int cand[8] = {64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256,
-                                    3072 + kStagedThreads};
+        static const int cand[10] = {64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256,
+                                     4096 + 128, 4096 + 256, 3072 + kStagedThreads};
         st = tuned_launch(c, 0, s, [&](int code) {
             int kind = code >> 10, bs = code & 1023;
             if (kind == 3 && (!staged || sgrid < 1)) kind = 0, bs = kTile;  // staged stream not built
@@ -723,10 +796,13 @@ int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *ou
             else if (kind == 1)
                 k_deo_df_ieee_split<2><<<(unsigned)((2 * c->Vh + bs - 1) / bs), bs, 0, s>>>(
                     g, L, (const double2 *)in, (double2 *)out, P);
-            else
+            else if (kind == 2)
                 k_deo_df_ieee_split<4><<<(unsigned)((4 * c->Vh + bs - 1) / bs), bs, 0, s>>>(
                     g, L, (const double2 *)in, (double2 *)out, P);
-        }, staged ? 8 : 7, cand);
+            else
+                k_deo_df_ieee_split<8><<<(unsigned)((8 * c->Vh + bs - 1) / bs), bs, 0, s>>>(
+                    g, L, (const double2 *)in, (double2 *)out, P);
+        }, staged ? 10 : 9, cand);
         break;
     }
     case LQCD_PREC_FP64_NATIVE:
@@ -762,3 +838,12 @@ int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *ou
 }
 
 }  // namespace lqcd
+
+extern "C" int lqcd_deo_tuned_config(const lqcd_ctx *c, int prec, int recon, int *code)
+{
+    if (!c || !code) return lqcd::fail(LQCD_EINVAL, "NULL argument");
+    const int v = lqcd::deo_variant(prec, recon);
+    if (v < 0) return lqcd::fail(LQCD_EINVAL, "no such D_eo variant");
+    *code = lqcd::deo_tuned_block(c, v);
+    return LQCD_OK;
+}

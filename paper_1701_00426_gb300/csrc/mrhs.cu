@@ -23,6 +23,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <cstdlib>
 #include <vector>
 
 #include "solver_kernels.cuh"
@@ -153,23 +154,77 @@ __global__ void __launch_bounds__(kTile) k_deo_mrhs(const MrhsArgs A)
     }
 }
 
-// Plain multi-RHS D on field-major batches: block (x, y) takes 256
-// consecutive sites of field group y.
+// Sites per block of the field-major kernel for G (1..16) field groups: the
+// block holds every group of its sites, G * sites <= 256 threads.
+__host__ __device__ constexpr int mrhs_fm_sites(int G) { return 256 / G; }
+
+// Plain multi-RHS D on field-major batches.  A block takes mrhs_fm_sites(G)
+// consecutive sites and all G = n / R groups of R fields: thread t works on
+// site t % sites, fields (t / sites) * R ... + R - 1.  The G threads of a
+// site are in different warps of the same block, so the link they share is
+// read from memory once and served to the other warps from L1; each warp's
+// spinor accesses are consecutive sites of one field.  The hop sign is
+// applied to the link (18 sign flips per hop, whatever R) instead of to each
+// field's spinor; products of a sign-flipped link and a spinor equal those of
+// the link and the sign-flipped spinor bit for bit, so every field keeps the
+// bits of the single-field operator.
 template <int LF, int R>
-__global__ void __launch_bounds__(kTile) k_deo_mrhs_fm(const MrhsArgs A)
+__global__ void __launch_bounds__(256, R >= 16 ? 1 : 2) k_deo_mrhs_fm(const MrhsArgs A)
 {
-    const int site = blockIdx.x * kTile + threadIdx.x;
+    const int sites = mrhs_fm_sites(A.G);
+    const int grp = threadIdx.x / sites;
+    const int site = blockIdx.x * sites + (threadIdx.x - grp * sites);
     if (site >= A.g.Vh) return;
-    const int j0 = blockIdx.y * R;
+    const int j0 = grp * R, Vh = A.g.Vh, n = A.n;
     Stencil S;
     make_stencil(A.g, site, A.P, S);
     float2 acc[R][3];
-    mrhs_site<LF, R, true>(A, S, site, j0, acc);
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[r][c] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        int f, b;
+        uint32_t nf, nb;
+        hop(A.g, S, mu, f, b, nf, nb);
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            float2 U[9];
+            const int idx = dir == 0 ? f : b;
+            const uint32_t ng = dir == 0 ? nf : nb;
+            load_link_f32<LF>(A.links, mu, dir == 0 ? A.P : 1 - A.P, dir == 0 ? site : b, Vh, U);
+#pragma unroll
+            for (int k = 0; k < 9; ++k)
+                U[k] = make_float2(__uint_as_float(__float_as_uint(U[k].x) ^ ng),
+                                   __uint_as_float(__float_as_uint(U[k].y) ^ ng));
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 v[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) v[c] = __ldg(A.in + mrhs_at<true>(c, idx, j0 + r, Vh, n));
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int bb = 0; bb < 3; ++bb) {
+                        if (dir == 0) {
+                            const float2 u = U[a * 3 + bb];
+                            acc[r][a].x = __fmaf_rn(u.x, v[bb].x, __fmaf_rn(-u.y, v[bb].y, acc[r][a].x));
+                            acc[r][a].y = __fmaf_rn(u.x, v[bb].y, __fmaf_rn(u.y, v[bb].x, acc[r][a].y));
+                        } else {
+                            const float2 u = U[bb * 3 + a];
+                            acc[r][a].x = __fmaf_rn(u.x, v[bb].x, __fmaf_rn(u.y, v[bb].y, acc[r][a].x));
+                            acc[r][a].y = __fmaf_rn(u.x, v[bb].y, __fmaf_rn(-u.y, v[bb].x, acc[r][a].y));
+                        }
+                    }
+            }
+        }
+    }
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            A.out[mrhs_at<true>(c, site, j0 + r, A.g.Vh, A.n)] = make_float2(0.5f * acc[r][c].x, 0.5f * acc[r][c].y);
+            A.out[mrhs_at<true>(c, site, j0 + r, Vh, n)] = make_float2(0.5f * acc[r][c].x, 0.5f * acc[r][c].y);
 }
 
 // Per-field deterministic block + tile reduction: vals[r] belongs to field
@@ -359,12 +414,14 @@ static void launch_deo_mrhs_R(const MrhsArgs &A, int R, unsigned nb, cudaStream_
 template <int LF>
 static void launch_deo_mrhs_fm_R(const MrhsArgs &A, int R, cudaStream_t s)
 {
-    const dim3 grid((unsigned)((A.g.Vh + kTile - 1) / kTile), (unsigned)(A.n / R));
-    if (R == 16) k_deo_mrhs_fm<LF, 16><<<grid, kTile, 0, s>>>(A);
-    else if (R == 8) k_deo_mrhs_fm<LF, 8><<<grid, kTile, 0, s>>>(A);
-    else if (R == 4) k_deo_mrhs_fm<LF, 4><<<grid, kTile, 0, s>>>(A);
-    else if (R == 2) k_deo_mrhs_fm<LF, 2><<<grid, kTile, 0, s>>>(A);
-    else k_deo_mrhs_fm<LF, 1><<<grid, kTile, 0, s>>>(A);
+    // A.G = n / R groups; a block holds all groups of its sites
+    const int sites = mrhs_fm_sites(A.G);
+    const unsigned grid = (unsigned)((A.g.Vh + sites - 1) / sites), block = (unsigned)(sites * A.G);
+    if (R == 16) k_deo_mrhs_fm<LF, 16><<<grid, block, 0, s>>>(A);
+    else if (R == 8) k_deo_mrhs_fm<LF, 8><<<grid, block, 0, s>>>(A);
+    else if (R == 4) k_deo_mrhs_fm<LF, 4><<<grid, block, 0, s>>>(A);
+    else if (R == 2) k_deo_mrhs_fm<LF, 2><<<grid, block, 0, s>>>(A);
+    else k_deo_mrhs_fm<LF, 1><<<grid, block, 0, s>>>(A);
 }
 
 // layout: 0 site-major, 1 field-major
@@ -399,6 +456,12 @@ static std::map<std::string, int> g_mr_tune;
 
 static int mrhs_pick_R(lqcd_ctx *c, MrhsArgs A, int lf, cudaStream_t s, int layout)
 {
+    // LQCD_MRHS_R=<R> fixes the fields per thread (when R divides n), for
+    // tests of every variant and for tuning studies
+    if (const char *e = getenv("LQCD_MRHS_R")) {
+        const int R = atoi(e);
+        if (R >= 1 && R <= 16 && (R & (R - 1)) == 0 && A.n % R == 0) return R;
+    }
     char key[96];
     snprintf(key, sizeof key, "n%d lf%d L%d %dx%dx%dx%d", A.n, lf, layout, c->dims[0], c->dims[1], c->dims[2],
              c->dims[3]);

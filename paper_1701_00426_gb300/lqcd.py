@@ -53,7 +53,8 @@ EXPORTED = [
     "lqcd_stout_smear", "lqcd_stout_restore", "lqcd_stout_force", "lqcd_deo_apply_mrhs_layout",
     "lqcd_selftest_stage_wait", "lqcd_inject_alloc_failure", "lqcd_bounds_errors",
     "lqcd_shard_create", "lqcd_shard_geometry", "lqcd_shard_links_upload", "lqcd_shard_deo_apply",
-    "lqcd_shard_exchange", "lqcd_shard_cg_solve",
+    "lqcd_shard_exchange", "lqcd_shard_cg_solve", "lqcd_deo_tuned_config",
+    "lqcd_measure_fma_rates",
 ]
 
 
@@ -166,6 +167,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_stout_smear": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_int]),
         "lqcd_stout_restore": (ctypes.c_int, [vp]),
         "lqcd_stout_force": (ctypes.c_int, [vp, vp, vp, ctypes.c_size_t]),
+        "lqcd_deo_tuned_config": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip]),
+        "lqcd_measure_fma_rates": (ctypes.c_int, [dp, dp]),
         "lqcd_shard_create": (ctypes.c_int, [ip, ctypes.c_int, ctypes.c_int, ctypes.POINTER(lqcd_opts),
                                              ctypes.POINTER(vp)]),
         "lqcd_shard_geometry": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_long)]),
@@ -371,6 +374,12 @@ class Context:
     def deo_apply_ex(self, out_parity: int, prec: int, recon: int, inp, out, stream=None):
         check(self.lib.lqcd_deo_apply_ex(self.h, int(out_parity), int(prec), int(recon), _dptr(inp), _dptr(out),
                                          _stream_ptr(stream)))
+
+    def deo_tuned_config(self, prec: int, recon: int) -> int:
+        """The autotuner's launch code for deo_apply_ex(prec, recon) (0: not tuned yet)."""
+        code = ctypes.c_int()
+        check(self.lib.lqcd_deo_tuned_config(self.h, int(prec), int(recon), ctypes.byref(code)))
+        return code.value
 
     def deo_apply_mrhs(self, out_parity: int, n_rhs: int, recon: int, inp, out, stream=None, layout: int = 0):
         """Multi-RHS D on device batches: layout 0 [3][Vh][n], 1 [3][n][Vh]."""
@@ -638,6 +647,13 @@ class Server:
         st = lqcd_serve_stats()
         check(self.lib.lqcd_serve_stats_get(self.h, ctypes.byref(st)))
         return st.as_dict()
+
+
+def measure_fma_rates() -> dict:
+    """FP64 and FP32 FMA issue rates of the current device (FMA per second)."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    check(load().lqcd_measure_fma_rates(ctypes.byref(a), ctypes.byref(b)))
+    return {"fp64_fma_per_s": a.value, "fp32_fma_per_s": b.value}
 
 
 def inject_alloc_failure(k: int):

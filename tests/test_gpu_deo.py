@@ -196,7 +196,8 @@ print(json.dumps(out))
 '''
 
 
-@pytest.mark.parametrize("code", [64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256, 3072 + 288])
+@pytest.mark.parametrize("code", [64, 128, 256, 1024 + 128, 1024 + 256, 2048 + 128, 2048 + 256, 4096 + 128,
+                                  4096 + 256, 3072 + 288])
 def test_every_tuned_fp64_variant_matches_oracle(gpu, tmp_path, code):
     """Each candidate of the autotuner, forced through a tuning-cache file."""
     import json

@@ -71,6 +71,34 @@ def test_field_major_equals_site_major_bitwise(gpu, n, recon):
             c.deo_apply_mrhs(0, n, recon, xf, of, layout=2)
 
 
+@pytest.mark.parametrize("R", [1, 2, 4, 8, 16])
+@pytest.mark.parametrize("layout", [0, 1])
+def test_every_fields_per_thread_variant_bitwise(gpu, monkeypatch, R, layout):
+    """Each fields-per-thread choice of the tuner, forced, gives every field
+    the bits of the single-field operator (n = 16, both layouts, 12-real and
+    18-real links)."""
+    n = 16
+    dims = (4, 6, 8, 10)
+    U = inputs.random_links(dims)
+    fields = [inputs.gaussian_field(dims, k=j) for j in range(n)]
+    monkeypatch.setenv("LQCD_MRHS_R", str(R))
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        for recon in (12, 18):
+            xs = batch_to_device(fields)                       # [3][Vh][n]
+            xin = xs if layout == 0 else xs.permute(0, 2, 1).contiguous()
+            out = torch.empty_like(xin)
+            c.deo_apply_mrhs(1, n, recon, xin, out, layout=layout)
+            torch.cuda.synchronize()
+            got = batch_from_device(out if layout == 0 else out.permute(0, 2, 1))
+            for j in range(n):
+                xsj = gpu.to_device_spinor(fields[j], dtype=torch.complex64)
+                osj = torch.empty_like(xsj)
+                c.deo_apply_ex(1, gpu.PREC_FP32, recon, xsj, osj)
+                torch.cuda.synchronize()
+                assert np.array_equal(got[j], gpu.from_device_spinor(osj)), f"R {R} field {j}"
+
+
 @pytest.mark.parametrize("n", [4, 16])
 def test_mrhs_unaligned_buffers_equal_aligned(gpu, n):
     """in / out 8 bytes off a 16-byte boundary take the one-field-per-access

@@ -87,6 +87,40 @@ def test_timed_workload_32_sampled_shifts(gpu, orc):
     assert abs(info["iters"] - counts["iters"]) <= 0.05 * counts["iters"]
 
 
+@pytest.mark.parametrize("prec,recon,fp64_until", [(1, 12, 3e-4), (2, 12, 0.0)])
+def test_timed_workload_32_mixed_precision_sampled_shifts(gpu, orc, prec, recon, fp64_until):
+    """The mixed-precision solves bench.py times on the same 32^4 workload:
+    FP32 12-real links after an FP64 phase to 3e-4 (the hybrid default), and
+    FP16 12-real links, with FP64 reliable updates and per-shift refinement.
+    At full size the route differs from the small-lattice tests (tens of
+    refinement iterations, several reliable updates), so the oracle
+    recomputes the true residual of the smallest, a middle and the largest
+    shift from the returned solutions, and every shift's solution is within
+    2 kappa_i tol of the FP64 GPU solve of the same system."""
+    dims = (32, 32, 32, 32)
+    U = inputs.random_links(dims)
+    b = inputs.gaussian_field(dims, k=0)
+    shifts = inputs.log_shifts(15)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        bd = gpu.to_device_spinor(b)
+        x64 = torch.empty((15, 3, c.Vh), dtype=torch.complex128, device="cuda")
+        c.mscg_solve_dev(0.01, shifts, 1e-10, bd, x64)
+        c.set_opts(prec=prec, recon=recon, fp64_until=fp64_until)
+        xd = torch.empty_like(x64)
+        info = c.mscg_solve_dev(0.01, shifts, 1e-10, bd, xd)
+        x, xr = gpu.from_device_spinor(xd), gpu.from_device_spinor(x64)
+    assert max(info["true_resid"][:15]) <= 1e-10
+    assert info["reliable_updates"] + info["refine_iters"] > 0
+    orc.set_threads(0)
+    for i in (0, 7, 14):
+        r = orc.true_residual(dims, U, 0.01, shifts[i], b, x[i])
+        assert r <= 1e-10, f"shift {shifts[i]}: oracle-recomputed true residual {r:.3e}"
+    for i, s in enumerate(shifts):
+        kappa = (0.01 ** 2 + s + 16) / (0.01 ** 2 + s)
+        assert np.linalg.norm(x[i] - xr[i]) / np.linalg.norm(xr[i]) <= 2 * kappa * 1e-10
+
+
 @pytest.mark.parametrize("prec,recon,fp64_until",
                          [(1, 18, 1e-4), (1, 12, 1e-4), (1, 12, 1e-2), (1, 18, 0.0), (1, 12, 0.0), (2, 12, 0.0)])
 def test_15_shifts_mixed_precision(gpu, orc, prec, recon, fp64_until):
