@@ -242,8 +242,8 @@ int lqcd_deo_apply_ex(lqcd_ctx *ctx, int out_parity, int prec, int recon,
  * each after emptying L2, and keeps the fastest for the process): *code =
  * kind * 1024 + threads per block, kind 0 = one thread per site, 1 / 2 / 4 =
  * 2 / 4 / 8 threads per site (the directions, or for 8 the half-hops, split
- * over adjacent lanes), 3 = the staged persistent FP64 kernel; 0 before the
- * first call.  LQCD_EINVAL for a (prec, recon) pair without a kernel. */
+ * over adjacent lanes), 3 = the staged persistent FP64 kernel, 5 = FP32 /
+ * FP16 with the direction loop unrolled; 0 before the first call.  LQCD_EINVAL for a (prec, recon) pair without a kernel. */
 int lqcd_deo_tuned_config(const lqcd_ctx *ctx, int prec, int recon, int *code);
 
 /* Multi-right-hand-side D_eo/D_oe in FP32: each link is loaded once for all

@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(kTile, 2)
     for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
 }
 
-template <int LF>
+template <int LF, int UNROLL = 1>
 __global__ void __launch_bounds__(kTile)
     k_deo_f32(Geom g, const void *__restrict__ L, const float2 *__restrict__ in, float2 *__restrict__ out, int P)
 {
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(kTile)
     Stencil S;
     make_stencil(g, i, P, S);
     float2 o[3];
-    deo_site_f32<LF>(g, L, in, S, i, P, g.Vh, o);
+    deo_site_f32<LF, UNROLL>(g, L, in, S, i, P, g.Vh, o);
 #pragma unroll
     for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
 }
@@ -663,7 +663,8 @@ constexpr size_t kEvictBytes = 256ull << 20;
 
 // Candidates are encoded as kind * 1024 + threads per block; kind selects a
 // kernel variant (0: one thread per site, 1/2/4: 2/4/8 threads per site,
-// 3: the staged persistent kernel).
+// 3: the staged persistent kernel, 5: FP32/FP16 with the direction loop
+// unrolled).
 template <class Launch>
 static int tuned_launch(lqcd_ctx *c, int variant, cudaStream_t s, Launch launch, int ncand = 3,
                         const int *cands = nullptr)
@@ -812,23 +813,32 @@ int deo_launch(lqcd_ctx *c, int P, int prec, int recon, const void *in, void *ou
         });
         break;
     case LQCD_PREC_FP32:
-        if (recon == 18)
-            st = tuned_launch(c, 2, s, [&](int bs) {
-                k_deo_f32<LF_F32_18><<<nb(bs), bs, 0, s>>>(g, c->lnk_f18.ptr, (const float2 *)in, (float2 *)out, P);
-            });
-        else if (recon == 12)
-            st = tuned_launch(c, 3, s, [&](int bs) {
-                k_deo_f32<LF_F32_12><<<nb(bs), bs, 0, s>>>(g, c->lnk_f12.ptr, (const float2 *)in, (float2 *)out, P);
-            });
-        else
-            return fail(LQCD_EINVAL, "recon must be 18 or 12");
+    case LQCD_PREC_FP16: {
+        // kind 0: the direction loop rolled; kind 5: unrolled (loads of
+        // later hops issued early)
+        static const int cand_f[6] = {64, 128, 256, 5120 + 64, 5120 + 128, 5120 + 256};
+        if (prec == LQCD_PREC_FP16 && recon != 12) return fail(LQCD_EINVAL, "FP16 links use 12-real storage");
+        if (recon != 18 && recon != 12) return fail(LQCD_EINVAL, "recon must be 18 or 12");
+        const int lf = prec == LQCD_PREC_FP16 ? LF_F16_12 : (recon == 18 ? LF_F32_18 : LF_F32_12);
+        const void *Lp = lf == LF_F16_12 ? c->lnk_h12.ptr : (lf == LF_F32_18 ? c->lnk_f18.ptr : c->lnk_f12.ptr);
+        const int variant = lf == LF_F16_12 ? 4 : (lf == LF_F32_18 ? 2 : 3);
+        st = tuned_launch(c, variant, s, [&](int code) {
+            const bool unr = (code >> 10) == 5;
+            const int bs = code & 1023;
+            const float2 *xi = (const float2 *)in;
+            float2 *xo = (float2 *)out;
+            if (lf == LF_F32_18)
+                unr ? k_deo_f32<LF_F32_18, 4><<<nb(bs), bs, 0, s>>>(g, Lp, xi, xo, P)
+                    : k_deo_f32<LF_F32_18, 1><<<nb(bs), bs, 0, s>>>(g, Lp, xi, xo, P);
+            else if (lf == LF_F32_12)
+                unr ? k_deo_f32<LF_F32_12, 4><<<nb(bs), bs, 0, s>>>(g, Lp, xi, xo, P)
+                    : k_deo_f32<LF_F32_12, 1><<<nb(bs), bs, 0, s>>>(g, Lp, xi, xo, P);
+            else
+                unr ? k_deo_f32<LF_F16_12, 4><<<nb(bs), bs, 0, s>>>(g, Lp, xi, xo, P)
+                    : k_deo_f32<LF_F16_12, 1><<<nb(bs), bs, 0, s>>>(g, Lp, xi, xo, P);
+        }, 6, cand_f);
         break;
-    case LQCD_PREC_FP16:
-        if (recon != 12) return fail(LQCD_EINVAL, "FP16 links use 12-real storage");
-        st = tuned_launch(c, 4, s, [&](int bs) {
-            k_deo_f32<LF_F16_12><<<nb(bs), bs, 0, s>>>(g, c->lnk_h12.ptr, (const float2 *)in, (float2 *)out, P);
-        });
-        break;
+    }
     default:
         return fail(LQCD_EINVAL, "unknown precision");
     }

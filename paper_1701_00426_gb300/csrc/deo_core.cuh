@@ -315,12 +315,16 @@ __device__ __forceinline__ void load_link_f32(const void *L, int mu, int par, in
     }
 }
 
-template <int LF>
+// UNROLL 4 unrolls the direction loop, so that the compiler may issue the
+// link and spinor loads of later hops before the FMAs of earlier ones (more
+// bytes in flight per thread, at the cost of registers); the FMAs and their
+// order are the same, so are the bits.
+template <int LF, int UNROLL = 1>
 __device__ __forceinline__ void deo_site_f32(const Geom &g, const void *L, const float2 *in, const Stencil &S, int i,
                                              int P, int Vh, float2 (&res)[3])
 {
     float2 acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-#pragma unroll 1
+#pragma unroll UNROLL
     for (int mu = 0; mu < 4; ++mu) {
         int f, b;
         uint32_t nf, nb;

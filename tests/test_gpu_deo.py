@@ -359,3 +359,46 @@ def test_calls_from_a_thread_that_never_set_a_device(gpu, orc):
     assert "error" not in out, out.get("error")
     for k in ("deo", "noalloc"):
         assert np.linalg.norm(out[k] - ref) / np.linalg.norm(ref) <= 1e-13
+
+
+LOWP_SCRIPT = r'''
+import sys, numpy as np, torch
+sys.path.insert(0, sys.argv[1])
+from paper_1701_00426_gb300 import inputs, lqcd
+out = {}
+for dims in [(4, 6, 8, 10), (8, 8, 8, 8)]:
+    U = inputs.random_links(dims)
+    with lqcd.Context(dims) as c:
+        c.links_upload(U)
+        x = lqcd.to_device_spinor(inputs.gaussian_field(dims, k=7), dtype=torch.complex64)
+        for prec, recon in ((1, 18), (1, 12), (2, 12)):
+            o = torch.empty_like(x)
+            c.deo_apply_ex(1, prec, recon, x, o)
+            torch.cuda.synchronize()
+            out[f"{dims}{prec}{recon}"] = o.cpu().numpy()
+np.savez(sys.argv[2], **out)
+'''
+
+
+def test_unrolled_low_precision_variants_are_bitwise_equal(gpu, tmp_path):
+    """The FP32 / FP16 kernels with the direction loop unrolled (tuner kind 5)
+    give the bits of the rolled kernels: same FMAs in the same order."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    script = tmp_path / "lowp.py"
+    script.write_text(LOWP_SCRIPT)
+    res = []
+    for code in (256, 5120 + 128):
+        cache = tmp_path / f"tune{code}.txt"
+        cache.write_text("".join(f"deo2 v{v} {d[0]}x{d[1]}x{d[2]}x{d[3]} {code}\n"
+                                 for v in (2, 3, 4) for d in [(4, 6, 8, 10), (8, 8, 8, 8)]))
+        npz = tmp_path / f"o{code}.npz"
+        r = subprocess.run([sys.executable, str(script), root, str(npz)], capture_output=True, text=True,
+                           timeout=300, env=dict(os.environ, LQCD_TUNE_CACHE=str(cache)))
+        assert r.returncode == 0, r.stderr[-2000:]
+        res.append(np.load(npz))
+    assert sorted(res[0].files) == sorted(res[1].files)
+    for k in res[0].files:
+        assert np.array_equal(res[0][k], res[1][k]), k
