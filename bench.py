@@ -465,14 +465,24 @@ def serving_bench(lqcd, inputs, n_req=40, loads=(0.5, 0.8, 0.95), budget=16 << 3
                                torch.empty((16, 3, ctxs[f].Vh), dtype=torch.complex128, device="cuda"))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    by_size = [0.0] * len(sizes)
     for f, ns, tol, k in reqs:
         xd = torch.empty((ns, 3, ctxs[f].Vh), dtype=torch.complex128, device="cuda")
-        ctxs[f].mscg_solve_dev(MASS, inputs.log_shifts(ns), tol, bds[f], xd)
+        t1 = time.perf_counter()
+        ctxs[f].mscg_solve_dev(MASS, inputs.log_shifts(ns), tol, bds[f], xd)  # returns when solved
+        by_size[f] += time.perf_counter() - t1
     torch.cuda.synchronize()
     seq = len(reqs) / (time.perf_counter() - t0)
     for c in ctxs:
         c.close()
     res["sequential_fp64_solves_per_s"] = round(seq, 3)
+    res["sequential_s_by_lattice"] = {f"{d[0]}^4": round(t, 3) for d, t in zip(sizes, by_size)}
+    # Packing can hide the launch-bound small lattices behind the large ones,
+    # but the 24^4 and 32^4 solves already stream at HBM speed alone: the
+    # burst cannot beat the sequential time of those.
+    big = sum(t for d, t in zip(sizes, by_size) if d[0] >= 24)
+    if big > 0:
+        res["bound_burst_vs_sequential_if_large_lattices_stay_bandwidth_bound"] = round(sum(by_size) / big, 3)
     res["speedup_burst_vs_sequential_fp64"] = round(res["burst"]["solves_per_s"] / seq, 3)
     return res
 
@@ -730,12 +740,22 @@ def deo_sweep(lqcd, inputs, torch, flush, hbm_peak, sizes):
             c.links_upload(U)
             del U
             res = {}
-            for name, prec, recon, dt, bps in variants:
-                x = lqcd.to_device_spinor(inputs.gaussian_field(dims), dtype=dt)
-                o = torch.empty_like(x)
+            for name, prec, recon, dt, bps in variants + [("fp16_12r_fp16_spinors_site_norm", None, 12, None, 224.0)]:
                 s = torch.cuda.current_stream()
+                if prec is None:  # FP16 spinors with a per-site norm (lqcd_deo_apply_h16)
+                    hx, nx = lqcd.to_device_h16(inputs.gaussian_field(dims))
+                    ho, no = torch.empty_like(hx), torch.empty_like(nx)
+
+                    def apply():
+                        c.deo_apply_h16(0, hx, nx, ho, no, s)
+                else:
+                    x = lqcd.to_device_spinor(inputs.gaussian_field(dims), dtype=dt)
+                    o = torch.empty_like(x)
+
+                    def apply():
+                        c.deo_apply_ex(0, prec, recon, x, o, s)
                 for _ in range(3):
-                    c.deo_apply_ex(0, prec, recon, x, o, s)
+                    apply()
                 ts = []
                 reps = 10 if L >= 48 else 20
                 for _ in range(reps):
@@ -743,13 +763,13 @@ def deo_sweep(lqcd, inputs, torch, flush, hbm_peak, sizes):
                     e0 = torch.cuda.Event(enable_timing=True)
                     e1 = torch.cuda.Event(enable_timing=True)
                     e0.record(s)
-                    c.deo_apply_ex(0, prec, recon, x, o, s)
+                    apply()
                     e1.record(s)
                     e1.synchronize()
                     ts.append(e0.elapsed_time(e1))
                 med = float(np.median(ts))
                 gbs = bps * c.Vh / (med * 1e-3) / 1e9
-                code = c.deo_tuned_config(prec, recon)
+                code = c.deo_tuned_config(prec, recon) if prec is not None else 5120 + 128
                 res[name] = {"ns_per_site": round(med * 1e6 / c.Vh, 4),
                              "tuned": {"kind": ["per-thread", "2 threads/site", "4 threads/site", "staged",
                                                 "8 threads/site", "per-thread unrolled"][code >> 10],
@@ -757,7 +777,10 @@ def deo_sweep(lqcd, inputs, torch, flush, hbm_peak, sizes):
                              "best_ns_per_site": round(min(ts) * 1e6 / c.Vh, 4), "GB_s": round(gbs, 1),
                              "frac_hbm": round(gbs / hbm_peak, 3), "frac_nominal_7900": round(gbs / 7900.0, 3),
                              "bytes_per_site": bps}
-                del x, o
+                if prec is None:
+                    del hx, nx, ho, no
+                else:
+                    del x, o
         out[f"{L}^4"] = res
         torch.cuda.empty_cache()
     return out

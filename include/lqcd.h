@@ -237,6 +237,20 @@ int lqcd_deo_apply_host_noalloc(lqcd_ctx *ctx, int out_parity, const double *in,
 int lqcd_deo_apply_ex(lqcd_ctx *ctx, int out_parity, int prec, int recon,
                       const void *in, void *out, void *stream);
 
+/* D_eo / D_oe with FP16 links (12 reals, Sec. 2.3) and FP16 spinors with a
+ * per-site FP32 norm, FP32 arithmetic (the half-precision storage variant
+ * with block-scaled spinors; 224 algorithmic bytes per output site).  Device
+ * spinors: `in` / `out` are half2 [3][Vh] (re, im per colour, structure of
+ * arrays as the other device spinors), `in_norm` / `out_norm` float [Vh]; the
+ * value of colour c at half index k is norm[k] * half2[c][k].  Each output
+ * site's norm is the largest |re|, |im| of its three result colours (0 for a
+ * zero site) and its halves are the result over that norm, rounded to
+ * nearest.  Relative error of a few 2^-11 (links, inputs and outputs each
+ * rounded to FP16).  Asynchronous on `stream` (NULL = the context's stream).
+ * in and out (and their norms) must not overlap. */
+int lqcd_deo_apply_h16(lqcd_ctx *ctx, int out_parity, const void *in, const float *in_norm, void *out,
+                       float *out_norm, void *stream);
+
 /* Launch configuration the autotuner chose for lqcd_deo_apply_ex(prec,
  * recon) on this context's lattice (the first such call times the candidates,
  * each after emptying L2, and keeps the fastest for the process): *code =

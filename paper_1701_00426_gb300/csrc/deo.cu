@@ -447,6 +447,67 @@ __global__ void __launch_bounds__(kTile)
     for (int cc = 0; cc < 3; ++cc) out[(size_t)cc * g.Vh + i] = o[cc];
 }
 
+// FP16 links (12 reals) and FP16 spinors with a per-site FP32 norm: the
+// value of colour c at half index k is norm[k] * in[c][k] (half2 re, im).
+// Products and sums in FP32, as deo_site_f32 with FP16 links, the direction
+// loop unrolled (the FP16 kernels are latency-bound rolled).  The output
+// site's norm is the largest |re|, |im| of its three colours, and the halves
+// are the result over that norm, rounded to nearest (0 for a zero result).
+__global__ void __launch_bounds__(kTile)
+    k_deo_h16(Geom g, const void *__restrict__ L, const __half2 *__restrict__ in, const float *__restrict__ in_norm,
+              __half2 *__restrict__ out, float *__restrict__ out_norm, int P)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int Vh = g.Vh;
+    if (i >= Vh) return;
+    Stencil S;
+    make_stencil(g, i, P, S);
+    float2 acc[3] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        int f, b;
+        uint32_t nf, nb;
+        hop(g, S, mu, f, b, nf, nb);
+#pragma unroll
+        for (int dir = 0; dir < 2; ++dir) {
+            const int idx = dir == 0 ? f : b;
+            const uint32_t ng = dir == 0 ? nf : nb;
+            float2 U[9], v[3];
+            load_link_f32<LF_F16_12>(L, mu, dir == 0 ? P : 1 - P, dir == 0 ? i : b, Vh, U);
+            const float nrm = __uint_as_float(__float_as_uint(__ldg(in_norm + idx)) ^ ng);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 t = __half22float2(in[(size_t)c * Vh + idx]);
+                v[c] = make_float2(nrm * t.x, nrm * t.y);
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int bb = 0; bb < 3; ++bb) {
+                    if (dir == 0) {
+                        const float2 u = U[a * 3 + bb];
+                        acc[a].x = __fmaf_rn(u.x, v[bb].x, __fmaf_rn(-u.y, v[bb].y, acc[a].x));
+                        acc[a].y = __fmaf_rn(u.x, v[bb].y, __fmaf_rn(u.y, v[bb].x, acc[a].y));
+                    } else {
+                        const float2 u = U[bb * 3 + a];
+                        acc[a].x = __fmaf_rn(u.x, v[bb].x, __fmaf_rn(u.y, v[bb].y, acc[a].x));
+                        acc[a].y = __fmaf_rn(u.x, v[bb].y, __fmaf_rn(-u.y, v[bb].x, acc[a].y));
+                    }
+                }
+        }
+    }
+    float m = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        acc[c] = make_float2(0.5f * acc[c].x, 0.5f * acc[c].y);
+        m = fmaxf(m, fmaxf(fabsf(acc[c].x), fabsf(acc[c].y)));
+    }
+    const float inv = m > 0.f ? 1.f / m : 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) out[(size_t)c * Vh + i] = __floats2half2_rn(acc[c].x * inv, acc[c].y * inv);
+    out_norm[i] = m;
+}
+
 // Stand-alone D_eo, consumers.
 template <int RECON>
 __device__ __forceinline__ void deo_staged_consume(const Geom &g, RingDF &R, const float4 *__restrict__ L,
@@ -855,5 +916,25 @@ extern "C" int lqcd_deo_tuned_config(const lqcd_ctx *c, int prec, int recon, int
     const int v = lqcd::deo_variant(prec, recon);
     if (v < 0) return lqcd::fail(LQCD_EINVAL, "no such D_eo variant");
     *code = lqcd::deo_tuned_block(c, v);
+    return LQCD_OK;
+}
+
+extern "C" int lqcd_deo_apply_h16(lqcd_ctx *c, int out_parity, const void *in, const float *in_norm, void *out,
+                                  float *out_norm, void *stream)
+{
+    using namespace lqcd;
+    NvtxRange nvtx_("lqcd_deo_apply_h16");
+    if (!c) return fail(LQCD_EINVAL, "NULL context");
+    LQCD_ON_DEVICE(c->device);
+    if (int lr = links_ready(c)) return lr;
+    if (out_parity != 0 && out_parity != 1) return fail(LQCD_EINVAL, "out_parity must be 0 or 1");
+    if (!in || !in_norm || !out || !out_norm) return fail(LQCD_EINVAL, "NULL spinor pointer");
+    if (in == out || (const void *)in_norm == (const void *)out_norm) return fail(LQCD_EINVAL, "in and out must not overlap");
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    const unsigned nb = (unsigned)((c->Vh + 127) / 128);
+    k_deo_h16<<<nb, 128, 0, s>>>(c->g, c->lnk_h12.ptr, (const __half2 *)in, in_norm, (__half2 *)out, out_norm,
+                                 out_parity);
+    LQCD_CUDA(cudaGetLastError());
+    c->launches += 1;
     return LQCD_OK;
 }

@@ -54,7 +54,7 @@ EXPORTED = [
     "lqcd_selftest_stage_wait", "lqcd_inject_alloc_failure", "lqcd_bounds_errors",
     "lqcd_shard_create", "lqcd_shard_geometry", "lqcd_shard_links_upload", "lqcd_shard_deo_apply",
     "lqcd_shard_exchange", "lqcd_shard_cg_solve", "lqcd_deo_tuned_config",
-    "lqcd_measure_fma_rates",
+    "lqcd_measure_fma_rates", "lqcd_deo_apply_h16",
 ]
 
 
@@ -169,6 +169,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "lqcd_stout_force": (ctypes.c_int, [vp, vp, vp, ctypes.c_size_t]),
         "lqcd_deo_tuned_config": (ctypes.c_int, [vp, ctypes.c_int, ctypes.c_int, ip]),
         "lqcd_measure_fma_rates": (ctypes.c_int, [dp, dp]),
+        "lqcd_deo_apply_h16": (ctypes.c_int, [vp, ctypes.c_int, vp, vp, vp, vp, vp]),
         "lqcd_shard_create": (ctypes.c_int, [ip, ctypes.c_int, ctypes.c_int, ctypes.POINTER(lqcd_opts),
                                              ctypes.POINTER(vp)]),
         "lqcd_shard_geometry": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_long)]),
@@ -230,6 +231,28 @@ def to_device_spinor(a: np.ndarray, dtype=None, device="cuda"):
     if dtype is not None:
         t = t.to(dtype)
     return t.to(device).contiguous()
+
+
+def to_device_h16(a: np.ndarray, device="cuda"):
+    """Canonical host [Vh, 3] -> (halves float16 [3, Vh, 2], norms float32 [Vh]):
+    the per-site norm is the largest |re|, |im| of the site (1 for a zero
+    site), the halves the values over it, rounded to FP16."""
+    import torch
+    a = np.asarray(a, np.complex128)
+    m = np.maximum(np.abs(a.real), np.abs(a.imag)).max(axis=1)
+    m = np.where(m > 0, m, 1.0)
+    s = a / m[:, None]
+    h = np.stack([s.real, s.imag], axis=-1).transpose(1, 0, 2)       # [3, Vh, 2]
+    return (torch.from_numpy(np.ascontiguousarray(h)).to(torch.float16).to(device),
+            torch.from_numpy(m.astype(np.float32)).to(device))
+
+
+def from_device_h16(h, norm) -> np.ndarray:
+    """(halves [3, Vh, 2], norms [Vh]) -> canonical host [Vh, 3] complex128."""
+    hv = h.detach().float().cpu().numpy().astype(np.float64)
+    nv = norm.detach().cpu().numpy().astype(np.float64)
+    z = (hv[..., 0] + 1j * hv[..., 1]) * nv[None, :]
+    return np.ascontiguousarray(z.T)
 
 
 def from_device_spinor(t) -> np.ndarray:
@@ -374,6 +397,11 @@ class Context:
     def deo_apply_ex(self, out_parity: int, prec: int, recon: int, inp, out, stream=None):
         check(self.lib.lqcd_deo_apply_ex(self.h, int(out_parity), int(prec), int(recon), _dptr(inp), _dptr(out),
                                          _stream_ptr(stream)))
+
+    def deo_apply_h16(self, out_parity: int, h_in, n_in, h_out, n_out, stream=None):
+        """D_eo with FP16 links and FP16 spinors with per-site norms (device)."""
+        check(self.lib.lqcd_deo_apply_h16(self.h, int(out_parity), _dptr(h_in), _dptr(n_in), _dptr(h_out),
+                                          _dptr(n_out), _stream_ptr(stream)))
 
     def deo_tuned_config(self, prec: int, recon: int) -> int:
         """The autotuner's launch code for deo_apply_ex(prec, recon) (0: not tuned yet)."""

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_symbols():
     src = open(os.path.join(ROOT, "include", "lqcd.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(lqcd_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(lqcd_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -184,7 +184,8 @@ def _entry_bodies():
         if not f.endswith(".cu"):
             continue
         src = open(os.path.join(csrc, f)).read()
-        for m in re.finditer(r"^(?:extern \"C\" )?(?:int|void) (lqcd_[a-z_]+)\((lqcd_ctx|lqcd_server|lqcd_ctx \*const) \*", src, re.M):
+        for m in re.finditer(r"^(?:extern \"C\" )?(?:int|void) (lqcd_[a-z0-9_]+)\((lqcd_ctx|lqcd_server|lqcd_ctx \*const) \*",
+                             src, re.M):
             start = src.index("{", m.end())
             depth, i = 0, start
             while True:

@@ -402,3 +402,39 @@ def test_unrolled_low_precision_variants_are_bitwise_equal(gpu, tmp_path):
     assert sorted(res[0].files) == sorted(res[1].files)
     for k in res[0].files:
         assert np.array_equal(res[0][k], res[1][k]), k
+
+
+@pytest.mark.parametrize("dims", [(4, 6, 8, 10), (8, 8, 8, 8), (10, 4, 6, 12)])
+def test_deo_fp16_spinors_with_site_norm(gpu, orc, dims):
+    """FP16 links and FP16 spinors with a per-site FP32 norm: against the
+    oracle within a few 2^-11 (links, inputs and outputs each rounded to
+    FP16), and the output halves lie in [-1, 1] with the site's largest
+    component at +-1."""
+    U = inputs.random_links(dims)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        for parity in (0, 1):
+            x = inputs.gaussian_field(dims, k=30 + parity)
+            h, n = gpu.to_device_h16(x)
+            ho, no = torch.empty_like(h), torch.empty_like(n)
+            c.deo_apply_h16(parity, h, n, ho, no)
+            torch.cuda.synchronize()
+            got = gpu.from_device_h16(ho, no)
+            ref = orc.deo(dims, parity, U, x)
+            nrm, _ = errs(got, ref)
+            assert nrm <= 3e-3, f"normwise {nrm:.2e}"
+            hv = ho.float().abs().amax(dim=(0, 2)).cpu().numpy()
+            assert np.all(hv <= 1.0) and np.allclose(hv[no.cpu().numpy() > 0], 1.0)
+
+
+def test_deo_fp16_spinors_zero_site(gpu):
+    """A zero input gives zero output with norm 0 (no division by zero)."""
+    dims = (4, 4, 4, 4)
+    with gpu.Context(dims) as c:
+        c.links_upload(inputs.random_links(dims))
+        x = np.zeros((c.Vh, 3), np.complex128)
+        h, n = gpu.to_device_h16(x)
+        ho, no = torch.empty_like(h), torch.empty_like(n)
+        c.deo_apply_h16(0, h, n, ho, no)
+        torch.cuda.synchronize()
+        assert not torch.any(no) and not torch.any(ho.float())
