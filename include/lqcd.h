@@ -251,6 +251,18 @@ int lqcd_deo_apply_ex(lqcd_ctx *ctx, int out_parity, int prec, int recon,
 int lqcd_deo_apply_h16(lqcd_ctx *ctx, int out_parity, const void *in, const float *in_norm, void *out,
                        float *out_norm, void *stream);
 
+/* Environment variables read by the autotuners:
+ *   LQCD_TUNE_CACHE=<file>  the stand-alone D_eo's launch choices are read
+ *                           from and appended to this file (lines
+ *                           "deo2 v<variant> <N0>x<N1>x<N2>x<N3> <code>"),
+ *                           so that later processes skip the timing, or a
+ *                           test fixes a variant;
+ *   LQCD_MRHS_R=<R>         the multi-RHS D_eo uses R fields per thread
+ *                           (1, 2, 4, 8 or 16, when R divides n_rhs) instead
+ *                           of timing the choices.
+ * Every choice gives results within the documented tolerances; the
+ * multi-RHS choices give identical bits. */
+
 /* Launch configuration the autotuner chose for lqcd_deo_apply_ex(prec,
  * recon) on this context's lattice (the first such call times the candidates,
  * each after emptying L2, and keeps the fastest for the process): *code =
