@@ -877,7 +877,7 @@ def run_ours(args, rank, world, local):
     # output array is allocated and touched once, as a caller's loop reuses it
     # host buffers in pinned (page-locked) memory, so the copies run at the
     # link's speed without staging through a bounce buffer
-    e2e_steps = max(1, min(args.steps, 3))
+    e2e_steps = max(1, args.steps)
     b_pin = torch.from_numpy(np.ascontiguousarray(b)).pin_memory().numpy()
     xh = torch.zeros((N_SHIFT, ctx.Vh, 3), dtype=torch.complex128).pin_memory().numpy()
     b = b_pin
