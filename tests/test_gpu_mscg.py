@@ -55,6 +55,25 @@ def test_15_shifts_fp64(gpu, orc, dims):
     check_solution(orc, dims, U, 0.01, shifts, b, x, 1e-10, xref)
 
 
+def test_maximum_shift_count(gpu, orc):
+    """32 shifts, the most one call takes: every lane of the warp that runs
+    the per-shift recurrences and convergence tests carries a shift, and the
+    active-shift mask uses all 32 bits."""
+    dims = (4, 4, 4, 8)
+    shifts = inputs.log_shifts(32, 1e-4, 1e2)
+    U = inputs.random_links(dims, seed=77)
+    b = inputs.gaussian_field(dims, k=3)
+    xref, _ = orc.mscg(dims, U, 0.05, shifts, b, 1e-10)
+    with gpu.Context(dims) as c:
+        c.links_upload(U)
+        x, info = c.mscg_solve(0.05, shifts, 1e-10, b)
+    assert len(info["shift_iters"]) == 32 and min(info["shift_iters"]) > 0
+    # larger shifts converge no later than smaller ones
+    assert all(a >= b_ for a, b_ in zip(info["shift_iters"], info["shift_iters"][1:]))
+    assert max(info["true_resid"]) <= 1e-10
+    check_solution(orc, dims, U, 0.05, shifts, b, x, 1e-10, xref)
+
+
 def test_timed_workload_32_sampled_shifts(gpu, orc):
     """The configuration bench.py times: 32^4 hot links (seed 1701), m = 0.01,
     the 15 log-spaced shifts, tol 1e-10, staged FP64 kernels, through the

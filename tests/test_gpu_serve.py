@@ -40,6 +40,34 @@ def test_packed_equals_solo(gpu, orc):
         c.close()
 
 
+def test_packed_maximum_job_count(gpu):
+    """64 lattices, the most one packed launch takes (the finaliser's job
+    mask has 64 bits): each result equals its lattice solved alone, bit for
+    bit; a 65th lattice is rejected before any launch."""
+    shifts = [1e-3, 0.1]
+    ctxs, bs, solo = [], [], []
+    try:
+        for k in range(65):
+            d = (6, 6, 6, 6) if k % 4 == 0 else (4, 4, 4, 4)  # 3 tiles or 1, both ragged
+            c = gpu.Context(d)
+            ctxs.append(c)
+            c.links_upload(inputs.random_links(d, seed=300 + k))
+            b = inputs.gaussian_field(d, k=k)
+            bs.append(b)
+            if k < 64:
+                solo.append(c.mscg_solve(0.05, shifts, 1e-10, b)[0])
+        xs, infos = gpu.mscg_solve_packed(ctxs[:64], [0.05] * 64, [shifts] * 64, [1e-10] * 64, bs[:64])
+        for k in range(64):
+            assert np.array_equal(xs[k], solo[k]), f"lattice {k}"
+            assert max(infos[k]["true_resid"]) <= 1e-10
+        with pytest.raises(gpu.LqcdError) as e:
+            gpu.mscg_solve_packed(ctxs, [0.05] * 65, [shifts] * 65, [1e-10] * 65, bs)
+        assert e.value.status == gpu.LQCD_EINVAL
+    finally:
+        for c in ctxs:
+            c.close()
+
+
 def _wait(srv, ticket, fid, n, timeout=120):
     t0 = time.time()
     while time.time() - t0 < timeout:
