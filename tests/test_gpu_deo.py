@@ -160,9 +160,10 @@ def test_links_roundtrip_and_upload_errors(gpu):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("dims", [(32, 32, 32, 32), (32, 32, 8, 32), (24, 24, 24, 24)])
+@pytest.mark.parametrize("dims", [(48, 48, 48, 48), (32, 32, 32, 32), (32, 32, 8, 32), (24, 24, 24, 24)])
 def test_deo_fp64_full_size_matches_oracle(gpu, orc, dims):
-    """Benchmark sizes, same launch configuration as bench.py, every output."""
+    """Benchmark sizes (the D_eo sweep runs 16^4 to 48^4), same launch
+    configuration as bench.py, every output."""
     U = inputs.random_links(dims)
     x = inputs.gaussian_field(dims, k=0)
     with gpu.Context(dims) as c:
