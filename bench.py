@@ -786,6 +786,73 @@ def deo_sweep(lqcd, inputs, torch, flush, hbm_peak, sizes):
     return out
 
 
+KERNEL_VARIANTS = {"f32_12": ("PREC_FP32", 12, "complex64"), "f16_12": ("PREC_FP16", 12, "complex64"),
+                   "f64_12": ("PREC_FP64", 12, "complex128"), "f64": ("PREC_FP64", 18, "complex128")}
+
+
+def kernels_probe(lqcd, inputs, torch, L, which, mrhs_n):
+    """Fixed launch sequence for ncu captures of single kernels on L^4.
+    D_eo variants (which): every variant is called once (the autotuner's
+    timing, unless LQCD_TUNE_CACHE already holds its choice, plus one
+    launch), then twice more.  Multi-RHS (mrhs_n > 0, FP32 12-real): in the
+    site-major and then the field-major layout, one call (tuning plus one
+    launch), then five launches after a 256 MB buffer write.  The repeated
+    launches sit in NVTX ranges ("deo_timed", "mrhs_site_major",
+    "mrhs_field_major") that ncu --nvtx-include selects.  Returns the tuned
+    launch codes and the event-timed launches."""
+    dims = (L,) * 4
+    out = {"lattice": list(dims), "deo": {}, "mrhs": {}}
+    with lqcd.Context(dims) as c:
+        c.links_upload(inputs.random_links(dims))
+        s = torch.cuda.current_stream()
+        bufs = {}
+        for w in which:
+            pname, recon, dt = KERNEL_VARIANTS[w]
+            x = lqcd.to_device_spinor(inputs.gaussian_field(dims), dtype=getattr(torch, dt))
+            o = torch.empty_like(x)
+            c.deo_apply_ex(0, getattr(lqcd, pname), recon, x, o, s)
+            bufs[w] = (x, o)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("deo_timed")
+        for w in which:
+            pname, recon, _ = KERNEL_VARIANTS[w]
+            ts = []
+            for _ in range(2):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                c.deo_apply_ex(0, getattr(lqcd, pname), recon, *bufs[w], s)
+                e1.record(s)
+                e1.synchronize()
+                ts.append(round(e0.elapsed_time(e1) * 1e3, 1))
+            out["deo"][w] = {"tuned_code": c.deo_tuned_config(getattr(lqcd, pname), recon), "us": ts}
+        torch.cuda.nvtx.range_pop()
+        del bufs
+        if mrhs_n > 0:
+            flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+            for layout in (0, 1):
+                shape = (3, c.Vh, mrhs_n) if layout == 0 else (3, mrhs_n, c.Vh)
+                x = torch.randn(shape, dtype=torch.complex64, device="cuda")
+                o = torch.empty_like(x)
+                c.deo_apply_mrhs(0, mrhs_n, 12, x, o, s, layout=layout)
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_push(["mrhs_site_major", "mrhs_field_major"][layout])
+                ts = []
+                for _ in range(5):
+                    flush.fill_(1.0)
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(s)
+                    c.deo_apply_mrhs(0, mrhs_n, 12, x, o, s, layout=layout)
+                    e1.record(s)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1) * 1e3)
+                torch.cuda.nvtx.range_pop()
+                med = float(np.median(ts))
+                out["mrhs"][["site_major", "field_major"][layout]] = {
+                    "n": mrhs_n, "us": round(med, 1), "ns_per_field_site": round(med * 1e3 / (c.Vh * mrhs_n), 4)}
+                del x, o
+    return out
+
+
 def run_ours(args, rank, world, local):
     global DIMS, WORKLOAD
     if args.lattice != 32:
@@ -799,6 +866,13 @@ def run_ours(args, rank, world, local):
     barrier(world)
     lqcd.load()
     hbm_peak, peak_src = peaks()
+    if args.only_kernels is not None:
+        if rank == 0:
+            which = [w for w in args.only_kernels.split(",") if w]
+            print(json.dumps({"metric": METRIC, "config": {"only_kernels": which, "mrhs_n": args.mrhs_n},
+                              "kernels_probe": kernels_probe(lqcd, inputs, torch, args.lattice, which,
+                                                             args.mrhs_n)}), flush=True)
+        return
     if args.only_md:
         if rank == 0:
             print(json.dumps({"metric": METRIC, "unit": "ns/site", "config": {"only_md": True},
@@ -1022,6 +1096,10 @@ def main():
                     help="only the gauge MD step timing at --lattice (for profiling)")
     ap.add_argument("--only-deo", action="store_true",
                     help="run the D_eo sweep only (sizes from --sweep); for ncu captures of the stencil")
+    ap.add_argument("--only-kernels", default=None, metavar="VARIANTS",
+                    help="fixed launch sequence for ncu captures on --lattice: D_eo variants, comma-separated, "
+                         "from " + ",".join(KERNEL_VARIANTS) + " (may be empty), then multi-RHS with --mrhs-n")
+    ap.add_argument("--mrhs-n", type=int, default=0, help="with --only-kernels: fields of the multi-RHS D_eo")
     ap.add_argument("--with-oracle-48", action="store_true",
                     help="mixed_48 section: also one full FP64 oracle solve on 48^4 (minutes on the host cores) "
                          "for every shift's error of the GPU results")
