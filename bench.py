@@ -909,6 +909,8 @@ def run_ours(args, rank, world, local):
     ctx.links_upload(U)
     if args.solve_prec == "fp32":
         ctx.set_opts(prec=1, recon=12, fp64_until=3e-4)
+    if args.stencils == "per-thread":
+        ctx.set_opts(staged=0)
     bd = lqcd.to_device_spinor(b)
     xd = torch.empty((N_SHIFT, 3, ctx.Vh), dtype=torch.complex128, device="cuda")
     info = None
@@ -942,7 +944,8 @@ def run_ours(args, rank, world, local):
                               "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
                               "iters": it["iters"], "max_true_resid": worst_res, "gpu_launches": launches,
                               "kernel_ms": [round(m, 4) for m in kms],
-                              "config": {"workload": WORKLOAD, "only_solve": True, "prec": args.solve_prec}}),
+                              "config": {"workload": WORKLOAD, "only_solve": True, "prec": args.solve_prec,
+                                         "stencils": args.stencils}}),
                   flush=True)
         ctx.close()
         return
@@ -1111,9 +1114,13 @@ def main():
     ap.add_argument("--solve-prec", choices=["fp64", "fp32"], default="fp64",
                     help="with --only-solve: precision of the timed solves (fp32: 12-real links, FP64 phase "
                          "to 3e-4, FP64 reliable updates)")
+    ap.add_argument("--stencils", choices=["staged", "per-thread"], default="staged",
+                    help="with --only-solve: the FP64 iteration's D_oe / D_eo kernels (per-thread: opts.staged = 0)")
     args = ap.parse_args()
     if args.solve_prec != "fp64" and not args.only_solve:
         ap.error("--solve-prec applies to --only-solve runs")
+    if args.stencils != "staged" and not args.only_solve:
+        ap.error("--stencils applies to --only-solve runs")
     if args.impl == "reference":
         # the oracle runs on the host; ranks other than 0 exit without work
         run_reference(args, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")))
