@@ -861,7 +861,9 @@ def run_ours(args, rank, world, local):
     import torch
     from paper_1701_00426_gb300 import build, inputs, lqcd
     torch.cuda.set_device(local)
-    if rank == 0 or world > 1:
+    # one rank per node compiles (the others would write the same objects);
+    # every rank loads the library after the barrier
+    if local == 0:
         build.build()
     barrier(world)
     lqcd.load()
