@@ -17,10 +17,12 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
 #include "solver_kernels.cuh"
+#include "solver_f32_persist.cuh"
 
 namespace lqcd {
 
@@ -408,6 +410,45 @@ static int staged_solver_blocks()
     return g_st_blocks[dev];
 }
 
+// Resident blocks of the persistent FP32 K2 (all link formats and batch
+// sizes), once per device; 0 = the one-block-per-tile k_it_deo2 runs.
+static int g_f32p_blocks[64];
+static bool g_f32p_done[64];
+
+template <class K>
+static int kernel_resident_blocks(K kern, int nsm)
+{
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kIterThreads, 0) != cudaSuccess) occ = 0;
+    cudaGetLastError();
+    return occ * nsm;
+}
+
+int f32_persist_blocks()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    std::lock_guard<std::mutex> lk(g_st_mu);
+    if (!g_f32p_done[dev]) {
+        g_f32p_done[dev] = true;
+        const char *env = getenv("LQCD_F32_K2_PERSIST");
+        if (env && env[0] == '0' && env[1] == '\0') {
+            g_f32p_blocks[dev] = 0;  // one block per tile (k_it_deo2)
+            return 0;
+        }
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) nsm = 0;
+        int b = kernel_resident_blocks(k_it_deo2_f32p<1, LF_F32_18>, nsm);
+        b = std::min(b, kernel_resident_blocks(k_it_deo2_f32p<1, LF_F32_12>, nsm));
+        b = std::min(b, kernel_resident_blocks(k_it_deo2_f32p<1, LF_F16_12>, nsm));
+        b = std::min(b, kernel_resident_blocks(k_it_deo2_f32p<kMaxJobs, LF_F32_18>, nsm));
+        b = std::min(b, kernel_resident_blocks(k_it_deo2_f32p<kMaxJobs, LF_F32_12>, nsm));
+        b = std::min(b, kernel_resident_blocks(k_it_deo2_f32p<kMaxJobs, LF_F16_12>, nsm));
+        g_f32p_blocks[dev] = b;
+    }
+    return g_f32p_blocks[dev];
+}
+
 // All jobs of the batch carry the staged link stream.
 template <int NJ>
 static bool batch_staged(const IterBatch<NJ> &B)
@@ -463,9 +504,19 @@ static void launch_kernel_k(const IterBatch<NJ> &B, int k, int ntot, int vp, int
         else launch_dep(k_it_deo1<NJ, VP_F32, LF_F16_12>, g1, tb, 0, s, dep, B);
     }
     if (k == 1) {
-        if (lf == LF_F32_18) launch_dep(k_it_deo2<NJ, VP_F32, LF_F32_18>, g1, tb, 0, s, dep, B);
-        else if (lf == LF_F32_12) launch_dep(k_it_deo2<NJ, VP_F32, LF_F32_12>, g1, tb, 0, s, dep, B);
-        else launch_dep(k_it_deo2<NJ, VP_F32, LF_F16_12>, g1, tb, 0, s, dep, B);
+        const int pb = std::min(ntot, f32_persist_blocks());
+        const dim3 gp((unsigned)pb);
+        if (pb > 0) {
+            if (lf == LF_F32_18) launch_dep(k_it_deo2_f32p<NJ, LF_F32_18>, gp, tb, 0, s, dep, B, ntot);
+            else if (lf == LF_F32_12) launch_dep(k_it_deo2_f32p<NJ, LF_F32_12>, gp, tb, 0, s, dep, B, ntot);
+            else launch_dep(k_it_deo2_f32p<NJ, LF_F16_12>, gp, tb, 0, s, dep, B, ntot);
+        } else if (lf == LF_F32_18) {
+            launch_dep(k_it_deo2<NJ, VP_F32, LF_F32_18>, g1, tb, 0, s, dep, B);
+        } else if (lf == LF_F32_12) {
+            launch_dep(k_it_deo2<NJ, VP_F32, LF_F32_12>, g1, tb, 0, s, dep, B);
+        } else {
+            launch_dep(k_it_deo2<NJ, VP_F32, LF_F16_12>, g1, tb, 0, s, dep, B);
+        }
     }
     if (k == 2) launch_dep(k_it_upd_r<NJ, VP_F32>, g1, tb, 0, s, dep, B);
     if (k == 3) launch_dep(k_it_upd_shifts<NJ, VP_F32>, g1, tb, 0, s, dep, B);

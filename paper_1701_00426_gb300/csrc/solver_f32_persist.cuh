@@ -1,0 +1,122 @@
+// solver_f32_persist.cuh -- persistent form of the FP32 K2 of the
+// multi-shift CG iteration (Sec. 2.2, Eq. lineqeo):
+// q = (m^2 + sigma_b) p - D_eo t and <p, q>, with the alpha / zeta finaliser.
+//
+// k_it_deo2<NJ, VP_F32, LF> launches one block per tile. Every block ends
+// with a fence and an atomic ticket, and the last block forms the total. In
+// the FP32 iteration that fixed cost is a large part of the kernel: 44.8 us
+// against 30.1 us for K1 at 32^4 under ncu, with only 12.6 MB more to read.
+// Here a grid of resident blocks walks the tiles gt = blockIdx.x,
+// blockIdx.x + gridDim.x, ... .
+// - Each tile's partial is a plain store.
+// - After its last tile, a block takes one ticket per job it worked on.
+// - The block that completes a job's tile count sums the partials in tile
+//   order and runs finalize_pq_warp.
+// The site arithmetic and the in-tile reduction are those of k_it_deo2, so
+// the tile partials, their tile-ordered sum and the iteration are bitwise
+// the same.
+#pragma once
+
+#include "solver_kernels.cuh"
+
+namespace lqcd {
+
+constexpr int kF32PersistMinBlocks = 4;  // resident blocks per SM asked of the compiler
+
+template <int NJ, int LF>
+__global__ void __launch_bounds__(kIterThreads, kF32PersistMinBlocks)
+    k_it_deo2_f32p(const __grid_constant__ IterBatch<NJ> B, int ntot)
+{
+    static_assert(kIterThreads == kStagedConsumers, "K2Shared holds one slot per warp of a 256-thread block");
+    static_assert(kMaxJobs <= 64, "job mask is 64 bits");
+    __shared__ K2Shared sh;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    dep_wait();
+    dep_launch();
+    if (threadIdx.x < NJ) sh.cnt[threadIdx.x] = 0u;
+    __syncthreads();
+    int nb = 0;
+    for (int gt = (int)blockIdx.x; gt < ntot; gt += gridDim.x) {
+        int j, tile;
+        tile_of(B, gt, j, tile);
+        const IterJob &J = B.job[j];
+        SolverState *st = J.st;
+        if (st->halt) continue;  // the same for every thread of the block
+        const int Vh = J.g.Vh;
+        const int i = tile * kSites + threadIdx.x;
+        Acc2 dot;
+        acc_zero(dot);
+        if (i < Vh) {
+            Stencil S;
+            make_stencil(J.g, i, 0, S);
+            float2 o[3];
+            deo_site_f32<LF>(J.g, J.links, (const float2 *)J.t, S, i, 0, Vh, o);
+            const float2 *p = (const float2 *)J.ps + (size_t)st->base * 3 * Vh;
+            float2 *q = (float2 *)J.q;
+            const float a = st->a0_df.x;
+            float d = 0.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float2 pv = p[(size_t)c * Vh + i];
+                const float2 qv = make_float2(__fmaf_rn(a, pv.x, -o[c].x), __fmaf_rn(a, pv.y, -o[c].y));
+                q[(size_t)c * Vh + i] = qv;
+                d = __fmaf_rn(pv.x, qv.x, __fmaf_rn(pv.y, qv.y, d));
+            }
+            dot.s = d;
+        }
+        // tile partial in the order of block_reduce_acc_n<256>.  The warp
+        // sums alternate between two buffers: thread 0 has read buffer b
+        // before it reaches the barrier of the next tile, which every warp
+        // passes before it writes b again.
+        const int b = nb & 1;
+        warp_reduce_acc(dot);
+        if (lane == 0) sh.red[b][w] = (double)dot.s + (double)dot.c;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double v = 0.0;
+#pragma unroll
+            for (int k = 0; k < kIterThreads / 32; ++k) v += sh.red[b][k];
+            J.part[tile] = v;
+            sh.cnt[j] += 1u;
+        }
+        ++nb;
+    }
+    // one fence and one ticket per job this block worked on
+    if (threadIdx.x == 0) {
+        unsigned long long last = 0ull;
+        __threadfence();
+        for (int j = 0; j < B.njobs; ++j) {
+            const unsigned n = sh.cnt[j];
+            if (!n) continue;
+            const unsigned prev = atomicAdd(B.job[j].ticket, n);
+            if (prev + n == (unsigned)B.job[j].ntiles) last |= 1ull << j;
+        }
+        sh.last = last;
+    }
+    __syncthreads();
+    unsigned long long last = sh.last;
+    while (last) {
+        const int j = __ffsll((long long)last) - 1;
+        last &= last - 1ull;
+        const IterJob &J = B.job[j];
+        // partials in tile order (the order of tile_finish_block)
+        __threadfence();
+        double sum = sum_strided(J.part, J.ntiles, (int)threadIdx.x, kIterThreads);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_down_sync(0xFFFFFFFFu, sum, o);
+        if (lane == 0) sh.red[0][w] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int k = 0; k < kIterThreads / 32; ++k) tot += sh.red[0][k];
+            sh.tot = tot;
+            *J.ticket = 0u;
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) finalize_pq_warp(J.st, sh.tot);
+        __threadfence();
+        __syncthreads();
+    }
+}
+
+}  // namespace lqcd
