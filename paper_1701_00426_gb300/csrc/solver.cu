@@ -410,8 +410,9 @@ static int staged_solver_blocks()
     return g_st_blocks[dev];
 }
 
-// Resident blocks of the persistent FP32 K2 (all link formats and batch
-// sizes), once per device; 0 = the one-block-per-tile k_it_deo2 runs.
+// Grid of the persistent FP32 K2 and K3: the resident blocks of K2 (all
+// link formats and batch sizes), once per device; 0 = the
+// one-block-per-tile k_it_deo2 / k_it_upd_r run.
 static int g_f32p_blocks[64];
 static bool g_f32p_done[64];
 
@@ -431,9 +432,9 @@ int f32_persist_blocks()
     std::lock_guard<std::mutex> lk(g_st_mu);
     if (!g_f32p_done[dev]) {
         g_f32p_done[dev] = true;
-        const char *env = getenv("LQCD_F32_K2_PERSIST");
+        const char *env = getenv("LQCD_F32_PERSIST");
         if (env && env[0] == '0' && env[1] == '\0') {
-            g_f32p_blocks[dev] = 0;  // one block per tile (k_it_deo2)
+            g_f32p_blocks[dev] = 0;  // one block per tile (k_it_deo2, k_it_upd_r)
             return 0;
         }
         int nsm = 0;
@@ -518,7 +519,11 @@ static void launch_kernel_k(const IterBatch<NJ> &B, int k, int ntot, int vp, int
             launch_dep(k_it_deo2<NJ, VP_F32, LF_F16_12>, g1, tb, 0, s, dep, B);
         }
     }
-    if (k == 2) launch_dep(k_it_upd_r<NJ, VP_F32>, g1, tb, 0, s, dep, B);
+    if (k == 2) {
+        const int pb = std::min(ntot, f32_persist_blocks());
+        if (pb > 0) launch_dep(k_it_upd_r_p<NJ, VP_F32>, dim3((unsigned)pb), tb, 0, s, dep, B, ntot);
+        else launch_dep(k_it_upd_r<NJ, VP_F32>, g1, tb, 0, s, dep, B);
+    }
     if (k == 3) launch_dep(k_it_upd_shifts<NJ, VP_F32>, g1, tb, 0, s, dep, B);
 }
 

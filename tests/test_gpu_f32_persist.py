@@ -1,9 +1,10 @@
-"""The two forms of the FP32 / FP16 K2 (q = A p and <p, q> with the alpha /
-zeta finaliser) through the C ABI.
+"""The two forms of the FP32 / FP16 reduction kernels of the solver
+iteration through the C ABI: K2 (q = A p and <p, q>, alpha / zeta
+finaliser) and K3 (r -= alpha q and ||r||^2, beta / convergence finaliser).
 
-By default the low-precision solver iterations run the persistent kernel:
+By default the low-precision iterations run the persistent kernels:
 resident blocks walk the tiles, and each block takes one ticket per job.
-With LQCD_F32_K2_PERSIST=0 they run one block per tile, with a ticket per
+With LQCD_F32_PERSIST=0 they run one block per tile, with a ticket per
 tile. The site arithmetic, the in-tile reductions and the tile-ordered sum
 are the same, so the bar is bitwise equality. It is checked on solutions,
 iteration counts, reliable updates and true residuals.
@@ -65,13 +66,13 @@ np.savez(sys.argv[2], **out)
 '''
 
 
-def test_persistent_fp32_k2_bitwise_equal_to_one_block_per_tile(gpu, tmp_path):
+def test_persistent_fp32_reductions_bitwise_equal_to_one_block_per_tile(gpu, tmp_path):
     script = tmp_path / "k2.py"
     script.write_text(SCRIPT)
     res = []
     for flag in ("1", "0"):
         npz = tmp_path / f"k2_{flag}.npz"
-        env = dict(os.environ, LQCD_F32_K2_PERSIST=flag)
+        env = dict(os.environ, LQCD_F32_PERSIST=flag)
         r = subprocess.run([sys.executable, str(script), ROOT, str(npz)], env=env, capture_output=True, text=True,
                            timeout=600)
         assert r.returncode == 0, r.stderr[-2000:]
