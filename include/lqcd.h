@@ -260,13 +260,13 @@ int lqcd_deo_apply_h16(lqcd_ctx *ctx, int out_parity, const void *in, const floa
  *   LQCD_MRHS_R=<R>         the multi-RHS D_eo uses R fields per thread
  *                           (1, 2, 4, 8 or 16, when R divides n_rhs) instead
  *                           of timing the choices;
- *   LQCD_F32_PERSIST=0      the FP32 and FP16 solver iterations compute
- *                           q = A p, <p, q> and r -= alpha q, ||r||^2 with
- *                           one block per tile instead of a grid of
- *                           resident blocks that walk the tiles (read once
- *                           per process and device).
+ *   LQCD_PERSIST_REDUCTIONS=0  the solver iterations compute r -= alpha q,
+ *                           ||r||^2 (every precision) and, in FP32 and FP16,
+ *                           q = A p, <p, q> with one block per tile instead
+ *                           of a grid of resident blocks that walk the tiles
+ *                           (read once per process and device).
  * Every choice gives results within the documented tolerances; the
- * multi-RHS choices and the two forms of the FP32 reductions give identical
+ * multi-RHS choices and the two forms of the reductions give identical
  * bits. */
 
 /* Launch configuration the autotuner chose for lqcd_deo_apply_ex(prec,

@@ -189,7 +189,7 @@ int upload_links(lqcd_ctx *c, const double *host, size_t n)
     if ((st = c->lnk_h12.ensure(8 * Vh * (sizeof(uint4) + sizeof(uint2))))) return st;
     const int ntiles = (int)((Vh + kTile - 1) / kTile);
     c->stout_n = 0;  // new links: no stout levels
-    (void)f32_persist_blocks();  // occupancy query now, never first inside a graph capture
+    (void)persist_blocks();  // occupancy query now, never first inside a graph capture
     const bool staged = c->opts.staged && staged_deo_ready() && staged_solver_ready();
     if (staged) {
         if ((st = c->lnk_dfs.ensure(staged_df_elems(ntiles) * sizeof(float4)))) return st;

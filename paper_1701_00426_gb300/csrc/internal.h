@@ -193,7 +193,7 @@ int upload_links(lqcd_ctx *c, const double *host, size_t n);
 bool staged_deo_ready();
 int stage_wait_selftest(lqcd_ctx *c, double limit_s);
 bool staged_solver_ready();
-int f32_persist_blocks();   // grid of the persistent FP32 K2 / K3 on this device (0: one block per tile)
+int persist_blocks();   // grid of the persistent K2 / K3 reduction kernels on this device (0: one block per tile)
 bool staged_active(const lqcd_ctx *c);   // staged option on and the staged link stream built
 // LQCD_ESTATE before an upload; otherwise makes every link format current
 // after molecular-dynamics updates (FP32 copy promoted, formats rebuilt).

@@ -410,9 +410,10 @@ static int staged_solver_blocks()
     return g_st_blocks[dev];
 }
 
-// Grid of the persistent FP32 K2 and K3: the resident blocks of K2 (all
-// link formats and batch sizes), once per device; 0 = the
-// one-block-per-tile k_it_deo2 / k_it_upd_r run.
+// Grid of the persistent reduction kernels (FP32 / FP16 K2, K3 of every
+// precision): the resident blocks of the FP32 K2 (all link formats and batch
+// sizes), once per device; 0 = the one-block-per-tile k_it_deo2 /
+// k_it_upd_r run.
 static int g_f32p_blocks[64];
 static bool g_f32p_done[64];
 
@@ -425,14 +426,14 @@ static int kernel_resident_blocks(K kern, int nsm)
     return occ * nsm;
 }
 
-int f32_persist_blocks()
+int persist_blocks()
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
     std::lock_guard<std::mutex> lk(g_st_mu);
     if (!g_f32p_done[dev]) {
         g_f32p_done[dev] = true;
-        const char *env = getenv("LQCD_F32_PERSIST");
+        const char *env = getenv("LQCD_PERSIST_REDUCTIONS");
         if (env && env[0] == '0' && env[1] == '\0') {
             g_f32p_blocks[dev] = 0;  // one block per tile (k_it_deo2, k_it_upd_r)
             return 0;
@@ -495,7 +496,11 @@ static void launch_kernel_k(const IterBatch<NJ> &B, int k, int ntot, int vp, int
         if (k == 1 && sb > 0) launch_dep(k_it_deo2_st<NJ>, gs, ts, kStagedIterSmem, s, dep, B, ntot);
         if (k == 0 && sb == 0) launch_dep(k_it_deo1<NJ, VP_DF, LF_DF18>, g1, tb, 0, s, dep, B);
         if (k == 1 && sb == 0) launch_dep(k_it_deo2<NJ, VP_DF, LF_DF18>, g1, tb, 0, s, dep, B);
-        if (k == 2) launch_dep(k_it_upd_r<NJ, VP_DF>, g1, tb, 0, s, dep, B);
+        if (k == 2) {
+            const int pb = std::min(ntot, persist_blocks());
+            if (pb > 0) launch_dep(k_it_upd_r_p<NJ, VP_DF>, dim3((unsigned)pb), tb, 0, s, dep, B, ntot);
+            else launch_dep(k_it_upd_r<NJ, VP_DF>, g1, tb, 0, s, dep, B);
+        }
         if (k == 3) launch_dep(k_it_upd_shifts<NJ, VP_DF>, g1, tb, 0, s, dep, B);
         return;
     }
@@ -505,7 +510,7 @@ static void launch_kernel_k(const IterBatch<NJ> &B, int k, int ntot, int vp, int
         else launch_dep(k_it_deo1<NJ, VP_F32, LF_F16_12>, g1, tb, 0, s, dep, B);
     }
     if (k == 1) {
-        const int pb = std::min(ntot, f32_persist_blocks());
+        const int pb = std::min(ntot, persist_blocks());
         const dim3 gp((unsigned)pb);
         if (pb > 0) {
             if (lf == LF_F32_18) launch_dep(k_it_deo2_f32p<NJ, LF_F32_18>, gp, tb, 0, s, dep, B, ntot);
@@ -520,7 +525,7 @@ static void launch_kernel_k(const IterBatch<NJ> &B, int k, int ntot, int vp, int
         }
     }
     if (k == 2) {
-        const int pb = std::min(ntot, f32_persist_blocks());
+        const int pb = std::min(ntot, persist_blocks());
         if (pb > 0) launch_dep(k_it_upd_r_p<NJ, VP_F32>, dim3((unsigned)pb), tb, 0, s, dep, B, ntot);
         else launch_dep(k_it_upd_r<NJ, VP_F32>, g1, tb, 0, s, dep, B);
     }
