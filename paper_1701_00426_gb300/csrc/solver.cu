@@ -22,7 +22,7 @@
 #include <mutex>
 
 #include "solver_kernels.cuh"
-#include "solver_f32_persist.cuh"
+#include "solver_persist.cuh"
 
 namespace lqcd {
 

@@ -1,8 +1,9 @@
-// solver_f32_persist.cuh -- persistent forms of the reduction kernels of
-// the FP32 / FP16 multi-shift CG iteration (Sec. 2.2, Eqs. lineqeo and
-// shlineq):
-//   K2  q = (m^2 + sigma_b) p - D_eo t and <p, q>, alpha / zeta finaliser;
-//   K3  r -= alpha q and ||r||^2, beta / convergence finaliser.
+// solver_persist.cuh -- persistent forms of the reduction kernels of the
+// multi-shift CG iteration (Sec. 2.2, Eqs. lineqeo and shlineq):
+//   K2  q = (m^2 + sigma_b) p - D_eo t and <p, q>, alpha / zeta finaliser
+//       (FP32 and FP16 iterations; the double-float K2 is the staged kernel);
+//   K3  r -= alpha q and ||r||^2, beta / convergence finaliser (every
+//       precision).
 //
 // k_it_deo2 / k_it_upd_r launch one block per tile. Every block ends with a
 // fence and an atomic ticket, and the last block forms the total. In the
