@@ -46,7 +46,7 @@ COUNTS_KEY = "mscg_32x32x32x32_m0.01_15shifts_tol1e-10"
 # with the even sites (links stream from HBM at both sizes, spinors hit L2), so
 # a launch at V/2 sites moves bytes_per_site * V/2.  Reported only while the
 # kernel sources still hash to the captured version.
-K2_TRAFFIC = {"bytes_per_site": 1257.0, "src_sha256_16": "5bb091ef087d8f45",
+K2_TRAFFIC = {"bytes_per_site": 1257.7, "src_sha256_16": "1c46e0f51e652eed",
               "sources": ["solver_kernels.cuh", "stencil_staged.cuh", "bulk.cuh", "deo_core.cuh", "common.cuh", "iteration.h"]}
 
 

@@ -425,6 +425,11 @@ __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo2(const 
         T *q = (T *)J.q;
         Stencil S;
         make_stencil(J.g, i, 0, S);
+        // p of the epilogue, loaded before the stencil (its latency is spent
+        // under the hops)
+        T pp[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) pp[c] = p[(size_t)c * Vh + i];
         if constexpr (VP == VP_DF) {
             float2 res[6];
             bool bad = false;
@@ -432,7 +437,7 @@ __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo2(const 
             const float2 a = st->a0_df;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float4 pv = p[(size_t)c * Vh + i];
+                const float4 pv = pp[c];
                 const float2 qr = df_fma(a, make_float2(pv.x, pv.y), df_neg(res[2 * c]));
                 const float2 qi = df_fma(a, make_float2(pv.z, pv.w), df_neg(res[2 * c + 1]));
                 q[(size_t)c * Vh + i] = make_float4(qr.x, qr.y, qi.x, qi.y);
@@ -446,7 +451,7 @@ __global__ void __launch_bounds__(kIterThreads, LQCD_ITER_MINB) k_it_deo2(const 
             float d = 0.f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float2 pv = p[(size_t)c * Vh + i];
+                const float2 pv = pp[c];
                 const float2 qv = make_float2(__fmaf_rn(a, pv.x, -o[c].x), __fmaf_rn(a, pv.y, -o[c].y));
                 q[(size_t)c * Vh + i] = qv;
                 d = __fmaf_rn(pv.x, qv.x, __fmaf_rn(pv.y, qv.y, d));
@@ -578,6 +583,14 @@ __device__ __forceinline__ void k2_staged_consume(RingDF &R, K2Shared &sh, const
         const bool live = i < Vh;
         Stencil S;
         make_stencil(J.g, live ? i : 0, 0, S);
+        // p of the epilogue, loaded before the stencil so that its latency
+        // is spent under the eight hops
+        float4 pp[3];
+        if (live) {
+            const float4 *p = (const float4 *)J.ps + (size_t)st->base * 3 * Vh;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pp[c] = p[(size_t)c * Vh + i];
+        }
         float2 res[6];
         bool bad = false;
         deo_site_df_staged<SF_DF>(R, q, dead, J.g, J.t, S, Vh, res, bad);
@@ -585,12 +598,11 @@ __device__ __forceinline__ void k2_staged_consume(RingDF &R, K2Shared &sh, const
         Acc2 dot;
         acc_zero(dot);
         if (live) {
-            const float4 *p = (const float4 *)J.ps + (size_t)st->base * 3 * Vh;
             float4 *qv = (float4 *)J.q;
             const float2 a = st->a0_df;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float4 pv = p[(size_t)c * Vh + i];
+                const float4 pv = pp[c];
                 const float2 qr = df_fma(a, make_float2(pv.x, pv.y), df_neg(res[2 * c]));
                 const float2 qi = df_fma(a, make_float2(pv.z, pv.w), df_neg(res[2 * c + 1]));
                 qv[(size_t)c * Vh + i] = make_float4(qr.x, qr.y, qi.x, qi.y);

@@ -97,15 +97,20 @@ __global__ void __launch_bounds__(kIterThreads, kF32PersistMinBlocks)
         if (i < Vh) {
             Stencil S;
             make_stencil(J.g, i, 0, S);
+            // p of the epilogue, loaded before the stencil (its latency is
+            // spent under the hops)
+            const float2 *p = (const float2 *)J.ps + (size_t)st->base * 3 * Vh;
+            float2 pp[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) pp[c] = p[(size_t)c * Vh + i];
             float2 o[3];
             deo_site_f32<LF>(J.g, J.links, (const float2 *)J.t, S, i, 0, Vh, o);
-            const float2 *p = (const float2 *)J.ps + (size_t)st->base * 3 * Vh;
             float2 *q = (float2 *)J.q;
             const float a = st->a0_df.x;
             float d = 0.f;
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const float2 pv = p[(size_t)c * Vh + i];
+                const float2 pv = pp[c];
                 const float2 qv = make_float2(__fmaf_rn(a, pv.x, -o[c].x), __fmaf_rn(a, pv.y, -o[c].y));
                 q[(size_t)c * Vh + i] = qv;
                 d = __fmaf_rn(pv.x, qv.x, __fmaf_rn(pv.y, qv.y, d));
