@@ -151,25 +151,50 @@ __global__ void __launch_bounds__(kIterThreads, kF32PersistMinBlocks)
     dep_launch();
     if (threadIdx.x < NJ) sh.cnt[threadIdx.x] = 0u;
     __syncthreads();
+    // The block's tiles of live jobs; each tile's r and q are loaded while
+    // the previous tile's norm is reduced.
+    auto next_live = [&](int gt) -> int {
+        for (; gt < ntot; gt += gridDim.x) {
+            int j, tile;
+            tile_of(B, gt, j, tile);
+            if (!B.job[j].st->halt) return gt;
+        }
+        return -1;
+    };
+    T rc[3], qc[3];
+    auto load_rq = [&](int gt) {
+        int j, tile;
+        tile_of(B, gt, j, tile);
+        const IterJob &J = B.job[j];
+        const int Vh = J.g.Vh;
+        const int i = tile * kSites + threadIdx.x;
+        if (i >= Vh) return;
+        const T *r = (const T *)J.r, *q = (const T *)J.q;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            rc[c] = r[(size_t)c * Vh + i];
+            qc[c] = q[(size_t)c * Vh + i];
+        }
+    };
     int nb = 0;
-    for (int gt = (int)blockIdx.x; gt < ntot; gt += gridDim.x) {
+    int gt = next_live((int)blockIdx.x);
+    if (gt >= 0) load_rq(gt);
+    while (gt >= 0) {
         int j, tile;
         tile_of(B, gt, j, tile);
         const IterJob &J = B.job[j];
         SolverState *st = J.st;
-        if (st->halt) continue;  // the same for every thread of the block
         const int Vh = J.g.Vh;
         const int i = tile * kSites + threadIdx.x;
         Acc2 nrm;
         acc_zero(nrm);
         if (i < Vh) {
             T *r = (T *)J.r;
-            const T *q = (const T *)J.q;
             if constexpr (VP == VP_DF) {
                 const float2 na = df_neg(st->alpha_df);
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float4 rv = r[(size_t)c * Vh + i], qv = q[(size_t)c * Vh + i];
+                    const float4 rv = rc[c], qv = qc[c];
                     const float2 x = df_fma(na, make_float2(qv.x, qv.y), make_float2(rv.x, rv.y));
                     const float2 y = df_fma(na, make_float2(qv.z, qv.w), make_float2(rv.z, rv.w));
                     r[(size_t)c * Vh + i] = make_float4(x.x, x.y, y.x, y.y);
@@ -181,7 +206,7 @@ __global__ void __launch_bounds__(kIterThreads, kF32PersistMinBlocks)
                 float d = 0.f;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float2 rv = r[(size_t)c * Vh + i], qv = q[(size_t)c * Vh + i];
+                    const float2 rv = rc[c], qv = qc[c];
                     const float2 v = make_float2(__fmaf_rn(na, qv.x, rv.x), __fmaf_rn(na, qv.y, rv.y));
                     r[(size_t)c * Vh + i] = v;
                     d = __fmaf_rn(v.x, v.x, __fmaf_rn(v.y, v.y, d));
@@ -189,6 +214,8 @@ __global__ void __launch_bounds__(kIterThreads, kF32PersistMinBlocks)
                 nrm.s = d;
             }
         }
+        const int gn = next_live(gt + (int)gridDim.x);
+        if (gn >= 0) load_rq(gn);
         const int b = nb & 1;  // double-buffered warp sums, as in k_it_deo2_f32p
         warp_reduce_acc(nrm);
         if (lane == 0) sh.red[b][w] = (double)nrm.s + (double)nrm.c;
@@ -201,6 +228,7 @@ __global__ void __launch_bounds__(kIterThreads, kF32PersistMinBlocks)
             sh.cnt[j] += 1u;
         }
         ++nb;
+        gt = gn;
     }
     persist_finish(sh, B, [](SolverState *st, double tot) { finalize_rr_warp(st, tot); });
 }
