@@ -15,6 +15,9 @@
 // - After its last tile, a block takes one ticket per job it worked on.
 // - The block that completes a job's tile count sums the partials in tile
 //   order and runs the finaliser.
+// Within a block, K2 loads p before the stencil and K3 loads the next
+// tile's r and q before the current tile's reduction, so that the loads
+// land under work instead of behind the tile's barrier.
 // The per-site arithmetic and the in-tile reduction are those of the
 // one-block-per-tile kernels, so the tile partials, their tile-ordered sum
 // and the iteration are bitwise the same.
